@@ -1,0 +1,247 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) tile rasterizer for point-based
+ * neural rendering (3D Gaussian splatting) with foveated multi-level
+ * rendering, after MetaSapiens (arXiv 2407.00435).
+ *
+ * Pipeline (Sec. 2.1 "General PBNR Pipeline", Fig. 1; foveated version
+ * Sec. 4.1, Fig. 7E):
+ *
+ *   gs_project         Projection: each point's ellipsoid is splatted to an
+ *                      ellipse on the image plane (2D mean, 2D covariance,
+ *                      depth, view-dependent SH colour g, tile rectangle).
+ *                      With foveation, the Filtering stage's tile levels
+ *                      are computed here too (Sec. 4.2).
+ *   gs_bin_sort        Sorting: per tile, the intersecting ellipses ordered
+ *                      by depth, near to far (tile/point pairs, radix sort,
+ *                      per-tile ranges); foveated pairs with t > m dropped.
+ *   gs_render          Rasterization: Eq. 1a per pixel, front to back.
+ *   gs_render_fov      Rasterization of foveated views: each pixel composites
+ *                      the nested subset of its quality level, pixels in a
+ *                      band outside a region boundary also composite the next
+ *                      better level and the two colours are blended
+ *                      (Sec. 4.1 "Main Pipeline", Sec. 4.2 multi-versioning).
+ *   gs_render_backward Adjoint of the above for retraining through the
+ *                      renderer (Sec. 3.4, Sec. 4.3).
+ *
+ * Conventions shared by every entry point:
+ *   * Pointers named *_dev or documented as "device" are CUDA device
+ *     memory owned by the caller; the library never frees or keeps them
+ *     beyond what gs_project records in the plan (the scene and camera
+ *     pointers, which must stay valid until the last call that uses them).
+ *   * The library allocates nothing.  All scratch lives in the caller's
+ *     workspace (size from gs_workspace_size) and in the caller's host-side
+ *     plan buffer (size from gs_plan_size).
+ *   * Every call is asynchronous on the given stream and returns as soon as
+ *     its kernels are enqueued; host-side argument errors return at once
+ *     and enqueue nothing.  No call synchronises except gs_get_error.
+ *   * Device-side problems (pair capacity exceeded, a bounded wait that gave
+ *     up) are recorded in a sticky status word inside the workspace and
+ *     reported by gs_get_error.  No exception crosses the ABI.
+ *   * Points with a non-finite parameter are culled and counted.
+ *   * Outputs are overwritten, never accumulated; gradient outputs are
+ *     zeroed by gs_render_backward itself.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gs_status;
+#define GS_OK 0
+#define GS_ERR_INVALID_ARG 1 /* bad host-side argument; nothing enqueued */
+#define GS_ERR_CAPACITY 2    /* more visible items or pairs than the plan holds */
+#define GS_ERR_TIMEOUT 3     /* a bounded device-side wait gave up */
+#define GS_ERR_CUDA 4        /* a CUDA runtime call failed */
+#define GS_ERR_UNSUPPORTED 5 /* valid but not supported (e.g. SH degree > 3) */
+
+/* Pinhole camera, world -> camera: p_c = R p_w + t, OpenCV axes (x right,
+ * y down, z forward).  Pixel (x, y) has its centre at (x + 0.5, y + 0.5);
+ * the projected mean of p_c is (fx x/z + cx, fy y/z + cy).  Points with
+ * z <= znear or z >= zfar are culled.  80 bytes, no padding. */
+typedef struct gs_camera {
+  float R[9]; /* row-major */
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float znear, zfar;
+} gs_camera;
+
+/* The scene: the trainable parameters of each point listed in Sec. 2.1
+ * (position, scales, orientation, opacity, SH colour).  All device, fp32,
+ * C-contiguous. */
+typedef struct gs_scene {
+  int64_t n;          /* number of points N */
+  int32_t sh_degree;  /* 0..3; S = (sh_degree + 1)^2 coefficients */
+  int32_t reserved;
+  const float *means;     /* (N,3) world positions */
+  const float *scales;    /* (N,3) per-axis std, already activated (> 0) */
+  const float *quats;     /* (N,4) rotation (w,x,y,z), any length; 0 -> identity */
+  const float *opacities; /* (N,)  already activated, in (0,1) */
+  const float *sh;        /* (N,S,3) SH coefficients, RGB innermost */
+} gs_scene;
+
+#define GS_MAX_LEVELS 8
+
+/* Foveation (Sec. 4.1-4.2).  Quality level 1 is the best.  A pixel at
+ * distance d (pixels) from the gaze point has level 1 + #{k : d >= R_k}
+ * with ring radius R_k = fy * ring_tan[k] (eccentricity boundary k of L-1,
+ * ascending).  Pixels with R_k <= d < R_k + band_px (boundary k, level
+ * k+1) also composite level k and output
+ *   w C_{k+1} + (1 - w) C_k,  w = (d - R_k) / band_px.
+ * Level l composites the points whose quality bound m >= l (nested
+ * subsets).  A tile's filter level is the smallest level any of its pixels
+ * needs; a pair (tile, point) is kept iff tile level <= m. */
+typedef struct gs_fov {
+  int32_t n_levels;            /* L, 1..GS_MAX_LEVELS */
+  float band_px;               /* >= 0 */
+  float ring_tan[GS_MAX_LEVELS - 1]; /* host values, L-1 used, ascending */
+  const uint8_t *bound_m;      /* device (N,) quality bound m in 1..L */
+  const float *gaze_px;        /* device (V,2) gaze pixel per view */
+  const uint8_t *view_fov;     /* device (V,) 1 foveated / 0 plain; NULL = all foveated */
+  const float *opacity_lv;     /* device (L-1,N) opacity of levels 2..L, or NULL */
+  const float *dc_lv;          /* device (L-1,N,3) SH DC of levels 2..L, or NULL */
+} gs_fov;
+
+/* Plan options.  Zero-initialised fields take the defaults given. */
+typedef struct gs_config {
+  int32_t tile;          /* tile edge in pixels: 16 (default) or 8 */
+  int32_t chunk;         /* heavy-tile chunk length in points; 0 = default, <0 = off */
+  int32_t flags;         /* GS_FLAG_* */
+  int32_t max_levels;    /* largest foveation L the plan must hold; 0 = 4 */
+  int64_t max_visible;   /* capacity of visible (view, point) items; 0 = N*V */
+  int64_t max_pairs;     /* capacity of tile/point pairs; 0 = 4 * max_visible */
+} gs_config;
+
+#define GS_FLAG_FOVEATED 1u  /* reserve foveation state (levels, per-level params) */
+#define GS_FLAG_BACKWARD 2u  /* reserve per-item gradient scratch for gs_render_backward */
+
+/* Counters read back by gs_get_error. */
+typedef struct gs_counters {
+  uint32_t status;       /* sticky device status (GS_OK, GS_ERR_CAPACITY, GS_ERR_TIMEOUT) */
+  uint32_t reserved;
+  uint64_t n_visible;    /* visible (view, point) items M */
+  uint64_t n_pairs;      /* tile/point pairs K (before any capacity clamp) */
+  uint64_t n_nonfinite;  /* (view, point) items culled for a non-finite parameter */
+  uint64_t n_evals;      /* (pixel, point) alpha evaluations of the last render with stats */
+  uint64_t n_blends;     /* of which blended (alpha >= 1/255, before the stop) */
+} gs_counters;
+
+/* Opaque host-side plan, caller-allocated with gs_plan_size() bytes
+ * (8-byte aligned).  Holds sizes, workspace offsets and the pointers given
+ * to gs_project; contains no device memory of its own. */
+typedef struct gs_plan gs_plan;
+
+size_t gs_plan_size(void);
+
+/* Fill a plan for N points of SH degree sh_degree rendered into n_views
+ * views.  cams_host (host memory, n_views entries) fixes the image sizes;
+ * later calls must pass device cameras of the same sizes (poses may
+ * change).  cfg may be NULL.  Errors: GS_ERR_INVALID_ARG (sizes, tile),
+ * GS_ERR_UNSUPPORTED (sh_degree > 3). */
+gs_status gs_plan_init(gs_plan *plan, int64_t n, int32_t sh_degree,
+                       const gs_camera *cams_host, int32_t n_views,
+                       const gs_config *cfg);
+
+/* Bytes of device workspace the plan needs (256-byte aligned base). */
+size_t gs_workspace_size(const gs_plan *plan);
+
+/* Projection (+ FR tile levels).  scene: device arrays; cams_dev: device
+ * array of n_views gs_camera; fov: NULL for plain rendering, else the
+ * foveation of every view (requires GS_FLAG_FOVEATED).  Records the scene,
+ * camera and fov in the plan for the calls below.
+ * Errors: GS_ERR_INVALID_ARG (NULL pointer, ws too small or unaligned,
+ * n mismatch, bad fov), GS_ERR_CUDA. */
+gs_status gs_project(gs_plan *plan, void *ws, size_t ws_bytes,
+                     const gs_scene *scene, const gs_camera *cams_dev,
+                     const gs_fov *fov, cudaStream_t stream);
+
+/* Sorting: emit (tile, point) pairs of the visible items in depth order,
+ * stable radix sort by tile, per-tile ranges and the render work list.
+ * Device-side capacity overflow sets GS_ERR_CAPACITY (pairs beyond the
+ * capacity are dropped, nothing is written out of bounds). */
+gs_status gs_bin_sort(gs_plan *plan, void *ws, cudaStream_t stream);
+
+/* Rasterization of plain views (Eq. 1a) with the readings: alpha =
+ * min(0.99, o exp(-1/2 d^T Sigma'^-1 d)), points with alpha < 1/255
+ * skipped, compositing stops before the point that would take T below
+ * 1e-4.  Outputs (device, pixels of all views concatenated view by view,
+ * row-major inside a view):
+ *   rgb     (P,3)  C + T bg
+ *   T_final (P,)   final transmittance
+ *   last    (P,)   position, inside the pixel's tile list, of the last
+ *                  blended point (-1 if none)
+ *   stats   (4,N)  uint32 or NULL: tiles_touched, tiles_used,
+ *                  pixels_blended, pixels_dominated, summed over the views
+ *                  (cost statistics of Sec. 3.2: Comp_i and Val_i).
+ * bg is host memory (3 floats).  All views of the plan must be plain (the
+ * plan's fov, if any, is ignored). */
+gs_status gs_render(gs_plan *plan, void *ws, const float bg[3], float *rgb,
+                    float *T_final, int32_t *last, uint32_t *stats,
+                    cudaStream_t stream);
+
+/* Rasterization with the fov given to gs_project (views with view_fov = 0
+ * render plain).  T_final and last have two entries per pixel: [0] for the
+ * pixel's own level, [1] for the better level inside a blend band (1 and
+ * -1 elsewhere).  stats count the pixel's own level. */
+gs_status gs_render_fov(gs_plan *plan, void *ws, const float bg[3], float *rgb,
+                        float *T_final, int32_t *last, uint32_t *stats,
+                        cudaStream_t stream);
+
+/* Adjoint of the last gs_render / gs_render_fov of this plan for the loss
+ * sum(dL_drgb * rgb).  T_final and last are that call's outputs (same
+ * layout); bg the same background.  Gradients (device, fp32, overwritten):
+ * d_means (N,3), d_scales (N,3), d_quats (N,4), d_opac (N,), d_sh (N,S,3),
+ * d_opac_lv (L-1,N) and d_dc_lv (L-1,N,3) (may be NULL when the fov has no
+ * per-level parameters).  Requires GS_FLAG_BACKWARD. */
+gs_status gs_render_backward(gs_plan *plan, void *ws, const float *dL_drgb,
+                             const float *T_final, const int32_t *last,
+                             const float bg[3], float *d_means, float *d_scales,
+                             float *d_quats, float *d_opac, float *d_sh,
+                             float *d_opac_lv, float *d_dc_lv,
+                             cudaStream_t stream);
+
+/* Synchronise `stream`, read the device status word and counters.  Returns
+ * the device status (GS_OK if nothing went wrong); out may be NULL.  The
+ * status word is reset by gs_project and then keeps the first device-side
+ * error of the frame (project, bin_sort, render, backward). */
+gs_status gs_get_error(const gs_plan *plan, const void *ws, cudaStream_t stream,
+                       gs_counters *out);
+
+/* Clear the sticky device status word (asynchronous). */
+gs_status gs_clear_error(const gs_plan *plan, void *ws, cudaStream_t stream);
+
+/* Location of a workspace region, for tests and debugging.  region is one
+ * of GS_REGION_*; offset and bytes are relative to the workspace base.
+ * Visible items j = 0..M-1 are numbered point-major: point i's visible
+ * views in view order, points in index order. */
+#define GS_REGION_ITEM_GID 1     /* uint32 (M)  point index of visible item j */
+#define GS_REGION_ITEM_VIEW 2    /* uint32 (M)  view of visible item j */
+#define GS_REGION_ITEM_DEPTH 3   /* uint32 (M)  float bits of camera z */
+#define GS_REGION_ITEM_COUNT 4   /* uint32 (M)  kept tile pairs of item j */
+#define GS_REGION_RANGES 7       /* uint32 (T,2) [start, end) per global tile */
+#define GS_REGION_TILE_LEVEL 8   /* uint8  (T)  FR filter level per global tile */
+gs_status gs_ws_region(const gs_plan *plan, int32_t region, size_t *offset,
+                       size_t *bytes);
+
+/* Device pointers to the K sorted pairs of the last gs_bin_sort: global
+ * tile id and visible item j of each pair, ordered by (tile, depth, point
+ * index).  Synchronises `stream` (the sort picks its output buffer on the
+ * device).  Pointers stay valid until the next gs_bin_sort. */
+gs_status gs_sorted_pairs(const gs_plan *plan, const void *ws, cudaStream_t stream,
+                          const uint32_t **pair_tile, const uint32_t **pair_item);
+
+/* Geometry helpers (host): total tiles and pixels of the plan's views. */
+int64_t gs_plan_tiles(const gs_plan *plan);
+int64_t gs_plan_pixels(const gs_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

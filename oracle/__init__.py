@@ -74,7 +74,7 @@ def lib():
         L.orc_sh_basis.argtypes = [p, p]
         L.orc_sh_basis.restype = None
         L.orc_render.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p, p,
-                                 C.c_int64, p, p, p, p, p, p]
+                                 C.c_int64, p, p, p, p, p, p, p]
         L.orc_render_brute.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p, p, p,
                                        p, p, p]
         L.orc_backward.argtypes = [C.c_int, p, p, p, p, p, C.c_int, C.c_int, p, C.c_int,
@@ -248,6 +248,7 @@ class Image:
     last: np.ndarray     # (P, 2)
     margin: np.ndarray   # (P,)
     wband: np.ndarray    # (P,)
+    ambT: np.ndarray     # (P,)
     stats: np.ndarray | None  # (4, N)
 
 
@@ -267,6 +268,7 @@ def render(scene, cams, tile, bins: Bins, fov: FovArrays | None = None, bg=(0, 0
     last = np.zeros((P, 2), np.int32)
     margin = np.zeros(P)
     wband = np.zeros(P)
+    ambT = np.zeros(P)
     st = np.zeros((4, n), np.uint32) if (stats and pix is None) else None
     fs = fov.struct() if fov is not None else None
     bgv = _c64(bg)
@@ -274,10 +276,10 @@ def render(scene, cams, tile, bins: Bins, fov: FovArrays | None = None, bg=(0, 0
                           bins.vals.ctypes.data, bins.ranges.ctypes.data,
                           C.addressof(fs) if fs is not None else None, bgv.ctypes.data,
                           _ptr(pix_arr), P, rgb.ctypes.data, T.ctypes.data, last.ctypes.data,
-                          margin.ctypes.data, wband.ctypes.data, _ptr(st))
+                          margin.ctypes.data, wband.ctypes.data, ambT.ctypes.data, _ptr(st))
     if rc != 0:
         raise RuntimeError(f"orc_render failed: {rc}")
-    return Image(rgb, T, last, margin, wband, st)
+    return Image(rgb, T, last, margin, wband, ambT, st)
 
 
 def render_brute(scene, cams, tile, fov: FovArrays | None = None, bg=(0, 0, 0)):

@@ -615,6 +615,7 @@ typedef struct {
   double C[3], T;
   int32_t last;     /* list position of the last blended point, -1 if none */
   double margin;
+  double amb_T;     /* largest T before a decision within AMB_REL of its threshold */
   int64_t dom_item; /* item with the largest T alpha (first maximum) */
   double dom_w;
 } acc_t;
@@ -646,6 +647,12 @@ static double rel_margin(double a, double thr) {
   return fabs(a / thr - 1.0);
 }
 
+/* Decisions closer than this (relative) to their threshold are "ambiguous":
+ * a finite-precision evaluation may take the other branch.  A flipped
+ * decision at transmittance T changes the pixel by at most about T times
+ * twice the largest colour, which the tests use as the bound. */
+#define AMB_REL 1e-3
+
 /* Composite one accumulator of one pixel over list positions [s, e).
  * `px`, `py` are the pixel centre.  Only points with m >= lvl take part
  * (lvl = 1 with no foveation: all points). */
@@ -657,6 +664,7 @@ static void composite(int n, const double *vp, const double *opac,
   acc->T = 1.0;
   acc->last = -1;
   acc->margin = INFINITY;
+  acc->amb_T = 0.0;
   acc->dom_item = -1;
   acc->dom_w = -1.0;
   for (int64_t k = s; k < e; ++k) {
@@ -671,10 +679,12 @@ static void composite(int n, const double *vp, const double *opac,
     if (alpha > ALPHA_MAX) alpha = ALPHA_MAX;
     double m = rel_margin(alpha, ALPHA_MIN);
     if (m < acc->margin) acc->margin = m;
+    if (m < AMB_REL && acc->T > acc->amb_T) acc->amb_T = acc->T;
     if (alpha < ALPHA_MIN) continue;
     double Tn = acc->T * (1.0 - alpha);
     m = rel_margin(Tn, T_MIN);
     if (m < acc->margin) acc->margin = m;
+    if (m < AMB_REL && acc->T > acc->amb_T) acc->amb_T = acc->T;
     if (Tn < T_MIN) break;
     double col[3];
     level_colour(fov, pv, n, i, lvl, col, NULL);
@@ -707,13 +717,14 @@ static void shade_pixel(int n, int V, const orc_cam *cams, const double *vp,
                         int64_t e, const orc_fov *fov, const double bg[3],
                         int v, int x, int y, double *rgb, double *T,
                         int32_t *last, double *margin, double *wband,
-                        acc_t *outA) {
+                        double *ambT, acc_t *outA) {
   (void)V;
   fov_px fp = pixel_level(&cams[v], fov, v, x, y);
   double px = x + 0.5, py = y + 0.5;
   acc_t A, B;
   composite(n, vp, opac, vals, s, e, fov, fp.level, px, py, &A);
   double mg = A.margin;
+  double at = fp.in_band ? fp.w * A.amb_T : A.amb_T;
   double out[3];
   for (int ch = 0; ch < 3; ++ch) out[ch] = A.C[ch] + A.T * bg[ch];
   T[0] = A.T; last[0] = A.last;
@@ -721,6 +732,7 @@ static void shade_pixel(int n, int V, const orc_cam *cams, const double *vp,
   if (fp.in_band) {
     composite(n, vp, opac, vals, s, e, fov, fp.level - 1, px, py, &B);
     if (B.margin < mg) mg = B.margin;
+    if ((1.0 - fp.w) * B.amb_T > at) at = (1.0 - fp.w) * B.amb_T;
     for (int ch = 0; ch < 3; ++ch)
       out[ch] = fp.w * out[ch] + (1.0 - fp.w) * (B.C[ch] + B.T * bg[ch]);
     T[1] = B.T; last[1] = B.last;
@@ -728,6 +740,7 @@ static void shade_pixel(int n, int V, const orc_cam *cams, const double *vp,
   for (int ch = 0; ch < 3; ++ch) rgb[ch] = out[ch];
   if (margin) *margin = mg;
   if (wband) *wband = fp.w;
+  if (ambT) *ambT = at;
   if (outA) *outA = A;
 }
 
@@ -735,7 +748,8 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
                const double *vp, const double *opac, const uint32_t *vals,
                const uint32_t *ranges, const orc_fov *fov, const double bg[3],
                const int64_t *pix, int64_t npix, double *rgb, double *T,
-               int32_t *last, double *margin, double *wband, uint32_t *stats) {
+               int32_t *last, double *margin, double *wband, double *ambT,
+               uint32_t *stats) {
   if (pix) {
     for (int64_t q = 0; q < npix; ++q) {
       int x, y;
@@ -746,7 +760,8 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
       int64_t gt = tile_base(V, cams, tile, v) + (int64_t)(y / tile) * tx + x / tile;
       shade_pixel(n, V, cams, vp, opac, vals, ranges[2 * gt], ranges[2 * gt + 1], fov,
                   bg, v, x, y, &rgb[3 * q], &T[2 * q], &last[2 * q],
-                  margin ? &margin[q] : NULL, wband ? &wband[q] : NULL, NULL);
+                  margin ? &margin[q] : NULL, wband ? &wband[q] : NULL,
+                  ambT ? &ambT[q] : NULL, NULL);
     }
     return 0;
   }
@@ -781,7 +796,8 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
             acc_t A;
             shade_pixel(n, V, cams, vp, opac, vals, s, e, fov, bg, v, x, y,
                         &rgb[3 * q], &T[2 * q], &last[2 * q],
-                        margin ? &margin[q] : NULL, wband ? &wband[q] : NULL, &A);
+                        margin ? &margin[q] : NULL, wband ? &wband[q] : NULL,
+                        ambT ? &ambT[q] : NULL, &A);
             if (stats && A.last >= 0) {
               /* re-walk to mark blended points (statistics of accumulator A) */
               fov_px fp = pixel_level(c, fov, v, x, y);
@@ -861,7 +877,7 @@ int orc_render_brute(int n, int V, const orc_cam *cams, int tile,
         for (int k = 0; k < cnt; ++k) ids[k] = lst[k].id;
         int64_t q = pb0 + (int64_t)y * c->width + x;
         shade_pixel(n, V, cams, vp, opac, ids, 0, cnt, fov, bg, v, x, y,
-                    &rgb[3 * q], &T[2 * q], &last[2 * q], NULL, NULL, NULL);
+                    &rgb[3 * q], &T[2 * q], &last[2 * q], NULL, NULL, NULL, NULL);
       }
   }
   free(lst);

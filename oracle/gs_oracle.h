@@ -120,6 +120,10 @@ void orc_sh_basis(const double dir[3], double Y[16]);
  *   margin   : (npix,)   smallest relative distance of any alpha-floor or
  *              early-stop decision from its threshold (ambiguity flag)
  *   wband    : (npix,)   blend weight w of accumulator A (1 outside bands)
+ *   ambT     : (npix,)   largest transmittance (weighted by the blend
+ *              weight) at which a decision lies within 1e-3 (relative) of
+ *              its threshold; 0 if none.  Bounds what a flipped decision
+ *              can change.
  *   stats    : (4,N) uint32 or NULL: tiles_touched, tiles_used,
  *              pixels_blended, pixels_dominated (accumulator A); only
  *              meaningful when pix == NULL (the whole batch).
@@ -129,7 +133,7 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
                const uint32_t *vals, const uint32_t *ranges,
                const orc_fov *fov, const double bg[3],
                const int64_t *pix, int64_t npix, double *rgb, double *T,
-               int32_t *last, double *margin, double *wband,
+               int32_t *last, double *margin, double *wband, double *ambT,
                uint32_t *stats);
 
 /* Brute force: same output as orc_render for all pixels, but each pixel

@@ -1,0 +1,146 @@
+// gs_internal.cuh -- shared declarations of the CUDA path (not part of the
+// public ABI).  Workspace layout, the host-side plan, device-side view table
+// and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+// Readings of the constants that the paper defers to the 3DGS paper
+// (Sec. 2.1, after Eq. 1).  Kept in one place.
+constexpr float kLowpass = 0.3f;          // px^2 added to the 2D covariance
+constexpr float kAlphaMax = 0.99f;        // alpha clamp
+constexpr float kTMin = 1e-4f;            // stop before T would drop below
+constexpr float kClampFov = 1.3f;         // J uses x/z clamped to 1.3 tan(fov/2)
+constexpr float kShOffset = 0.5f;         // colour = max(0, SH.Y + 0.5)
+// log2(1/255): alpha >= 1/255  <=>  log2(alpha) >= kLog2AlphaMin
+constexpr float kLog2AlphaMin = -7.99435343685886f;
+// sqrt(0.5 * log2(e)): whitened coordinates t with -(t1^2+t2^2) = log2 of
+// exp(-1/2 d^T Q d)
+constexpr float kWhiten = 0.84932180028801904f;
+
+constexpr int kMaxViews = 4096;
+
+// --------------------------------------------------------------------------
+// workspace regions
+// --------------------------------------------------------------------------
+enum Region : int {
+  R_HDR = 0,
+  R_VIEWS,
+  R_TILE_LEVEL,
+  R_REC_MEAN,    // float4 (mx_hi, my_hi, mx_lo, my_lo)
+  R_REC_SHAPE,   // float4 whitening rows (w1x, w1y, w2x, w2y)
+  R_REC_COLOR,   // float4 (r, g, b, log2 opacity)
+  R_REC_REST,    // float4 (view-dependent colour part r, g, b, -) [foveated]
+  R_REC_DEPTH,   // u32 float bits of camera z
+  R_REC_COUNT,   // u32 kept tile pairs
+  R_REC_RECT,    // uint2 packed tile rect (x0 | x1 << 16, y0 | y1 << 16)
+  R_REC_GID,     // u32 point index
+  R_REC_VIEW,    // u32 view index
+  R_REC_M,       // u8 quality bound (foveated)
+  R_DKEY_A, R_DKEY_B, R_DVAL_A, R_DVAL_B,   // depth sort ping-pong (M)
+  R_OFFSETS,     // u32 exclusive pair offsets in depth order (M)
+  R_PKEY_A, R_PKEY_B, R_PVAL_A, R_PVAL_B,   // pair sort ping-pong (K)
+  R_RANGES,      // uint2 per tile
+  R_WORK,        // u32 render work list (tiles, heavy first)
+  R_SCAN,        // u64 lookback slots of single-value scans
+  R_LOOKBACK,    // u64 radix lookback slots, two buffers
+  R_GRAD_ITEM,   // float per item gradient scratch (backward)
+  R_GRAD_LV,     // float per (level, item) gradient scratch (backward, foveated)
+  R_COUNT_
+};
+
+// Header at the start of the workspace (device).
+struct Hdr {
+  uint32_t status;
+  uint32_t pad0;
+  unsigned long long n_visible;   // M (raw)
+  unsigned long long n_pairs;     // K (raw)
+  unsigned long long n_nonfinite;
+  unsigned long long n_evals;     // (pixel, point) evaluations of the last stats render
+  unsigned long long n_blends;    // blends of the last stats render
+  uint32_t ticket[32];            // partition tickets of lookback kernels
+  uint32_t sel_depth;             // buffer holding the sorted depth order (0 = A)
+  uint32_t sel_pair;              // buffer holding the sorted pairs (0 = A)
+  uint32_t skip[8];               // per-pass "digit constant" flags
+  uint32_t hist[2][4][256];       // digit histograms: [sort][pass][digit]
+};
+
+// Per-view constants, computed on the device from the cameras.
+struct ViewDev {
+  int32_t W, H, tx, ty;
+  long long tile_base, pix_base;
+  float ccx, ccy, ccz;   // camera centre in world coordinates
+  float limx, limy;      // clamp of x/z, y/z used by J
+  int32_t fov;           // 1 = foveated
+  float gx, gy;          // gaze pixel
+  float R[GS_MAX_LEVELS - 1];   // ring radii (px), fy * ring_tan
+  float pad[1];
+};
+
+// Lookback flags in the top two bits of a 64-bit slot.
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 20;   // bounded waits (about a second), then GS_ERR_TIMEOUT
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortPart = kSortThreads * kSortItems;   // 4096 keys per partition
+constexpr int kProjThreads = 128;
+
+}  // namespace gs
+
+// Host-side plan (what gs_plan_size() measures).
+struct gs_plan {
+  uint64_t magic;
+  int64_t n;
+  int32_t sh_degree, V, tile, chunk;
+  uint32_t flags;
+  int32_t num_sms;
+  int64_t tiles_total, pixels_total;
+  int64_t max_visible, max_pairs;
+  int32_t tile_bits;
+  int32_t last_fov;       // last render was foveated
+  size_t off[gs::R_COUNT_];
+  size_t bytes[gs::R_COUNT_];
+  size_t ws_bytes;
+  // recorded by gs_project
+  gs_scene scene;
+  const gs_camera *cams;
+  int32_t has_fov;
+  int32_t fov_mv;         // per-level opacity/DC present
+  gs_fov fov;
+  int32_t max_w, max_h;
+};
+
+namespace gs {
+
+template <typename T>
+inline T *region(const gs_plan *p, void *ws, int r) {
+  return reinterpret_cast<T *>(static_cast<char *>(ws) + p->off[r]);
+}
+
+// ---- launchers (each returns cudaGetLastError()) ------------------------
+cudaError_t launch_views(const gs_plan *p, void *ws, cudaStream_t s);
+cudaError_t launch_tile_levels(const gs_plan *p, void *ws, cudaStream_t s);
+cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s);
+cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s);
+cudaError_t launch_render(const gs_plan *p, void *ws, bool fov, const float bg[3],
+                          float *rgb, float *T, int32_t *last, uint32_t *stats,
+                          cudaStream_t s);
+cudaError_t launch_backward(const gs_plan *p, void *ws, const float *dL, const float *T,
+                            const int32_t *last, const float bg[3], float *d_means,
+                            float *d_scales, float *d_quats, float *d_opac, float *d_sh,
+                            float *d_opac_lv, float *d_dc_lv, cudaStream_t s);
+
+// device helpers shared by several kernels
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) {
+  atomicCAS(status, 0u, code);
+}
+
+}  // namespace gs

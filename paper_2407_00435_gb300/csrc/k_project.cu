@@ -1,0 +1,580 @@
+// k_project.cu -- view table, foveation tile levels and the projection
+// kernel (Sec. 2.1 "Projection"; Sec. 4.2 "Filtering").
+//
+// This translation unit is compiled with --fmad=false: the "keyed" part of
+// the projection (visibility, camera depth, tile rectangle, the per-pixel
+// foveation level) must be bit-identical to a plain IEEE evaluation of the
+// same expressions in the same order, so no multiply-add may be contracted
+// implicitly.  Where a fused multiply-add is wanted (error-free
+// transformations of the value path) it is written as fmaf().
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs_internal.cuh"
+#include "lookback.cuh"
+
+namespace gs {
+
+// --------------------------------------------------------------------------
+// view table
+// --------------------------------------------------------------------------
+struct FovArgs {
+  int32_t n_levels;
+  float band;
+  float ring_tan[GS_MAX_LEVELS - 1];
+  const float *gaze;
+  const uint8_t *view_fov;
+};
+
+__global__ void k_views(const gs_camera *cams, int V, int tile, FovArgs fa, int has_fov,
+                        ViewDev *views, Hdr *hdr, long long tiles_total,
+                        long long pixels_total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long tb = 0, pb = 0;
+  for (int v = 0; v < V; ++v) {
+    const gs_camera c = cams[v];
+    ViewDev d;
+    d.W = c.width;
+    d.H = c.height;
+    d.tx = (c.width + tile - 1) / tile;
+    d.ty = (c.height + tile - 1) / tile;
+    d.tile_base = tb;
+    d.pix_base = pb;
+    // camera centre -R^T t
+    d.ccx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
+    d.ccy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
+    d.ccz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
+    d.limx = kClampFov * ((0.5f * (float)c.width) / c.fx);
+    d.limy = kClampFov * ((0.5f * (float)c.height) / c.fy);
+    d.fov = has_fov && fa.n_levels > 1 ? (fa.view_fov ? (int)fa.view_fov[v] : 1) : 0;
+    d.gx = has_fov ? fa.gaze[2 * v] : 0.0f;
+    d.gy = has_fov ? fa.gaze[2 * v + 1] : 0.0f;
+    for (int k = 0; k < GS_MAX_LEVELS - 1; ++k)
+      d.R[k] = (has_fov && k < fa.n_levels - 1) ? c.fy * fa.ring_tan[k] : 0.0f;
+    d.pad[0] = 0.0f;
+    views[v] = d;
+    tb += (long long)d.tx * d.ty;
+    pb += (long long)c.width * c.height;
+  }
+  // the device cameras must describe the image sizes the plan was made for
+  if (tb != tiles_total || pb != pixels_total) set_status(&hdr->status, GS_ERR_INVALID_ARG);
+}
+
+cudaError_t launch_views(const gs_plan *p, void *ws, cudaStream_t s) {
+  FovArgs fa = {};
+  if (p->has_fov) {
+    fa.n_levels = p->fov.n_levels;
+    fa.band = p->fov.band_px;
+    for (int k = 0; k < GS_MAX_LEVELS - 1; ++k) fa.ring_tan[k] = p->fov.ring_tan[k];
+    fa.gaze = p->fov.gaze_px;
+    fa.view_fov = p->fov.view_fov;
+  }
+  k_views<<<1, 32, 0, s>>>(p->cams, p->V, p->tile, fa, p->has_fov, region<ViewDev>(p, ws, R_VIEWS),
+                           region<Hdr>(p, ws, R_HDR), p->tiles_total, p->pixels_total);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// foveation level of a pixel (keyed FP32; same expressions as the oracle)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int pixel_need_level(const ViewDev &vd, int L, float band, int x,
+                                                int y) {
+  float dx = ((float)x + 0.5f) - vd.gx;
+  float dy = ((float)y + 0.5f) - vd.gy;
+  float d2 = dx * dx + dy * dy;
+  int lvl = 1;
+  for (int k = 0; k < L - 1; ++k) {
+    float Rk = vd.R[k];
+    if (d2 >= Rk * Rk) lvl++;
+  }
+  int need = lvl;
+  if (lvl >= 2 && band > 0.0f) {
+    float Rb = vd.R[lvl - 2] + band;
+    if (d2 < Rb * Rb) need = lvl - 1;
+  }
+  return need;
+}
+
+// One block per tile; the tile's filter level is the smallest level any of
+// its pixels needs (Sec. 4.2: a point takes part in a tile only if the
+// tile's level t <= m).
+__global__ void k_tile_levels(const ViewDev *views, int V, int tile, int L, float band,
+                              uint8_t *tile_level, long long tiles_total) {
+  long long t = blockIdx.x;
+  if (t >= tiles_total) return;
+  // find the view by binary search over tile bases
+  int lo = 0, hi = V - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (views[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+  }
+  const ViewDev vd = views[lo];
+  int local = (int)(t - vd.tile_base);
+  int bx = local % vd.tx, by = local / vd.tx;
+  int need = 255;
+  if (vd.fov) {
+    for (int q = threadIdx.x; q < tile * tile; q += blockDim.x) {
+      int x = bx * tile + q % tile, y = by * tile + q / tile;
+      if (x < vd.W && y < vd.H) need = min(need, pixel_need_level(vd, L, band, x, y));
+    }
+  } else {
+    need = 1;
+  }
+  // block minimum
+  for (int o = 16; o > 0; o >>= 1) need = min(need, __shfl_xor_sync(0xffffffffu, need, o));
+  __shared__ int wmin[32];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = need;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 255;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = min(m, wmin[w]);
+    tile_level[t] = (uint8_t)m;
+  }
+}
+
+cudaError_t launch_tile_levels(const gs_plan *p, void *ws, cudaStream_t s) {
+  if (!p->has_fov || p->tiles_total == 0) return cudaSuccess;
+  k_tile_levels<<<(unsigned)p->tiles_total, 64, 0, s>>>(
+      region<ViewDev>(p, ws, R_VIEWS), p->V, p->tile, p->fov.n_levels, p->fov.band_px,
+      region<uint8_t>(p, ws, R_TILE_LEVEL), p->tiles_total);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// projection
+// --------------------------------------------------------------------------
+struct ProjArgs {
+  long long n;
+  int V, S, tile;
+  const float *means, *scales, *quats, *opac, *sh;
+  const gs_camera *cams;
+  const ViewDev *views;
+  const uint8_t *tile_level;   // null unless foveated
+  const uint8_t *bound_m;      // null unless foveated
+  Hdr *hdr;
+  unsigned long long *scan_slots;
+  long long max_visible;
+  float4 *rec_mean, *rec_shape, *rec_color, *rec_rest;
+  uint32_t *rec_depth, *rec_count, *rec_gid, *rec_view;
+  uint2 *rec_rect;
+  uint8_t *rec_m;
+};
+
+struct Keyed {
+  float px, py, pz;      // camera-space mean (plain FP32)
+  float tx, ty;          // px/pz, py/pz
+  int x0, x1, y0, y1;    // inclusive tile rect
+  float M[9];            // Rq diag(s)
+  float j00, j02, j11, j12;
+};
+
+// The keyed FP32 projection.  Every statement is one IEEE operation in a
+// fixed order; the FP32 mode of the oracle evaluates the same expressions.
+__device__ __forceinline__ bool keyed_project(const float mu[3], const float s[3],
+                                              const float q[4], const gs_camera &c,
+                                              int tile, int tiles_x, int tiles_y, Keyed &k) {
+  const float *R = c.R;
+  float px = R[0] * mu[0];
+  px = px + R[1] * mu[1];
+  px = px + R[2] * mu[2];
+  px = px + c.t[0];
+  float py = R[3] * mu[0];
+  py = py + R[4] * mu[1];
+  py = py + R[5] * mu[2];
+  py = py + c.t[1];
+  float pz = R[6] * mu[0];
+  pz = pz + R[7] * mu[1];
+  pz = pz + R[8] * mu[2];
+  pz = pz + c.t[2];
+  if (!(pz > c.znear) || !(pz < c.zfar)) return false;
+
+  float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+  float n2 = qw * qw;
+  n2 = n2 + qx * qx;
+  n2 = n2 + qy * qy;
+  n2 = n2 + qz * qz;
+  if (n2 > 0.0f) {
+    float inv = 1.0f / sqrtf(n2);
+    qw = qw * inv; qx = qx * inv; qy = qy * inv; qz = qz * inv;
+  } else {
+    qw = 1.0f; qx = 0.0f; qy = 0.0f; qz = 0.0f;
+  }
+  float r[9];
+  r[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+  r[1] = 2.0f * (qx * qy - qw * qz);
+  r[2] = 2.0f * (qx * qz + qw * qy);
+  r[3] = 2.0f * (qx * qy + qw * qz);
+  r[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+  r[5] = 2.0f * (qy * qz - qw * qx);
+  r[6] = 2.0f * (qx * qz - qw * qy);
+  r[7] = 2.0f * (qy * qz + qw * qx);
+  r[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) k.M[3 * j + kk] = r[3 * j + kk] * s[kk];
+
+  float W = (float)c.width, H = (float)c.height;
+  float limx = 1.3f * ((0.5f * W) / c.fx);
+  float limy = 1.3f * ((0.5f * H) / c.fy);
+  float tx = px / pz;
+  float ty = py / pz;
+  float txc = fminf(fmaxf(tx, -limx), limx);
+  float tyc = fminf(fmaxf(ty, -limy), limy);
+  float xc = txc * pz;
+  float yc = tyc * pz;
+  float iz = 1.0f / pz;
+  float iz2 = iz * iz;
+  float j00 = c.fx * iz;
+  float j02 = -((c.fx * xc) * iz2);
+  float j11 = c.fy * iz;
+  float j12 = -((c.fy * yc) * iz2);
+  float T0[3], T1[3];
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    T0[kk] = j00 * R[kk] + j02 * R[6 + kk];
+    T1[kk] = j11 * R[3 + kk] + j12 * R[6 + kk];
+  }
+  float G0[3], G1[3];
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    float g0 = T0[0] * k.M[kk];
+    g0 = g0 + T0[1] * k.M[3 + kk];
+    g0 = g0 + T0[2] * k.M[6 + kk];
+    G0[kk] = g0;
+    float g1 = T1[0] * k.M[kk];
+    g1 = g1 + T1[1] * k.M[3 + kk];
+    g1 = g1 + T1[2] * k.M[6 + kk];
+    G1[kk] = g1;
+  }
+  float a = G0[0] * G0[0];
+  a = a + G0[1] * G0[1];
+  a = a + G0[2] * G0[2];
+  a = a + 0.3f;
+  float b = G0[0] * G1[0];
+  b = b + G0[1] * G1[1];
+  b = b + G0[2] * G1[2];
+  float cc = G1[0] * G1[0];
+  cc = cc + G1[1] * G1[1];
+  cc = cc + G1[2] * G1[2];
+  cc = cc + 0.3f;
+  float det = a * cc - b * b;
+  if (!(det > 0.0f)) return false;
+  float mid = 0.5f * (a + cc);
+  float disc = mid * mid - det;
+  disc = fmaxf(0.1f, disc);
+  float lam = mid + sqrtf(disc);
+  float rad = ceilf(3.0f * sqrtf(lam));
+  float u = c.fx * tx + c.cx;
+  float v = c.fy * ty + c.cy;
+  float invB = 1.0f / (float)tile;
+  float x0 = floorf((u - rad) * invB);
+  float x1 = floorf((u + rad) * invB);
+  float y0 = floorf((v - rad) * invB);
+  float y1 = floorf((v + rad) * invB);
+  x0 = fmaxf(x0, 0.0f);
+  y0 = fmaxf(y0, 0.0f);
+  x1 = fminf(x1, (float)(tiles_x - 1));
+  y1 = fminf(y1, (float)(tiles_y - 1));
+  if (!(x0 <= x1) || !(y0 <= y1)) return false;
+  k.px = px; k.py = py; k.pz = pz;
+  k.tx = tx; k.ty = ty;
+  k.x0 = (int)x0; k.x1 = (int)x1; k.y0 = (int)y0; k.y1 = (int)y1;
+  k.j00 = j00; k.j02 = j02; k.j11 = j11; k.j12 = j12;
+  return true;
+}
+
+// ---- error-free transformations for the value path -----------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// Compensated R_row . mu + t: returns hi + lo to about twice FP32 precision.
+__device__ __forceinline__ void dot3_comp(const float *Rr, const float mu[3], float t, float &hi,
+                                          float &lo) {
+  float p0, e0, p1, e1, p2, e2;
+  two_prod(Rr[0], mu[0], p0, e0);
+  two_prod(Rr[1], mu[1], p1, e1);
+  two_prod(Rr[2], mu[2], p2, e2);
+  float s, es, s2, es2, s3, es3;
+  two_sum(p0, p1, s, es);
+  two_sum(s, p2, s2, es2);
+  two_sum(s2, t, s3, es3);
+  hi = s3;
+  lo = ((e0 + e1) + (e2 + es)) + (es2 + es3);
+}
+
+// (fh + fl) / (zh + zl) * f + c  as hi + lo
+__device__ __forceinline__ void proj_comp(float xh, float xl, float zh, float zl, float f,
+                                          float c, float &uh, float &ul) {
+  float q = xh / zh;
+  float r = fmaf(-q, zh, xh);          // exact residual of the division
+  r = r + xl;
+  r = fmaf(-q, zl, r);
+  float ql = r / zh;
+  float p, ep;
+  two_prod(f, q, p, ep);
+  float s, es;
+  two_sum(p, c, s, es);
+  uh = s;
+  ul = es + fmaf(f, ql, ep);
+}
+
+// Real SH basis (degree <= 3) at unit direction, ordered m = -l..l.
+__device__ __forceinline__ void sh_basis(float x, float y, float z, int S, float Y[16]) {
+  const float k1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+  const float k2a = 1.0925484305920792f;   // 1/2 sqrt(15 / pi)
+  const float k2b = 0.31539156525252005f;  // 1/4 sqrt(5 / pi)
+  const float k2c = 0.54627421529603959f;  // 1/4 sqrt(15 / pi)
+  const float k3a = 0.59004358992664352f;  // 1/4 sqrt(35 / (2 pi))
+  const float k3b = 2.8906114426405538f;   // 1/2 sqrt(105 / pi)
+  const float k3c = 0.45704579946446572f;  // 1/4 sqrt(21 / (2 pi))
+  const float k3d = 0.37317633259011546f;  // 1/4 sqrt(7 / pi)
+  const float k3e = 1.4453057213202769f;   // 1/4 sqrt(105 / pi)
+  Y[0] = 0.28209479177387814f;
+  if (S > 1) {
+    Y[1] = -k1 * y;
+    Y[2] = k1 * z;
+    Y[3] = -k1 * x;
+  }
+  if (S > 4) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = k2a * x * y;
+    Y[5] = -k2a * y * z;
+    Y[6] = k2b * (2.0f * zz - xx - yy);
+    Y[7] = -k2a * x * z;
+    Y[8] = k2c * (xx - yy);
+    if (S > 9) {
+      Y[9] = -k3a * y * (3.0f * xx - yy);
+      Y[10] = k3b * x * y * z;
+      Y[11] = -k3c * y * (4.0f * zz - xx - yy);
+      Y[12] = k3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+      Y[13] = -k3c * x * (4.0f * zz - xx - yy);
+      Y[14] = k3e * z * (xx - yy);
+      Y[15] = -k3a * x * (xx - 3.0f * yy);
+    }
+  }
+}
+
+__device__ __forceinline__ bool all_finite(const float *p, int n) {
+  bool ok = true;
+  for (int k = 0; k < n; ++k) ok &= isfinite(p[k]);
+  return ok;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
+  __shared__ uint32_t s_part;
+  __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_wsum[kProjThreads / 32];
+  __shared__ uint32_t s_nonfinite;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_part = atomicAdd(&a.hdr->ticket[0], 1u);
+    s_nonfinite = 0;
+  }
+  __syncthreads();
+  const uint32_t part = s_part;
+  const long long i = (long long)part * kProjThreads + tid;
+  const bool valid = i < a.n;
+
+  float mu[3] = {0, 0, 0}, sc[3] = {1, 1, 1}, q[4] = {1, 0, 0, 0}, op = 0.5f;
+  float shc[S * 3];
+  bool fin = false;
+  if (valid) {
+    mu[0] = a.means[3 * i]; mu[1] = a.means[3 * i + 1]; mu[2] = a.means[3 * i + 2];
+    sc[0] = a.scales[3 * i]; sc[1] = a.scales[3 * i + 1]; sc[2] = a.scales[3 * i + 2];
+    q[0] = a.quats[4 * i]; q[1] = a.quats[4 * i + 1];
+    q[2] = a.quats[4 * i + 2]; q[3] = a.quats[4 * i + 3];
+    op = a.opac[i];
+#pragma unroll
+    for (int k = 0; k < S * 3; ++k) shc[k] = a.sh[(long long)S * 3 * i + k];
+    fin = all_finite(mu, 3) && all_finite(sc, 3) && all_finite(q, 4) && isfinite(op) &&
+          all_finite(shc, S * 3);
+  }
+  if (valid && !fin) atomicAdd(&s_nonfinite, (uint32_t)a.V);
+
+  // phase 1: visibility per view (keyed path only) -> count of records
+  uint32_t cnt = 0;
+  if (valid && fin) {
+    for (int v = 0; v < a.V; ++v) {
+      const ViewDev &vd = a.views[v];
+      Keyed k;
+      cnt += keyed_project(mu, sc, q, a.cams[v], a.tile, vd.tx, vd.ty, k) ? 1u : 0u;
+    }
+  }
+  // block exclusive scan of cnt
+  const int lane = tid & 31, warp = tid >> 5;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  uint32_t woff = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kProjThreads / 32; ++w) {
+    uint32_t t = s_wsum[w];
+    if (w < warp) woff += t;
+    total += t;
+  }
+  if (tid == 0) {
+    unsigned long long excl = lookback_single(a.scan_slots, part, total, &a.hdr->status);
+    s_base = excl;
+    const uint32_t nparts = (uint32_t)((a.n + kProjThreads - 1) / kProjThreads);
+    if (part == nparts - 1) a.hdr->n_visible = excl + total;
+    if (s_nonfinite) atomicAdd(&a.hdr->n_nonfinite, (unsigned long long)s_nonfinite);
+  }
+  __syncthreads();
+  unsigned long long j = s_base + woff + (incl - cnt);
+  if (cnt == 0) return;
+
+  // phase 2: full projection of the visible views, written at j, j+1, ...
+  for (int v = 0; v < a.V; ++v) {
+    const gs_camera cam = a.cams[v];
+    const ViewDev &vd = a.views[v];
+    Keyed k;
+    if (!keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) continue;
+    if ((long long)j >= a.max_visible) {
+      set_status(&a.hdr->status, GS_ERR_CAPACITY);
+      return;
+    }
+    // --- compensated 2D mean ---
+    float xh, xl, yh, yl, zh, zl;
+    dot3_comp(&cam.R[0], mu, cam.t[0], xh, xl);
+    dot3_comp(&cam.R[3], mu, cam.t[1], yh, yl);
+    dot3_comp(&cam.R[6], mu, cam.t[2], zh, zl);
+    float uh, ul, vh, vl;
+    proj_comp(xh, xl, zh, zl, cam.fx, cam.cx, uh, ul);
+    proj_comp(yh, yl, zh, zl, cam.fy, cam.cy, vh, vl);
+    // --- 2D covariance from G = J W M, whitened (eigen form) ---
+    float G0[3], G1[3];
+    float T0[3], T1[3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      T0[kk] = fmaf(k.j02, cam.R[6 + kk], k.j00 * cam.R[kk]);
+      T1[kk] = fmaf(k.j12, cam.R[6 + kk], k.j11 * cam.R[3 + kk]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      G0[kk] = fmaf(T0[2], k.M[6 + kk], fmaf(T0[1], k.M[3 + kk], T0[0] * k.M[kk]));
+      G1[kk] = fmaf(T1[2], k.M[6 + kk], fmaf(T1[1], k.M[3 + kk], T1[0] * k.M[kk]));
+    }
+    float n0 = fmaf(G0[2], G0[2], fmaf(G0[1], G0[1], G0[0] * G0[0]));
+    float n1 = fmaf(G1[2], G1[2], fmaf(G1[1], G1[1], G1[0] * G1[0]));
+    float aa = n0 + kLowpass, cc = n1 + kLowpass;
+    float bb = fmaf(G0[2], G1[2], fmaf(G0[1], G1[1], G0[0] * G1[0]));
+    // det(G G^T + 0.3 I) = sum of squared 2x2 minors + 0.3 (|G0|^2 + |G1|^2) + 0.09
+    float det = kLowpass * kLowpass + kLowpass * (n0 + n1);
+#pragma unroll
+    for (int p0 = 0; p0 < 3; ++p0) {
+      int p1 = (p0 + 1) % 3;
+      float w = G0[p1] * G1[p0];
+      float e = fmaf(-G0[p1], G1[p0], w);
+      float f = fmaf(G0[p0], G1[p1], -w);
+      float m = f + e;
+      det = fmaf(m, m, det);
+    }
+    float hd = 0.5f * (aa - cc);
+    float hyp = sqrtf(fmaf(hd, hd, bb * bb));
+    float l1 = 0.5f * (aa + cc) + hyp;
+    float l2 = det / l1;
+    float e1x, e1y;
+    if (aa >= cc) { e1x = hd + hyp; e1y = bb; } else { e1x = bb; e1y = hyp - hd; }
+    float en = sqrtf(fmaf(e1x, e1x, e1y * e1y));
+    if (en > 0.0f) { e1x = e1x / en; e1y = e1y / en; } else { e1x = 1.0f; e1y = 0.0f; }
+    float s1 = kWhiten / sqrtf(l1), s2 = kWhiten / sqrtf(l2);
+    float4 shape = make_float4(e1x * s1, e1y * s1, -e1y * s2, e1x * s2);
+    // --- colour g(SH) at the view direction ---
+    float dx = mu[0] - vd.ccx, dy = mu[1] - vd.ccy, dz = mu[2] - vd.ccz;
+    float dn = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    float inv = dn > 0.0f ? 1.0f / dn : 0.0f;
+    float Y[16];
+    sh_basis(dx * inv, dy * inv, dz * inv, S, Y);
+    float rest[3], col[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int kk = 1; kk < S; ++kk) acc = fmaf(shc[3 * kk + ch], Y[kk], acc);
+      rest[ch] = acc;
+      col[ch] = fmaxf(0.0f, fmaf(shc[ch], Y[0], acc) + kShOffset);
+    }
+    // --- pairs kept by the foveation filter ---
+    uint32_t pairs;
+    uint8_t m = 0;
+    if (a.tile_level) {
+      m = a.bound_m[i];
+      pairs = 0;
+      const long long tb = vd.tile_base;
+      for (int y = k.y0; y <= k.y1; ++y)
+        for (int x = k.x0; x <= k.x1; ++x)
+          pairs += a.tile_level[tb + (long long)y * vd.tx + x] <= m ? 1u : 0u;
+    } else {
+      pairs = (uint32_t)((k.x1 - k.x0 + 1) * (k.y1 - k.y0 + 1));
+    }
+    a.rec_mean[j] = make_float4(uh, vh, ul, vl);
+    a.rec_shape[j] = shape;
+    a.rec_color[j] = make_float4(col[0], col[1], col[2], log2f(op));
+    if (a.rec_rest) {
+      a.rec_rest[j] = make_float4(rest[0], rest[1], rest[2], 0.0f);
+      a.rec_m[j] = m;
+    }
+    a.rec_depth[j] = __float_as_uint(k.pz);
+    a.rec_count[j] = pairs;
+    a.rec_rect[j] = make_uint2((uint32_t)k.x0 | ((uint32_t)k.x1 << 16),
+                               (uint32_t)k.y0 | ((uint32_t)k.y1 << 16));
+    a.rec_gid[j] = (uint32_t)i;
+    a.rec_view[j] = (uint32_t)v;
+    ++j;
+  }
+}
+
+cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
+  if (p->n == 0) return cudaSuccess;
+  ProjArgs a;
+  a.n = p->n;
+  a.V = p->V;
+  a.S = (p->sh_degree + 1) * (p->sh_degree + 1);
+  a.tile = p->tile;
+  a.means = p->scene.means;
+  a.scales = p->scene.scales;
+  a.quats = p->scene.quats;
+  a.opac = p->scene.opacities;
+  a.sh = p->scene.sh;
+  a.cams = p->cams;
+  a.views = region<ViewDev>(p, ws, R_VIEWS);
+  a.tile_level = p->has_fov ? region<uint8_t>(p, ws, R_TILE_LEVEL) : nullptr;
+  a.bound_m = p->has_fov ? p->fov.bound_m : nullptr;
+  a.hdr = region<Hdr>(p, ws, R_HDR);
+  a.scan_slots = region<unsigned long long>(p, ws, R_SCAN);
+  a.max_visible = p->max_visible;
+  a.rec_mean = region<float4>(p, ws, R_REC_MEAN);
+  a.rec_shape = region<float4>(p, ws, R_REC_SHAPE);
+  a.rec_color = region<float4>(p, ws, R_REC_COLOR);
+  a.rec_rest = p->bytes[R_REC_REST] ? region<float4>(p, ws, R_REC_REST) : nullptr;
+  a.rec_depth = region<uint32_t>(p, ws, R_REC_DEPTH);
+  a.rec_count = region<uint32_t>(p, ws, R_REC_COUNT);
+  a.rec_gid = region<uint32_t>(p, ws, R_REC_GID);
+  a.rec_view = region<uint32_t>(p, ws, R_REC_VIEW);
+  a.rec_rect = region<uint2>(p, ws, R_REC_RECT);
+  a.rec_m = p->bytes[R_REC_M] ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
+  unsigned grid = (unsigned)((p->n + kProjThreads - 1) / kProjThreads);
+  switch (a.S) {
+    case 1: k_project<1><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 4: k_project<4><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 9: k_project<9><<<grid, kProjThreads, 0, s>>>(a); break;
+    default: k_project<16><<<grid, kProjThreads, 0, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gs

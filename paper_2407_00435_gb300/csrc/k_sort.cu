@@ -1,0 +1,475 @@
+// k_sort.cu -- Sorting stage (Sec. 2.1 "Sorting": per tile, the intersecting
+// ellipses ordered by depth, closest first).
+//
+// The per-tile depth order is produced by two stable LSD radix sorts:
+//   1. the visible (view, point) items by the FP32 bits of camera depth
+//      (ties keep item order, i.e. point index inside a view);
+//   2. the (tile, item) pairs, emitted in that depth order, by tile id.
+// Together they order the pairs by (tile, depth, point index), the same
+// order as one stable sort of (tile << 32 | depth) keys.
+//
+// Each radix pass is a single "onesweep" kernel: persistent blocks take
+// 4096-key partitions by atomic ticket, rank digits inside each warp with
+// __match_any_sync, publish per-digit partition counts and look back over
+// their predecessors (decoupled look-back, bounded spin) to get global
+// positions, then scatter.  A pass whose digit is the same for all keys is
+// skipped on the device.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs_internal.cuh"
+#include "lookback.cuh"
+
+namespace gs {
+
+struct SortArgs {
+  const uint32_t *first_keys;        // input keys (read by the first executed pass)
+  const uint32_t *first_vals;        // input values, or null: values = key index
+  uint32_t *keys[2];                 // ping-pong buffers
+  uint32_t *vals[2];
+  const unsigned long long *count;   // device-side number of keys
+  long long capacity;                // keys beyond are ignored
+  uint32_t *sel;                     // out: buffer index holding the result
+  uint32_t *hist;                    // [4][256] digit histograms -> offsets
+  uint32_t *skip;                    // [4] pass skipped (constant digit)
+  uint32_t *tickets;                 // [4] partition tickets
+  unsigned long long *lb;            // [2][max_parts][256] look-back slots
+  long long max_parts;
+  int passes;
+  uint32_t *status;
+};
+
+__device__ __forceinline__ uint32_t sort_n(const SortArgs &a) {
+  unsigned long long n = *a.count;
+  if ((long long)n > a.capacity) n = (unsigned long long)a.capacity;
+  return (uint32_t)n;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---- histograms of every pass in one read; also resets tickets and the
+// first look-back buffer -------------------------------------------------
+__global__ void __launch_bounds__(256) k_hist(SortArgs a) {
+  __shared__ uint32_t sh[4][256];
+  const uint32_t n = sort_n(a);
+  for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // warp-uniform trip count so that __match_any_sync sees the full warp
+  const long long start = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long iters = ((long long)n + stride - 1) / stride;
+  for (long long it = 0; it < iters; ++it) {
+    long long idx = start + it * stride;
+    bool valid = idx < (long long)n;
+    uint32_t key = valid ? a.first_keys[idx] : 0u;
+    for (int p = 0; p < a.passes; ++p) {
+      uint32_t d = (key >> (8 * p)) & 255u;
+      uint32_t tag = valid ? d : 0x100u;
+      uint32_t peers = __match_any_sync(0xffffffffu, tag);
+      if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.passes * 256; q += blockDim.x) {
+    uint32_t c = (&sh[0][0])[q];
+    if (c) atomicAdd(&a.hist[q], c);
+  }
+  // reset look-back buffer 0 for the partitions this sort will use
+  const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
+  for (long long q = start; q < nparts * 256; q += stride) a.lb[q] = 0ull;
+  if (blockIdx.x == 0 && threadIdx.x < 4) a.tickets[threadIdx.x] = 0u;
+}
+
+// exclusive scan of each pass's histogram; constant-digit passes skipped
+__global__ void __launch_bounds__(256) k_hist_scan(SortArgs a) {
+  __shared__ uint32_t s_w[8];
+  const uint32_t n = sort_n(a);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int executed = 0;
+  // an index-generating sort must run at least one pass to write its values
+  const bool force_first = a.first_vals == nullptr;
+  for (int p = 0; p < a.passes; ++p) {
+    uint32_t c = a.hist[p * 256 + t];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int q = 0; q < w; ++q) woff += s_w[q];
+    a.hist[p * 256 + t] = woff + incl - c;
+    int constant = __syncthreads_or(c == n);
+    bool sk = (constant || n == 0) && !(force_first && executed == 0 && p == a.passes - 1);
+    if (t == 0) a.skip[p] = sk ? 1u : 0u;
+    executed += sk ? 0 : 1;
+    __syncthreads();
+  }
+  if (t == 0) *a.sel = (uint32_t)(executed & 1);
+}
+
+// ---- one onesweep pass -----------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass) {
+  __shared__ uint32_t s_wh[kSortThreads / 32][256];
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_part;
+  const uint32_t n = sort_n(a);
+  const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
+  unsigned long long *lb_next = a.lb + (long long)((pass + 1) & 1) * a.max_parts * 256;
+  if (a.skip[pass]) {
+    // keep the next pass's look-back buffer clean even though this one idles
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nparts * 256;
+         q += stride)
+      lb_next[q] = 0ull;
+    return;
+  }
+  unsigned long long *lb_cur = a.lb + (long long)(pass & 1) * a.max_parts * 256;
+  int before = 0;
+  for (int p = 0; p < pass; ++p) before += a.skip[p] ? 0 : 1;
+  const uint32_t *kin = before == 0 ? a.first_keys : a.keys[before & 1];
+  const uint32_t *vin = before == 0 ? a.first_vals : a.vals[before & 1];
+  uint32_t *kout = a.keys[(before + 1) & 1];
+  uint32_t *vout = a.vals[(before + 1) & 1];
+  const bool iota = vin == nullptr;
+  const int shift = 8 * pass;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t ltmask = lanemask_lt();
+  const uint32_t *goff = a.hist + pass * 256;
+
+  for (;;) {
+    if (tid == 0) s_part = atomicAdd(&a.tickets[pass], 1u);
+    for (int q = tid; q < (kSortThreads / 32) * 256; q += kSortThreads) (&s_wh[0][0])[q] = 0u;
+    __syncthreads();
+    const uint32_t part = s_part;
+    if ((long long)part >= nparts) break;
+    const long long wbase = (long long)part * kSortPart + warp * (32 * kSortItems);
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      long long idx = wbase + k * 32 + lane;
+      bool valid = idx < (long long)n;
+      key[k] = valid ? kin[idx] : 0u;
+      val[k] = valid ? (iota ? (uint32_t)idx : vin[idx]) : 0u;
+    }
+    // warp-level stable ranking (original order = (k, lane))
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      long long idx = wbase + k * 32 + lane;
+      bool valid = idx < (long long)n;
+      uint32_t d = (key[k] >> shift) & 255u;
+      uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+      uint32_t before_w = valid ? s_wh[warp][d] : 0u;
+      rank[k] = before_w + __popc(peers & ltmask);
+      __syncwarp();
+      if (valid && (__ffs(peers) - 1) == lane) s_wh[warp][d] = before_w + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: warp offsets inside the partition, then look-back
+    {
+      const int d = tid;  // kSortThreads == 256 digits
+      uint32_t tot = 0;
+#pragma unroll
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        uint32_t c = s_wh[w][d];
+        s_wh[w][d] = tot;
+        tot += c;
+      }
+      unsigned long long *slot = lb_cur + (long long)part * 256 + d;
+      unsigned long long excl = 0;
+      if (part == 0) {
+        st_release_u64(slot, kFlagPre | tot);
+      } else {
+        st_release_u64(slot, kFlagAgg | tot);
+        long long q = (long long)part - 1;
+        int spins = 0;
+        while (q >= 0) {
+          unsigned long long wv = ld_acquire_u64(lb_cur + q * 256 + d);
+          unsigned long long f = wv >> 62;
+          if (f == 2ull) { excl += wv & kValMask; break; }
+          if (f == 1ull) { excl += wv & kValMask; --q; continue; }
+          if (++spins > kSpinLimit) { set_status(a.status, GS_ERR_TIMEOUT); break; }
+          __nanosleep(20);
+        }
+        st_release_u64(slot, kFlagPre | (excl + tot));
+      }
+      s_base[d] = goff[d] + (uint32_t)excl;
+      lb_next[(long long)part * 256 + d] = 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      long long idx = wbase + k * 32 + lane;
+      if (idx < (long long)n) {
+        uint32_t d = (key[k] >> shift) & 255u;
+        uint32_t dst = s_base[d] + s_wh[warp][d] + rank[k];
+        if (dst < n) {
+          kout[dst] = key[k];
+          vout[dst] = val[k];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static int g_sort_blocks = 0;
+
+static cudaError_t run_sort(const SortArgs &a, cudaStream_t s) {
+  if (g_sort_blocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onesweep, kSortThreads, 0);
+    g_sort_blocks = sms * (per > 0 ? per : 1);
+  }
+  k_hist<<<g_sort_blocks, 256, 0, s>>>(a);
+  k_hist_scan<<<1, 256, 0, s>>>(a);
+  for (int p = 0; p < a.passes; ++p) k_onesweep<<<g_sort_blocks, kSortThreads, 0, s>>>(a, p);
+  return cudaGetLastError();
+}
+
+// ---- exclusive scan of pair counts in depth order -> emit offsets --------
+struct ScanArgs {
+  const uint32_t *sorted_items[2];
+  const uint32_t *sel;
+  const uint32_t *count;            // rec_count (by item)
+  const unsigned long long *n_items;
+  long long capacity;
+  uint32_t *offsets;
+  unsigned long long *slots;
+  uint32_t *ticket;
+  unsigned long long *n_pairs;
+  uint32_t *status;
+};
+
+__global__ void __launch_bounds__(256) k_offsets(ScanArgs a) {
+  __shared__ uint32_t s_part;
+  __shared__ unsigned long long s_w[8];
+  __shared__ unsigned long long s_base;
+  unsigned long long nn = *a.n_items;
+  const uint32_t n = (uint32_t)((long long)nn > a.capacity ? a.capacity : (long long)nn);
+  const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
+  const uint32_t *items = a.sorted_items[*a.sel];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_part = atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const uint32_t part = s_part;
+    if ((long long)part >= nparts) break;
+    const long long base = (long long)part * kSortPart + (long long)tid * 16;
+    unsigned long long c[16];
+    unsigned long long tsum = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      long long idx = base + k;
+      c[k] = idx < (long long)n ? a.count[items[idx]] : 0ull;
+      tsum += c[k];
+    }
+    unsigned long long incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    unsigned long long woff = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      if (w < warp) woff += s_w[w];
+      total += s_w[w];
+    }
+    if (tid == 0) {
+      unsigned long long ex = lookback_single(a.slots, part, total, a.status);
+      s_base = ex;
+      if ((long long)part == nparts - 1) *a.n_pairs = ex + total;
+    }
+    __syncthreads();
+    unsigned long long run = s_base + woff + incl - tsum;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      long long idx = base + k;
+      if (idx < (long long)n) a.offsets[idx] = (uint32_t)(run > 0xffffffffull ? 0xffffffffull : run);
+      run += c[k];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- emit (tile, item) pairs in depth order ------------------------------
+struct EmitArgs {
+  const uint32_t *sorted_items[2];
+  const uint32_t *sel;
+  const unsigned long long *n_items;
+  long long item_capacity;
+  const uint32_t *offsets;
+  const uint32_t *count;
+  const uint2 *rect;
+  const uint32_t *view;
+  const ViewDev *views;
+  const uint8_t *tile_level;
+  const uint8_t *rec_m;
+  const unsigned long long *n_pairs;
+  long long pair_capacity;
+  uint32_t *pkey, *pval;
+  uint32_t *status;
+};
+
+__global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
+  unsigned long long nn = *a.n_items;
+  const long long n = (long long)nn > a.item_capacity ? a.item_capacity : (long long)nn;
+  const uint32_t *items = a.sorted_items[*a.sel];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (long long)*a.n_pairs > a.pair_capacity)
+    set_status(a.status, GS_ERR_CAPACITY);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const uint32_t j = items[k];
+    long long off = a.offsets[k];
+    const uint2 r = a.rect[j];
+    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+    const ViewDev &vd = a.views[a.view[j]];
+    const long long tb = vd.tile_base;
+    const uint8_t m = a.tile_level ? a.rec_m[j] : 0;
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) {
+        const long long t = tb + (long long)y * vd.tx + x;
+        if (a.tile_level && a.tile_level[t] > m) continue;
+        if (off < a.pair_capacity) {
+          a.pkey[off] = (uint32_t)t;
+          a.pval[off] = j;
+        }
+        ++off;
+      }
+  }
+}
+
+// ---- per-tile ranges ------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t *key_a, const uint32_t *key_b,
+                                                const uint32_t *sel,
+                                                const unsigned long long *n_pairs,
+                                                long long capacity, uint2 *ranges) {
+  unsigned long long nn = *n_pairs;
+  const long long n = (long long)nn > capacity ? capacity : (long long)nn;
+  const uint32_t *key = *sel ? key_b : key_a;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const uint32_t t = key[p];
+    if (p == 0 || key[p - 1] != t) ranges[t].x = (uint32_t)p;
+    if (p == n - 1 || key[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+  }
+}
+
+cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
+  Hdr *hdr = region<Hdr>(p, ws, R_HDR);
+  cudaError_t e;
+  // histograms and tickets of this stage start from zero (ticket 0 belongs
+  // to the projection)
+  e = cudaMemsetAsync(&hdr->hist[0][0][0], 0, sizeof(hdr->hist), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&hdr->ticket[1], 0, sizeof(hdr->ticket) - sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const long long proj_parts = (p->n + kProjThreads - 1) / kProjThreads;
+  const long long off_parts = (p->max_visible + kSortPart - 1) / kSortPart;
+  e = cudaMemsetAsync(region<unsigned long long>(p, ws, R_SCAN) + proj_parts, 0,
+                      sizeof(unsigned long long) * (size_t)off_parts, s);
+  if (e != cudaSuccess) return e;
+  if (p->n == 0) {
+    // nothing visible: empty ranges
+    e = cudaMemsetAsync(region<uint2>(p, ws, R_RANGES), 0, p->bytes[R_RANGES], s);
+    return e;
+  }
+  const long long max_parts =
+      ((p->max_visible > p->max_pairs ? p->max_visible : p->max_pairs) + kSortPart - 1) / kSortPart;
+  // 1. depth sort of the visible items
+  SortArgs d = {};
+  d.first_keys = region<uint32_t>(p, ws, R_REC_DEPTH);
+  d.first_vals = nullptr;
+  d.keys[0] = region<uint32_t>(p, ws, R_DKEY_A);
+  d.keys[1] = region<uint32_t>(p, ws, R_DKEY_B);
+  d.vals[0] = region<uint32_t>(p, ws, R_DVAL_A);
+  d.vals[1] = region<uint32_t>(p, ws, R_DVAL_B);
+  d.count = &hdr->n_visible;
+  d.capacity = p->max_visible;
+  d.sel = &hdr->sel_depth;
+  d.hist = &hdr->hist[0][0][0];
+  d.skip = &hdr->skip[0];
+  d.tickets = &hdr->ticket[1];
+  d.lb = region<unsigned long long>(p, ws, R_LOOKBACK);
+  d.max_parts = max_parts;
+  d.passes = 4;
+  d.status = &hdr->status;
+  e = run_sort(d, s);
+  if (e != cudaSuccess) return e;
+  // 2. pair offsets in depth order
+  ScanArgs sa = {};
+  sa.sorted_items[0] = d.vals[0];
+  sa.sorted_items[1] = d.vals[1];
+  sa.sel = &hdr->sel_depth;
+  sa.count = region<uint32_t>(p, ws, R_REC_COUNT);
+  sa.n_items = &hdr->n_visible;
+  sa.capacity = p->max_visible;
+  sa.offsets = region<uint32_t>(p, ws, R_OFFSETS);
+  sa.slots = region<unsigned long long>(p, ws, R_SCAN) + proj_parts;
+  sa.ticket = &hdr->ticket[9];
+  sa.n_pairs = &hdr->n_pairs;
+  sa.status = &hdr->status;
+  k_offsets<<<g_sort_blocks, 256, 0, s>>>(sa);
+  // 3. emit pairs
+  EmitArgs ea = {};
+  ea.sorted_items[0] = d.vals[0];
+  ea.sorted_items[1] = d.vals[1];
+  ea.sel = &hdr->sel_depth;
+  ea.n_items = &hdr->n_visible;
+  ea.item_capacity = p->max_visible;
+  ea.offsets = sa.offsets;
+  ea.count = sa.count;
+  ea.rect = region<uint2>(p, ws, R_REC_RECT);
+  ea.view = region<uint32_t>(p, ws, R_REC_VIEW);
+  ea.views = region<ViewDev>(p, ws, R_VIEWS);
+  ea.tile_level = p->has_fov ? region<uint8_t>(p, ws, R_TILE_LEVEL) : nullptr;
+  ea.rec_m = p->has_fov ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
+  ea.n_pairs = &hdr->n_pairs;
+  ea.pair_capacity = p->max_pairs;
+  ea.pkey = region<uint32_t>(p, ws, R_PKEY_A);
+  ea.pval = region<uint32_t>(p, ws, R_PVAL_A);
+  ea.status = &hdr->status;
+  k_emit<<<g_sort_blocks, 256, 0, s>>>(ea);
+  // 4. stable sort of the pairs by tile
+  SortArgs t = {};
+  t.first_keys = ea.pkey;
+  t.first_vals = ea.pval;
+  t.keys[0] = ea.pkey;
+  t.keys[1] = region<uint32_t>(p, ws, R_PKEY_B);
+  t.vals[0] = ea.pval;
+  t.vals[1] = region<uint32_t>(p, ws, R_PVAL_B);
+  t.count = &hdr->n_pairs;
+  t.capacity = p->max_pairs;
+  t.sel = &hdr->sel_pair;
+  t.hist = &hdr->hist[1][0][0];
+  t.skip = &hdr->skip[4];
+  t.tickets = &hdr->ticket[5];
+  t.lb = d.lb;
+  t.max_parts = max_parts;
+  t.passes = (p->tile_bits + 7) / 8;
+  t.status = &hdr->status;
+  e = run_sort(t, s);
+  if (e != cudaSuccess) return e;
+  // 5. ranges (the pointer pair lives in the header's spare words)
+  uint2 *ranges = region<uint2>(p, ws, R_RANGES);
+  e = cudaMemsetAsync(ranges, 0, p->bytes[R_RANGES], s);
+  if (e != cudaSuccess) return e;
+  k_ranges<<<g_sort_blocks, 256, 0, s>>>(t.keys[0], t.keys[1], &hdr->sel_pair, &hdr->n_pairs,
+                                         p->max_pairs, ranges);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,354 @@
+"""Thin ctypes binding of ``libgs.so`` (the C ABI in ``include/gs.h``).
+
+Argument marshalling only: every stage runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  There is no CPU fallback: if
+the library is missing or fails to load, importing the binding raises.
+
+Function names follow the C ABI (``gs_project``, ``gs_bin_sort``,
+``gs_render``, ``gs_render_fov``, ``gs_render_backward``, ...).  The
+:class:`Renderer` class owns a plan and a workspace and is what the tests,
+the benchmark and the autograd wrapper use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_UNSUPPORTED = range(6)
+GS_FLAG_FOVEATED = 1
+GS_FLAG_BACKWARD = 2
+GS_MAX_LEVELS = 8
+(GS_REGION_ITEM_GID, GS_REGION_ITEM_VIEW, GS_REGION_ITEM_DEPTH, GS_REGION_ITEM_COUNT) = (1, 2, 3, 4)
+GS_REGION_RANGES, GS_REGION_TILE_LEVEL = 7, 8
+
+_STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY",
+                 3: "GS_ERR_TIMEOUT", 4: "GS_ERR_CUDA", 5: "GS_ERR_UNSUPPORTED"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {_STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float),
+                ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("znear", C.c_float),
+                ("zfar", C.c_float)]
+
+
+class gs_scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("reserved", C.c_int32),
+                ("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacities", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class gs_fov(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("band_px", C.c_float),
+                ("ring_tan", C.c_float * (GS_MAX_LEVELS - 1)), ("bound_m", C.c_void_p),
+                ("gaze_px", C.c_void_p), ("view_fov", C.c_void_p), ("opacity_lv", C.c_void_p),
+                ("dc_lv", C.c_void_p)]
+
+
+class gs_config(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("chunk", C.c_int32), ("flags", C.c_int32),
+                ("max_levels", C.c_int32), ("max_visible", C.c_int64), ("max_pairs", C.c_int64)]
+
+
+class gs_counters(C.Structure):
+    _fields_ = [("status", C.c_uint32), ("reserved", C.c_uint32), ("n_visible", C.c_uint64),
+                ("n_pairs", C.c_uint64), ("n_nonfinite", C.c_uint64),
+                ("n_evals", C.c_uint64), ("n_blends", C.c_uint64)]
+
+
+assert C.sizeof(gs_camera) == 80
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        path = _build.build()
+    lib = C.CDLL(path)
+    p, s = C.c_void_p, C.c_int32
+    lib.gs_plan_size.restype = C.c_size_t
+    lib.gs_plan_init.argtypes = [p, C.c_int64, s, p, s, p]
+    lib.gs_plan_init.restype = s
+    lib.gs_workspace_size.argtypes = [p]
+    lib.gs_workspace_size.restype = C.c_size_t
+    lib.gs_project.argtypes = [p, p, C.c_size_t, p, p, p, p]
+    lib.gs_project.restype = s
+    lib.gs_bin_sort.argtypes = [p, p, p]
+    lib.gs_bin_sort.restype = s
+    lib.gs_render.argtypes = [p, p, p, p, p, p, p, p]
+    lib.gs_render.restype = s
+    lib.gs_render_fov.argtypes = [p, p, p, p, p, p, p, p]
+    lib.gs_render_fov.restype = s
+    lib.gs_render_backward.argtypes = [p, p, p, p, p, p, p, p, p, p, p, p, p, p]
+    lib.gs_render_backward.restype = s
+    lib.gs_get_error.argtypes = [p, p, p, p]
+    lib.gs_get_error.restype = s
+    lib.gs_clear_error.argtypes = [p, p, p]
+    lib.gs_clear_error.restype = s
+    lib.gs_ws_region.argtypes = [p, s, p, p]
+    lib.gs_ws_region.restype = s
+    lib.gs_sorted_pairs.argtypes = [p, p, p, p, p]
+    lib.gs_sorted_pairs.restype = s
+    lib.gs_plan_tiles.argtypes = [p]
+    lib.gs_plan_tiles.restype = C.c_int64
+    lib.gs_plan_pixels.argtypes = [p]
+    lib.gs_plan_pixels.restype = C.c_int64
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(code, what):
+    if code != GS_OK:
+        raise GsError(code, what)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def cams_host(cams: np.ndarray):
+    """(V, 20) float32 packed cameras -> ctypes array of gs_camera."""
+    cams = np.asarray(cams, np.float32).reshape(-1, 20)
+    arr = (gs_camera * len(cams))()
+    for v, row in enumerate(cams):
+        c = arr[v]
+        for k in range(9):
+            c.R[k] = float(row[k])
+        for k in range(3):
+            c.t[k] = float(row[9 + k])
+        c.fx, c.fy, c.cx, c.cy = (float(x) for x in row[12:16])
+        c.width, c.height = int(row[16]), int(row[17])
+        c.znear, c.zfar = float(row[18]), float(row[19])
+    return arr
+
+
+def cams_device(cams: np.ndarray, device="cuda") -> torch.Tensor:
+    """(V, 20) float32 packed cameras -> device bytes laid out as gs_camera[V]."""
+    h = cams_host(cams)
+    raw = np.frombuffer(bytes(h), np.uint8).copy()
+    return torch.from_numpy(raw).to(device)
+
+
+# --------------------------------------------------------------------------
+# C-ABI wrappers with the library's names
+# --------------------------------------------------------------------------
+def gs_plan_init(plan_buf, n, sh_degree, cams_h, n_views, cfg):
+    _check(_lib.gs_plan_init(plan_buf, n, sh_degree, cams_h, n_views, C.byref(cfg)),
+           "gs_plan_init")
+
+
+def gs_project(plan_buf, ws, scene, cams_d, fov, stream=None):
+    _check(_lib.gs_project(plan_buf, _ptr(ws), ws.numel() * ws.element_size(), C.byref(scene),
+                           _ptr(cams_d), C.byref(fov) if fov is not None else None,
+                           _stream(stream)), "gs_project")
+
+
+def gs_bin_sort(plan_buf, ws, stream=None):
+    _check(_lib.gs_bin_sort(plan_buf, _ptr(ws), _stream(stream)), "gs_bin_sort")
+
+
+def gs_render(plan_buf, ws, bg, rgb, T, last, stats=None, stream=None):
+    bgv = (C.c_float * 3)(*[float(x) for x in bg])
+    _check(_lib.gs_render(plan_buf, _ptr(ws), bgv, _ptr(rgb), _ptr(T), _ptr(last), _ptr(stats),
+                          _stream(stream)), "gs_render")
+
+
+def gs_render_fov(plan_buf, ws, bg, rgb, T, last, stats=None, stream=None):
+    bgv = (C.c_float * 3)(*[float(x) for x in bg])
+    _check(_lib.gs_render_fov(plan_buf, _ptr(ws), bgv, _ptr(rgb), _ptr(T), _ptr(last),
+                              _ptr(stats), _stream(stream)), "gs_render_fov")
+
+
+def gs_render_backward(plan_buf, ws, dL, T, last, bg, d_means, d_scales, d_quats, d_opac, d_sh,
+                       d_opac_lv=None, d_dc_lv=None, stream=None):
+    bgv = (C.c_float * 3)(*[float(x) for x in bg])
+    _check(_lib.gs_render_backward(plan_buf, _ptr(ws), _ptr(dL), _ptr(T), _ptr(last), bgv,
+                                   _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opac),
+                                   _ptr(d_sh), _ptr(d_opac_lv), _ptr(d_dc_lv), _stream(stream)),
+           "gs_render_backward")
+
+
+def gs_get_error(plan_buf, ws, stream=None):
+    c = gs_counters()
+    code = _lib.gs_get_error(plan_buf, _ptr(ws), _stream(stream), C.byref(c))
+    return code, c
+
+
+# --------------------------------------------------------------------------
+# Renderer: plan + workspace + outputs
+# --------------------------------------------------------------------------
+class Renderer:
+    """One plan (scene size, views, options) and its device workspace.
+
+    ``scene_t``: dict of device tensors means/scales/quats/opac/sh;
+    ``cams``: (V, 20) packed float32 cameras (numpy).
+    """
+
+    def __init__(self, n, sh_degree, cams, tile=16, foveated=False, backward=False,
+                 max_pairs=0, max_visible=0, max_levels=0, chunk=0, device="cuda"):
+        self.n, self.sh_degree = int(n), int(sh_degree)
+        self.cams_np = np.asarray(cams, np.float32).reshape(-1, 20)
+        self.V = len(self.cams_np)
+        self.device = device
+        self.cfg = gs_config(tile, chunk, (GS_FLAG_FOVEATED if foveated else 0)
+                             | (GS_FLAG_BACKWARD if backward else 0), max_levels,
+                             max_visible, max_pairs)
+        self.plan = C.create_string_buffer(int(_lib.gs_plan_size()))
+        self._cams_h = cams_host(self.cams_np)
+        gs_plan_init(self.plan, self.n, self.sh_degree, self._cams_h, self.V, self.cfg)
+        self.ws_bytes = int(_lib.gs_workspace_size(self.plan))
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.cams_d = cams_device(self.cams_np, device)
+        self.P = int(_lib.gs_plan_pixels(self.plan))
+        self.T_tiles = int(_lib.gs_plan_tiles(self.plan))
+        self.tile = tile
+        self._keep = None
+
+    # -- stages ------------------------------------------------------------
+    def set_cameras(self, cams):
+        cams = np.asarray(cams, np.float32).reshape(-1, 20)
+        assert cams.shape == self.cams_np.shape
+        self.cams_np = cams
+        self.cams_d.copy_(cams_device(cams, self.device))
+
+    def project(self, sc: dict, fov: dict | None = None, stream=None):
+        scene = gs_scene(self.n, self.sh_degree, 0, sc["means"].data_ptr(),
+                         sc["scales"].data_ptr(), sc["quats"].data_ptr(), sc["opac"].data_ptr(),
+                         sc["sh"].data_ptr())
+        f = None
+        if fov is not None:
+            f = gs_fov()
+            f.n_levels = int(fov["n_levels"])
+            f.band_px = float(fov["band_px"])
+            for k, v in enumerate(np.asarray(fov["ring_tan"], np.float32)):
+                f.ring_tan[k] = float(v)
+            f.bound_m = fov["bound_m"].data_ptr()
+            f.gaze_px = fov["gaze"].data_ptr()
+            f.view_fov = fov["view_fov"].data_ptr() if fov.get("view_fov") is not None else None
+            f.opacity_lv = fov["opacity_lv"].data_ptr() if fov.get("opacity_lv") is not None else None
+            f.dc_lv = fov["dc_lv"].data_ptr() if fov.get("dc_lv") is not None else None
+        self._keep = (sc, fov)   # the plan records these pointers
+        gs_project(self.plan, self.ws, scene, self.cams_d, f, stream)
+
+    def bin_sort(self, stream=None):
+        gs_bin_sort(self.plan, self.ws, stream)
+
+    def _replan(self, max_pairs):
+        self.cfg.max_pairs = int(max_pairs)
+        gs_plan_init(self.plan, self.n, self.sh_degree, self._cams_h, self.V, self.cfg)
+        self.ws_bytes = int(_lib.gs_workspace_size(self.plan))
+        self.ws = None
+        torch.cuda.empty_cache()
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+
+    def fit(self, sc: dict, fov: dict | None = None, headroom=1.15, stream=None):
+        """project + bin_sort; if the pairs overflow the plan's capacity,
+        re-plan with room for K * headroom pairs and run both again.  Returns
+        the counters (synchronises)."""
+        for _ in range(2):
+            self.project(sc, fov, stream)
+            self.bin_sort(stream)
+            code, c = self.counters(stream)
+            if code != GS_ERR_CAPACITY:
+                break
+            self._replan(int(c["n_pairs"] * headroom) + 1024)
+        if code != GS_OK:
+            raise GsError(code, "fit")
+        return c
+
+    def alloc_outputs(self, fov=False, stats=False):
+        P = self.P
+        k = 2 if fov else 1
+        out = {"rgb": torch.empty(P, 3, device=self.device),
+               "T": torch.empty(P * k, device=self.device),
+               "last": torch.empty(P * k, dtype=torch.int32, device=self.device)}
+        if stats:
+            out["stats"] = torch.empty(4, self.n, dtype=torch.int32, device=self.device)
+        return out
+
+    def render(self, out, bg=(0, 0, 0), fov=False, stream=None):
+        fn = gs_render_fov if fov else gs_render
+        fn(self.plan, self.ws, bg, out["rgb"], out["T"], out["last"], out.get("stats"), stream)
+
+    def backward(self, dL, out, grads, bg=(0, 0, 0), stream=None):
+        gs_render_backward(self.plan, self.ws, dL, out["T"], out["last"], bg, grads["means"],
+                           grads["scales"], grads["quats"], grads["opac"], grads["sh"],
+                           grads.get("opac_lv"), grads.get("dc_lv"), stream)
+
+    def launches_per_frame(self, fov=False, stats=False):
+        """Kernels of this library launched by project + bin_sort + render."""
+        tile_bits = max(1, int(self.T_tiles - 1).bit_length())
+        project = 1 + (1 if fov else 0) + (1 if self.n > 0 else 0)
+        sort = 0 if self.n == 0 else (2 + 4) + 2 + (2 + (tile_bits + 7) // 8) + 1
+        render = 1 + (1 if stats and self.n > 0 else 0)
+        return project + sort + render
+
+    def counters(self, stream=None):
+        code, c = gs_get_error(self.plan, self.ws, stream)
+        return code, {"status": c.status, "n_visible": c.n_visible, "n_pairs": c.n_pairs,
+                      "n_nonfinite": c.n_nonfinite, "n_evals": c.n_evals,
+                      "n_blends": c.n_blends}
+
+    def clear_error(self, stream=None):
+        _check(_lib.gs_clear_error(self.plan, _ptr(self.ws), _stream(stream)), "gs_clear_error")
+
+    # -- debug views of the workspace ----------------------------------------
+    def region(self, rid, dtype, count):
+        off, nb = C.c_size_t(), C.c_size_t()
+        _check(_lib.gs_ws_region(self.plan, rid, C.byref(off), C.byref(nb)), "gs_ws_region")
+        esz = torch.empty(0, dtype=dtype).element_size()
+        return self.ws[off.value: off.value + count * esz].view(dtype)
+
+    def sorted_pairs(self, K, stream=None):
+        pt, pi = C.c_void_p(), C.c_void_p()
+        _check(_lib.gs_sorted_pairs(self.plan, _ptr(self.ws), _stream(stream), C.byref(pt),
+                                    C.byref(pi)), "gs_sorted_pairs")
+        base = self.ws.data_ptr()
+        ot, oi = pt.value - base, pi.value - base
+        return (self.ws[ot: ot + 4 * K].view(torch.int32), self.ws[oi: oi + 4 * K].view(torch.int32))
+
+
+def scene_to_device(scene, device="cuda") -> dict:
+    """numpy Scene (synth.Scene) -> dict of contiguous device tensors."""
+    return {"means": torch.from_numpy(np.ascontiguousarray(scene.means, np.float32)).to(device),
+            "scales": torch.from_numpy(np.ascontiguousarray(scene.scales, np.float32)).to(device),
+            "quats": torch.from_numpy(np.ascontiguousarray(scene.quats, np.float32)).to(device),
+            "opac": torch.from_numpy(np.ascontiguousarray(scene.opac, np.float32)).to(device),
+            "sh": torch.from_numpy(np.ascontiguousarray(scene.sh, np.float32)).to(device)}
+
+
+def fov_to_device(f, device="cuda", opacity_lv=None, dc_lv=None) -> dict | None:
+    if f is None:
+        return None
+    op = f.opacity_lv if opacity_lv is None else opacity_lv
+    dc = f.dc_lv if dc_lv is None else dc_lv
+    t = lambda a, dt: None if a is None else torch.from_numpy(np.ascontiguousarray(a, dt)).to(device)  # noqa: E731
+    return {"n_levels": int(f.n_levels), "band_px": float(f.band_px),
+            "ring_tan": np.asarray(f.ring_tan, np.float32), "bound_m": t(f.bound_m, np.uint8),
+            "gaze": t(f.gaze, np.float32), "view_fov": t(f.view_fov, np.uint8),
+            "opacity_lv": t(op, np.float32), "dc_lv": t(dc, np.float32)}

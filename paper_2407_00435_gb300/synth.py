@@ -177,10 +177,11 @@ def _random_rotations(rng, k):
 # Blob mixture calibration: blob axis standard deviations are log-uniform in
 # [BLOB_STD_LO, BLOB_STD_HI] and blob k gets weight (k + 1)^-BLOB_ZIPF.  The
 # values were chosen so that the 1920x1080, 1M-point workload has a heavy
-# tailed per-tile count (maximum near 5k per 16x16 tile, see DESIGN notes).
-BLOB_STD_LO = 0.02
-BLOB_STD_HI = 0.35
-BLOB_ZIPF = 1.1
+# tailed per-tile count: 16x16-tile counts p10 ~220, median ~720, max ~5.1k,
+# K ~ 9.4M tile/point pairs.
+BLOB_STD_LO = 0.5
+BLOB_STD_HI = 2.0
+BLOB_ZIPF = 0.3
 
 
 def blob_scene(rng, n, n_blobs=200, degree=3, log_scale=(-4.5, 0.7),
