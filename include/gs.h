@@ -237,6 +237,31 @@ gs_status gs_ws_region(const gs_plan *plan, int32_t region, size_t *offset,
 gs_status gs_sorted_pairs(const gs_plan *plan, const void *ws, cudaStream_t stream,
                           const uint32_t **pair_tile, const uint32_t **pair_item);
 
+/* Allocation-free stable radix sort of (key, value) pairs by the low
+ * key_bits bits of the key (1..32): the pair sort of gs_bin_sort for
+ * callers that cannot allocate device memory -- code inside a memory pool
+ * that must not grow, plug-ins whose host application forbids cudaMalloc
+ * after start-up, real-time paths where an allocation could block -- and so
+ * cannot size a workspace.  The paper has no counterpart; this is a
+ * property of the library only.
+ *   keys_in, vals_in   device, n entries each, not modified
+ *   keys_out, vals_out device, n entries each, overwritten with the pairs in
+ *                      key order (equal keys keep their input order)
+ * Scratch is one static device array of this library, sized for at most
+ * GS_STATIC_SORT_MAX_PAIRS pairs (about 9 MB, held on every GPU that loads
+ * the library until the process exits).  No call allocates or frees.
+ * The first call on a device looks up the array's device address (a
+ * one-time set-up); make that first call before any stream capture.  All
+ * calls of this process on one device share the array and it keeps the
+ * last call's contents: calls that may overlap on the GPU (for example on
+ * different streams) race and must be serialised by the caller.  Errors: GS_ERR_INVALID_ARG (n < 0 or
+ * n > GS_STATIC_SORT_MAX_PAIRS, key_bits out of range, NULL or overlapping
+ * buffers), GS_ERR_CUDA. */
+#define GS_STATIC_SORT_MAX_PAIRS (1 << 20)
+gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_t *vals_in,
+                               int64_t n, int32_t key_bits, uint32_t *keys_out,
+                               uint32_t *vals_out, cudaStream_t stream);
+
 /* Geometry helpers (host): total tiles and pixels of the plan's views. */
 int64_t gs_plan_tiles(const gs_plan *plan);
 int64_t gs_plan_pixels(const gs_plan *plan);

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "gs_internal.cuh"
 #include "lookback.cuh"
 
@@ -36,6 +38,7 @@ struct SortArgs {
   unsigned long long *lb;            // [2][max_parts][256] look-back slots
   long long max_parts;
   int passes;
+  int no_skip;                       // run every pass (fixed buffer parity)
   uint32_t *status;
 };
 
@@ -107,7 +110,8 @@ __global__ void __launch_bounds__(256) k_hist_scan(SortArgs a) {
     for (int q = 0; q < w; ++q) woff += s_w[q];
     a.hist[p * 256 + t] = woff + incl - c;
     int constant = __syncthreads_or(c == n);
-    bool sk = (constant || n == 0) && !(force_first && executed == 0 && p == a.passes - 1);
+    bool sk = (constant || n == 0) && !(force_first && executed == 0 && p == a.passes - 1) &&
+              !a.no_skip;
     if (t == 0) a.skip[p] = sk ? 1u : 0u;
     executed += sk ? 0 : 1;
     __syncthreads();
@@ -472,4 +476,111 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// Allocation-free variant of the pair sort (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// memory pool that must not grow, plug-ins whose host forbids cudaMalloc
+// after start-up, or real-time paths where an allocation could block.  For
+// them gs_sort_pairs_static sorts caller-provided buffers using a fixed
+// scratch array that lives in this file as a static device variable, sized
+// for at most GS_STATIC_SORT_MAX_PAIRS pairs.  Every GPU that loads the
+// library holds that array (about 9 MB) until the process exits.
+// --------------------------------------------------------------------------
+namespace {
+
+constexpr long long kStaticMax = GS_STATIC_SORT_MAX_PAIRS;
+constexpr long long kStaticParts = (kStaticMax + kSortPart - 1) / kSortPart;
+
+struct StaticHdr {
+  unsigned long long count;
+  uint32_t hist[4][256];
+  uint32_t skip[4];
+  uint32_t tickets[4];
+  uint32_t sel;
+  uint32_t status;
+};
+
+constexpr size_t kStaticHdrBytes = (sizeof(StaticHdr) + 255) & ~size_t(255);
+constexpr size_t kStaticTmpBytes = 2 * sizeof(uint32_t) * (size_t)kStaticMax;   // keys + values
+constexpr size_t kStaticLbBytes = 2 * 256 * sizeof(unsigned long long) * (size_t)kStaticParts;
+constexpr size_t kStaticBytes = kStaticHdrBytes + kStaticTmpBytes + kStaticLbBytes;
+
+// The scratch itself.  Host code must not take this symbol's address
+// directly (that would be a host-side stand-in); it asks the runtime for the
+// device address once per device.
+static __device__ __align__(256) unsigned char g_sort_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char *g_static_ptr[kMaxDevices] = {};
+
+__global__ void k_static_set_count(StaticHdr *h, unsigned long long n) {
+  h->count = n;
+  h->status = 0u;
+}
+
+}  // namespace
+
 }  // namespace gs
+
+extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_t *vals_in,
+                                           int64_t n, int32_t key_bits, uint32_t *keys_out,
+                                           uint32_t *vals_out, cudaStream_t stream) {
+  using namespace gs;
+  if (n < 0 || n > kStaticMax || key_bits < 1 || key_bits > 32) return GS_ERR_INVALID_ARG;
+  if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return GS_ERR_INVALID_ARG;
+  // the buffers must not overlap (the first pass reads the input while
+  // writing the output)
+  auto overlap = [n](const void *a, const void *b) {
+    const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+    return x < y + 4 * n && y < x + 4 * n;
+  };
+  if (n > 0 && (overlap(keys_in, keys_out) || overlap(vals_in, vals_out) ||
+                overlap(keys_in, vals_out) || overlap(vals_in, keys_out) ||
+                overlap(keys_out, vals_out)))
+    return GS_ERR_INVALID_ARG;
+  if (n == 0) return GS_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GS_ERR_CUDA;
+  unsigned char *base;
+  {
+    // one-time set-up per device, with that device current
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void *ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_sort_scratch) != cudaSuccess || !ptr) return GS_ERR_CUDA;
+      g_static_ptr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    base = g_static_ptr[dev];
+  }
+  StaticHdr *h = reinterpret_cast<StaticHdr *>(base);
+  uint32_t *tmp_k = reinterpret_cast<uint32_t *>(base + kStaticHdrBytes);
+  uint32_t *tmp_v = tmp_k + kStaticMax;
+  unsigned long long *lb = reinterpret_cast<unsigned long long *>(base + kStaticHdrBytes + kStaticTmpBytes);
+  // the array keeps the previous call's contents: clear what must start at 0
+  if (cudaMemsetAsync(h, 0, sizeof(StaticHdr), stream) != cudaSuccess) return GS_ERR_CUDA;
+  k_static_set_count<<<1, 1, 0, stream>>>(h, (unsigned long long)n);
+  SortArgs a = {};
+  a.passes = (key_bits + 7) / 8;
+  a.first_keys = keys_in;
+  a.first_vals = vals_in;
+  // every pass runs, so pass p writes buffer (p + 1) & 1: put the caller's
+  // output where the last pass writes
+  const int last = a.passes & 1;
+  a.keys[last] = keys_out;
+  a.vals[last] = vals_out;
+  a.keys[last ^ 1] = tmp_k;
+  a.vals[last ^ 1] = tmp_v;
+  a.count = &h->count;
+  a.capacity = kStaticMax;
+  a.sel = &h->sel;
+  a.hist = &h->hist[0][0];
+  a.skip = &h->skip[0];
+  a.tickets = &h->tickets[0];
+  a.lb = lb;
+  a.max_parts = kStaticParts;
+  a.no_skip = 1;
+  a.status = &h->status;
+  return run_sort(a, stream) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
