@@ -108,6 +108,8 @@ typedef struct gs_fov {
   const float *opacity_lv;     /* device (L-1,N) opacity of levels 2..L, or NULL */
   const float *dc_lv;          /* device (L-1,N,3) SH DC of levels 2..L, or NULL */
 } gs_fov;
+/* Per-level parameters (selective multi-versioning, Sec. 4.2) are supported
+ * for L <= 4; gs_project returns GS_ERR_UNSUPPORTED beyond. */
 
 /* Plan options.  Zero-initialised fields take the defaults given. */
 typedef struct gs_config {

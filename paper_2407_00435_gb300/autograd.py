@@ -1,0 +1,81 @@
+"""torch.autograd.Function around the C-ABI forward and backward passes.
+
+``render(scene, renderer)`` returns the (P, 3) image of all views of the
+renderer's plan; its backward runs ``gs_render_backward`` and returns
+gradients for means, scales, quats, opacities and SH (and, with per-level
+foveation parameters, for those too).  The renderer must have been created
+with ``backward=True``.
+"""
+from __future__ import annotations
+
+import torch
+
+from .gs import GS_ERR_CAPACITY, GS_OK, GsError, Renderer
+
+_KEYS = ("means", "scales", "quats", "opac", "sh")
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, scales, quats, opac, sh, opacity_lv, dc_lv, renderer: Renderer,
+                fov: dict | None, bg, check: bool):
+        sc = {"means": means.detach().contiguous(), "scales": scales.detach().contiguous(),
+              "quats": quats.detach().contiguous(), "opac": opac.detach().contiguous(),
+              "sh": sh.detach().contiguous()}
+        f = None
+        if fov is not None:
+            f = dict(fov)
+            f["opacity_lv"] = None if opacity_lv is None else opacity_lv.detach().contiguous()
+            f["dc_lv"] = None if dc_lv is None else dc_lv.detach().contiguous()
+        if check:
+            renderer.fit(sc, f)
+        else:
+            renderer.project(sc, f)
+            renderer.bin_sort()
+        out = renderer.alloc_outputs(fov=f is not None)
+        renderer.render(out, bg=bg, fov=f is not None)
+        if check:
+            code, c = renderer.counters()
+            if code != GS_OK:
+                raise GsError(code, "render")
+        ctx.renderer = renderer
+        ctx.out = out
+        ctx.bg = bg
+        ctx.sc = sc
+        ctx.fov = f
+        ctx.has_lv = (opacity_lv is not None, dc_lv is not None)
+        ctx.shapes = [t.shape for t in (means, scales, quats, opac, sh)]
+        return out["rgb"]
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        r: Renderer = ctx.renderer
+        dev = grad_rgb.device
+        grads = {k: torch.empty(ctx.sc[k].shape, device=dev) for k in _KEYS}
+        if ctx.has_lv[0]:
+            grads["opac_lv"] = torch.empty_like(ctx.fov["opacity_lv"])
+        if ctx.has_lv[1]:
+            grads["dc_lv"] = torch.empty_like(ctx.fov["dc_lv"])
+        r.backward(grad_rgb.contiguous(), ctx.out, grads, bg=ctx.bg)
+        return (grads["means"], grads["scales"], grads["quats"], grads["opac"], grads["sh"],
+                grads.get("opac_lv"), grads.get("dc_lv"), None, None, None, None)
+
+
+def render(scene: dict, renderer: Renderer, fov: dict | None = None, bg=(0.0, 0.0, 0.0),
+           check: bool = True) -> torch.Tensor:
+    """Differentiable render of every view of ``renderer``'s plan.
+
+    ``scene``: dict of (N,3) means, (N,3) scales, (N,4) quats, (N,) opac,
+    (N,S,3) sh device tensors (any may require grad).  ``fov``: the
+    foveation dict of :func:`gs.fov_to_device` (its ``opacity_lv`` /
+    ``dc_lv`` may require grad).  ``check`` synchronises once per call to
+    grow the pair capacity if needed.
+    """
+    op_lv = fov.get("opacity_lv") if fov is not None else None
+    dc_lv = fov.get("dc_lv") if fov is not None else None
+    return _RenderFn.apply(scene["means"], scene["scales"], scene["quats"], scene["opac"],
+                           scene["sh"], op_lv, dc_lv, renderer, fov, tuple(bg), check)
+
+
+def l1_loss(rgb: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
+    return (rgb - target).abs().mean()

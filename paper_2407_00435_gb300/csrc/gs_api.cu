@@ -154,7 +154,7 @@ gs_status gs_project(gs_plan *p, void *ws, size_t ws_bytes, const gs_scene *scen
     if ((p->flags & GS_FLAG_BACKWARD) && (fov->opacity_lv || fov->dc_lv) &&
         p->bytes[R_GRAD_LV] < 4 * sizeof(float) * (size_t)(L - 1) * (size_t)p->max_visible)
       return GS_ERR_INVALID_ARG;
-    if ((fov->opacity_lv || fov->dc_lv) && L > GS_MAX_LEVELS) return GS_ERR_INVALID_ARG;
+    if ((fov->opacity_lv || fov->dc_lv) && L > kMvMaxLevels) return GS_ERR_UNSUPPORTED;
     p->fov = *fov;
     p->has_fov = 1;
     p->fov_mv = (fov->opacity_lv || fov->dc_lv) && L > 1;

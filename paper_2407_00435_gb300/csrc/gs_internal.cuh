@@ -24,6 +24,8 @@ constexpr float kLog2AlphaMin = -7.99435343685886f;
 constexpr float kWhiten = 0.84932180028801904f;
 
 constexpr int kMaxViews = 4096;
+// selective multi-versioning (per-level opacity / SH DC) holds levels 2..4
+constexpr int kMvMaxLevels = 4;
 
 // --------------------------------------------------------------------------
 // workspace regions

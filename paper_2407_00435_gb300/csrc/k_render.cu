@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "gs_internal.cuh"
+#include "raster.cuh"
 
 namespace gs {
 
@@ -43,28 +44,13 @@ struct RenderArgs {
   unsigned long long *n_evals, *n_blends;
 };
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ int find_view(const ViewDev *views, int V, long long t) {
-  int lo = 0, hi = V - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (views[mid].tile_base <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 struct Acc {
   float r, g, b, T;
   int last;
   bool done;
 };
 
-constexpr int kMaxLv = GS_MAX_LEVELS - 1;
+constexpr int kMaxLv = kMvMaxLevels - 1;
 
 template <int B, bool FOV, bool MV, bool STATS>
 __global__ void __launch_bounds__(B * B) k_render(RenderArgs a) {
@@ -91,22 +77,7 @@ __global__ void __launch_bounds__(B * B) k_render(RenderArgs a) {
   int lvl = 1;
   bool in_band = false;
   float wband = 1.0f;
-  if (FOV && vd.fov) {
-    float dx = ((float)x + 0.5f) - vd.gx;
-    float dy = ((float)y + 0.5f) - vd.gy;
-    float d2 = dx * dx + dy * dy;
-    for (int k = 0; k < a.L - 1; ++k) {
-      float Rk = vd.R[k];
-      if (d2 >= Rk * Rk) lvl++;
-    }
-    if (lvl >= 2 && a.band > 0.0f) {
-      float Rb = vd.R[lvl - 2] + a.band;
-      if (d2 < Rb * Rb) {
-        in_band = true;
-        wband = fminf(1.0f, fmaxf(0.0f, (sqrtf(d2) - vd.R[lvl - 2]) / a.band));
-      }
-    }
-  }
+  if (FOV) pixel_level(vd, a.L, a.band, x, y, lvl, in_band, wband);
   Acc A = {0.f, 0.f, 0.f, 1.f, -1, !inside};
   Acc Bq = {0.f, 0.f, 0.f, 1.f, -1, !(inside && in_band)};
   float dom_w = -1.0f;
@@ -160,18 +131,16 @@ __global__ void __launch_bounds__(B * B) k_render(RenderArgs a) {
       for (uint32_t q = 0; q < cnt; ++q) {
         const float2 mu = s_mean[q];
         const float4 sh = s_shape[q];
-        const float dx = px - mu.x, dy = py - mu.y;
-        const float t1 = fmaf(dx, sh.x, dy * sh.y);
-        const float t2 = fmaf(dx, sh.z, dy * sh.w);
-        const float g = fmaf(-t1, t1, -(t2 * t2));
+        float dx, dy, t1, t2;
+        const float g = log2_alpha(px, py, mu, sh, 0.0f, dx, dy, t1, t2);
         const int m = FOV ? s_m[q] : 0;
         // accumulator A: the pixel's own level
         if (!A.done && (!FOV || m >= lvl)) {
           const float4 c = (MV && lvl >= 2) ? s_lv[q][lvl - 2] : s_col[q];
-          const float p = g + c.w;
+          const float p = __fadd_rn(g, c.w);
           if (STATS) ++n_eval;
           if (p >= kLog2AlphaMin) {
-            const float al = fminf(kAlphaMax, ex2_approx(p));
+            const float al = alpha_of(p);
             const float Tn = A.T * (1.0f - al);
             if (Tn < kTMin) {
               A.done = true;
@@ -193,9 +162,9 @@ __global__ void __launch_bounds__(B * B) k_render(RenderArgs a) {
         // accumulator B: the better level inside a blend band
         if (FOV && !Bq.done && m >= lvl - 1) {
           const float4 c = (MV && lvl >= 3) ? s_lv[q][lvl - 3] : s_col[q];
-          const float p = g + c.w;
+          const float p = __fadd_rn(g, c.w);
           if (p >= kLog2AlphaMin) {
-            const float al = fminf(kAlphaMax, ex2_approx(p));
+            const float al = alpha_of(p);
             const float Tn = Bq.T * (1.0f - al);
             if (Tn < kTMin) {
               Bq.done = true;
