@@ -36,6 +36,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--only", nargs="*", default=None, help="extras to run")
     return ap.parse_args()
 
 
@@ -243,7 +244,22 @@ def gpu_arm(args):
 
     e2e_ms, _ = time_steps(torch, e2e_step, max(3, args.steps // 2), 2, flush)
     e2e_ms /= max(3, args.steps // 2)
+    gpu_launches = args.steps * r.launches_per_frame()
 
+    P_head = r.P
+    extras = {}
+    if not args.no_extras:
+        del r, sc, dev, host, out
+        torch.cuda.empty_cache()
+        steps_x = max(3, min(args.steps, 10))
+        for name, fn in (("foveated_stereo", extra_foveated), ("fwd_bwd", extra_fwd_bwd),
+                         ("batched_64_views", extra_batched)):
+            if args.only and name not in args.only:
+                continue
+            try:
+                extras[name] = fn(torch, gs, synth, flush, steps_x)
+            except Exception as e:  # report, never hide
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
     res = {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -254,16 +270,163 @@ def gpu_arm(args):
                    "pairs_K": int(c["n_pairs"]), "visible": int(c["n_visible"]),
                    "l2": "flushed between steps (256 MB write) and scene 236 MB > L2",
                    "parallelism": f"replicas x{world}"},
-        "gpix_per_s": round(value * r.P / 1e9, 3),
+        "gpix_per_s": round(value * P_head / 1e9, 3),
         "blends_per_s": round(n_blends * value, 1),
         "evals_per_s": round(n_evals * value, 1),
         "roofline": roofline,
         "e2e": {"value": round(1000.0 / e2e_ms * world, 2), "unit": "frames/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
-        "gpu_launches": args.steps * r.launches_per_frame(),
+        "gpu_launches": gpu_launches,
+        "extras": extras,
     }
     return res, rank, world
+
+
+# --------------------------------------------------------------------------
+# the other workloads: foveated stereo, forward+backward, batched views
+# --------------------------------------------------------------------------
+def _ms(torch, fn, steps, warmup, flush):
+    total, _ = time_steps(torch, lambda kev: fn(), steps, warmup, flush)
+    return total / steps
+
+
+def extra_foveated(torch, gs, synth, flush, steps):
+    """3M points, 2 eyes at 1920x1920, 4 nested levels: foveated vs plain."""
+    wl = synth.workload(2)
+    sc = gs.scene_to_device(wl.scene)
+    f = gs.fov_to_device(wl.fov)
+    rf = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True)
+    cf = rf.fit(sc, f)
+    of = rf.alloc_outputs(fov=True, stats=True)
+    rf.render(of, fov=True)
+    _, cntf = rf.counters()
+    of = rf.alloc_outputs(fov=True)
+    rp = gs.Renderer(wl.scene.n, 3, wl.cams)
+    cp = rp.fit(sc)
+    op = rp.alloc_outputs()
+
+    def fov_step():
+        rf.project(sc, f)
+        rf.bin_sort()
+        rf.render(of, fov=True)
+
+    def plain_step():
+        rp.project(sc)
+        rp.bin_sort()
+        rp.render(op)
+
+    ms_f = _ms(torch, fov_step, steps, 2, flush)
+    ms_p = _ms(torch, plain_step, steps, 2, flush)
+    px = rf.P
+    del rf, rp, sc
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "fps_foveated": round(1000 / ms_f, 2),
+            "fps_plain": round(1000 / ms_p, 2), "speedup": round(ms_p / ms_f, 3),
+            "gpix_per_s_foveated": round(px / ms_f / 1e6, 3),
+            "pairs_foveated": int(cf["n_pairs"]), "pairs_plain": int(cp["n_pairs"]),
+            "blends_per_s_foveated": round(int(cntf["n_blends"]) * 1000 / ms_f, 1),
+            "frame": "2 eyes"}
+
+
+def extra_fwd_bwd(torch, gs, synth, flush, steps):
+    """500k points, SH3, 8 views at 1024^2, L1 loss: one batched plan vs 8
+    per-view plans, forward + backward."""
+    import numpy as np
+    from paper_2407_00435_gb300 import autograd as ga
+    wl = synth.workload(3)
+    sc = gs.scene_to_device(wl.scene)
+    V = len(wl.cams)
+    rng = np.random.default_rng(1003)
+    target = torch.from_numpy(rng.uniform(0, 1, (V * 1024 * 1024, 3)).astype(np.float32)).cuda()
+    rb = gs.Renderer(wl.scene.n, 3, wl.cams, backward=True)
+    rb.fit(sc)
+    per = [gs.Renderer(wl.scene.n, 3, wl.cams[v:v + 1], backward=True) for v in range(V)]
+    for r in per:
+        r.fit(sc)
+    g = {k: torch.empty_like(v) for k, v in sc.items()}
+    ob = rb.alloc_outputs()
+    ov = [r.alloc_outputs() for r in per]
+    npx = 1024 * 1024
+
+    def batched():
+        rb.project(sc)
+        rb.bin_sort()
+        rb.render(ob)
+        dL = torch.sign(ob["rgb"] - target) / ob["rgb"].numel()
+        rb.backward(dL, ob, g)
+
+    def per_view():
+        for v, r in enumerate(per):
+            r.project(sc)
+            r.bin_sort()
+            r.render(ov[v])
+            tv = target[v * npx:(v + 1) * npx]
+            dL = torch.sign(ov[v]["rgb"] - tv) / (ov[v]["rgb"].numel() * V)
+            r.backward(dL, ov[v], g)
+
+    def bwd_only():
+        dL = torch.sign(ob["rgb"] - target) / ob["rgb"].numel()
+        rb.backward(dL, ob, g)
+
+    ms_b = _ms(torch, batched, steps, 2, flush)
+    ms_v = _ms(torch, per_view, steps, 2, flush)
+    batched()
+    ms_bwd = _ms(torch, bwd_only, steps, 2, flush)
+    # autograd path (L1 loss through torch.autograd.Function)
+    scg = {k: v.clone().requires_grad_(True) for k, v in sc.items()}
+
+    def autograd_step():
+        for v in scg.values():
+            v.grad = None
+        loss = ga.l1_loss(ga.render(scg, rb, check=False), target)
+        loss.backward()
+
+    ms_ag = _ms(torch, autograd_step, steps, 2, flush)
+    del rb, per, sc
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "views": V, "fwd_bwd_ms_batched": round(ms_b, 3),
+            "fwd_bwd_ms_per_view_plans": round(ms_v, 3), "speedup": round(ms_v / ms_b, 3),
+            "bwd_ms_per_view": round(ms_bwd / V, 4), "autograd_step_ms": round(ms_ag, 3)}
+
+
+def extra_batched(torch, gs, synth, flush, steps):
+    """6M points, 64 views of uneven sizes, half foveated: project + sort +
+    render of all views as one CUDA graph (one render launch for all tiles)."""
+    wl = synth.workload(4)
+    sc = gs.scene_to_device(wl.scene)
+    f = gs.fov_to_device(wl.fov)
+    r = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True)
+    c = r.fit(sc, f, headroom=1.05)
+    out = r.alloc_outputs(fov=True)
+
+    def frame():
+        r.project(sc, f)
+        r.bin_sort()
+        r.render(out, fov=True)
+
+    frame()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        frame()   # warm the side stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            frame()
+    torch.cuda.current_stream().wait_stream(s)
+    code, c2 = r.counters()
+    ms = _ms(torch, graph.replay, steps, 1, flush)
+    code, c3 = r.counters()
+    res = {"workload": wl.name, "views": len(wl.cams), "pixels": r.P,
+           "ms_per_batch": round(ms, 3), "views_per_s": round(len(wl.cams) * 1000 / ms, 2),
+           "gpix_per_s": round(r.P / ms / 1e6, 3), "pairs": int(c["n_pairs"]),
+           "visible": int(c["n_visible"]), "status": int(code),
+           "kernel_launches_in_graph": r.launches_per_frame(fov=True)}
+    del r, sc, graph
+    torch.cuda.empty_cache()
+    return res
 
 
 # --------------------------------------------------------------------------
