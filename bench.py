@@ -178,18 +178,24 @@ def gpu_arm(args):
     n_evals, n_blends = int(cnt["n_evals"]), int(cnt["n_blends"])
     out = r.alloc_outputs()
 
+    stage_ev = []
+
     def step(kev):
+        if kev is None:
+            r.project(sc)
+            r.bin_sort()
+            r.render(out)
+            return
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
         r.project(sc)
+        e[1].record()
         r.bin_sort()
-        if kev is not None:
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            r.render(out)
-            b.record()
-            kev.append((a, b))
-        else:
-            r.render(out)
+        e[2].record()
+        r.render(out)
+        e[3].record()
+        kev.append((e[2], e[3]))
+        stage_ev.append(e)
 
     for _ in range(args.warmup):
         step(None)
@@ -213,6 +219,8 @@ def gpu_arm(args):
     value = fps_rank * world
     render_ms = sum(k_ms) / len(k_ms)
     clocks = clk.summary()
+    stages = {nm: round(sum(e[q].elapsed_time(e[q + 1]) for e in stage_ev) / len(stage_ev), 4)
+              for q, nm in enumerate(("project", "bin_sort", "render"))}
 
     # roofline of the dominant kernel (render): FP32 issue bound
     peaks, src = _peaks()
@@ -273,6 +281,7 @@ def gpu_arm(args):
         "gpix_per_s": round(value * P_head / 1e9, 3),
         "blends_per_s": round(n_blends * value, 1),
         "evals_per_s": round(n_evals * value, 1),
+        "stages_ms": stages,
         "roofline": roofline,
         "e2e": {"value": round(1000.0 / e2e_ms * world, 2), "unit": "frames/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -368,8 +368,159 @@ __device__ __forceinline__ bool all_finite(const float *p, int n) {
   return ok;
 }
 
+// Padded shared-memory rows (odd strides: no bank conflicts when every
+// thread reads element k of its own row).
 template <int S>
+struct ProjSmem {
+  static constexpr int kSh = (S * 3) | 1;
+  float sh[kProjThreads][kSh];
+  float mu[kProjThreads][3];
+  float sc[kProjThreads][3];
+  float q[kProjThreads][5];
+  float op[kProjThreads];
+};
+
+// Coalesced load of `cnt` consecutive rows of `width` floats from global
+// `src` (row `row0`) into a padded shared array with row stride `stride`.
+__device__ __forceinline__ void stage_rows(float *dst, int stride, const float *src, long long row0,
+                                           int cnt, int width) {
+  const long long f0 = row0 * width;
+  const int total = cnt * width;
+  const float *g = src + f0;
+  if ((((uintptr_t)g) & 15) == 0) {
+    const int n4 = total >> 2;
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    for (int v = threadIdx.x; v < n4; v += blockDim.x) {
+      const float4 x = g4[v];
+      const int f = v * 4;
+      dst[(f / width) * stride + f % width] = x.x;
+      dst[((f + 1) / width) * stride + (f + 1) % width] = x.y;
+      dst[((f + 2) / width) * stride + (f + 2) % width] = x.z;
+      dst[((f + 3) / width) * stride + (f + 3) % width] = x.w;
+    }
+    for (int f = (n4 << 2) + threadIdx.x; f < total; f += blockDim.x)
+      dst[(f / width) * stride + f % width] = g[f];
+  } else {
+    for (int f = threadIdx.x; f < total; f += blockDim.x)
+      dst[(f / width) * stride + f % width] = g[f];
+  }
+}
+
+struct Rec {
+  float4 mean, shape, color, rest;
+  uint32_t depth, count;
+  uint2 rect;
+  uint8_t m;
+};
+
+// Full projection of one (point, view) that passed the keyed test.
+template <int S>
+__device__ __forceinline__ void project_value(const ProjArgs &a, const ProjSmem<S> &sm, int tid,
+                                              long long i, const float mu[3],
+                                              const gs_camera &cam, const ViewDev &vd,
+                                              const Keyed &k, Rec &out) {
+  // --- compensated 2D mean ---
+  float xh, xl, yh, yl, zh, zl;
+  dot3_comp(&cam.R[0], mu, cam.t[0], xh, xl);
+  dot3_comp(&cam.R[3], mu, cam.t[1], yh, yl);
+  dot3_comp(&cam.R[6], mu, cam.t[2], zh, zl);
+  float uh, ul, vh, vl;
+  proj_comp(xh, xl, zh, zl, cam.fx, cam.cx, uh, ul);
+  proj_comp(yh, yl, zh, zl, cam.fy, cam.cy, vh, vl);
+  // --- 2D covariance from G = J W M, whitened (eigen form) ---
+  float G0[3], G1[3], T0[3], T1[3];
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    T0[kk] = fmaf(k.j02, cam.R[6 + kk], k.j00 * cam.R[kk]);
+    T1[kk] = fmaf(k.j12, cam.R[6 + kk], k.j11 * cam.R[3 + kk]);
+  }
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    G0[kk] = fmaf(T0[2], k.M[6 + kk], fmaf(T0[1], k.M[3 + kk], T0[0] * k.M[kk]));
+    G1[kk] = fmaf(T1[2], k.M[6 + kk], fmaf(T1[1], k.M[3 + kk], T1[0] * k.M[kk]));
+  }
+  const float n0 = fmaf(G0[2], G0[2], fmaf(G0[1], G0[1], G0[0] * G0[0]));
+  const float n1 = fmaf(G1[2], G1[2], fmaf(G1[1], G1[1], G1[0] * G1[0]));
+  const float aa = n0 + kLowpass, cc = n1 + kLowpass;
+  const float bb = fmaf(G0[2], G1[2], fmaf(G0[1], G1[1], G0[0] * G1[0]));
+  // det(G G^T + 0.3 I) = sum of squared 2x2 minors + 0.3 (|G0|^2 + |G1|^2) + 0.09
+  float det = kLowpass * kLowpass + kLowpass * (n0 + n1);
+#pragma unroll
+  for (int p0 = 0; p0 < 3; ++p0) {
+    const int p1 = (p0 + 1) % 3;
+    const float w = G0[p1] * G1[p0];
+    const float e = fmaf(-G0[p1], G1[p0], w);
+    const float f = fmaf(G0[p0], G1[p1], -w);
+    const float m = f + e;
+    det = fmaf(m, m, det);
+  }
+  const float hd = 0.5f * (aa - cc);
+  const float hyp = sqrtf(fmaf(hd, hd, bb * bb));
+  const float l1 = 0.5f * (aa + cc) + hyp;
+  const float l2 = det / l1;
+  float e1x, e1y;
+  if (aa >= cc) { e1x = hd + hyp; e1y = bb; } else { e1x = bb; e1y = hyp - hd; }
+  const float en = sqrtf(fmaf(e1x, e1x, e1y * e1y));
+  if (en > 0.0f) { e1x = e1x / en; e1y = e1y / en; } else { e1x = 1.0f; e1y = 0.0f; }
+  const float s1 = kWhiten / sqrtf(l1), s2 = kWhiten / sqrtf(l2);
+  out.shape = make_float4(e1x * s1, e1y * s1, -e1y * s2, e1x * s2);
+  // --- colour g(SH) at the view direction ---
+  const float dx = mu[0] - vd.ccx, dy = mu[1] - vd.ccy, dz = mu[2] - vd.ccz;
+  const float dn = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  const float inv = dn > 0.0f ? 1.0f / dn : 0.0f;
+  float Y[16];
+  sh_basis(dx * inv, dy * inv, dz * inv, S, Y);
+  const float *shc = sm.sh[tid];
+  float rest[3], col[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int kk = 1; kk < S; ++kk) acc = fmaf(shc[3 * kk + ch], Y[kk], acc);
+    rest[ch] = acc;
+    col[ch] = fmaxf(0.0f, fmaf(shc[ch], Y[0], acc) + kShOffset);
+  }
+  // --- pairs kept by the foveation filter ---
+  uint32_t pairs;
+  uint8_t m = 0;
+  if (a.tile_level) {
+    m = a.bound_m[i];
+    pairs = 0;
+    const long long tb = vd.tile_base;
+    for (int y = k.y0; y <= k.y1; ++y)
+      for (int x = k.x0; x <= k.x1; ++x)
+        pairs += a.tile_level[tb + (long long)y * vd.tx + x] <= m ? 1u : 0u;
+  } else {
+    pairs = (uint32_t)((k.x1 - k.x0 + 1) * (k.y1 - k.y0 + 1));
+  }
+  out.mean = make_float4(uh, vh, ul, vl);
+  out.color = make_float4(col[0], col[1], col[2], log2f(sm.op[tid]));
+  out.rest = make_float4(rest[0], rest[1], rest[2], 0.0f);
+  out.depth = __float_as_uint(k.pz);
+  out.count = pairs;
+  out.rect = make_uint2((uint32_t)k.x0 | ((uint32_t)k.x1 << 16), (uint32_t)k.y0 | ((uint32_t)k.y1 << 16));
+  out.m = m;
+}
+
+__device__ __forceinline__ void write_rec(const ProjArgs &a, unsigned long long j, const Rec &r,
+                                          uint32_t gid, uint32_t v) {
+  a.rec_mean[j] = r.mean;
+  a.rec_shape[j] = r.shape;
+  a.rec_color[j] = r.color;
+  if (a.rec_rest) {
+    a.rec_rest[j] = r.rest;
+    a.rec_m[j] = r.m;
+  }
+  a.rec_depth[j] = r.depth;
+  a.rec_count[j] = r.count;
+  a.rec_rect[j] = r.rect;
+  a.rec_gid[j] = gid;
+  a.rec_view[j] = v;
+}
+
+template <int S, bool ONE_VIEW>
 __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
+  __shared__ ProjSmem<S> sm;
   __shared__ uint32_t s_part;
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_wsum[kProjThreads / 32];
@@ -381,35 +532,52 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
   }
   __syncthreads();
   const uint32_t part = s_part;
-  const long long i = (long long)part * kProjThreads + tid;
-  const bool valid = i < a.n;
+  const long long row0 = (long long)part * kProjThreads;
+  const int cnt_rows = (int)min((long long)kProjThreads, a.n - row0);
+  // coalesced staging of this block's points
+  stage_rows(&sm.sh[0][0], ProjSmem<S>::kSh, a.sh, row0, cnt_rows, S * 3);
+  stage_rows(&sm.mu[0][0], 3, a.means, row0, cnt_rows, 3);
+  stage_rows(&sm.sc[0][0], 3, a.scales, row0, cnt_rows, 3);
+  stage_rows(&sm.q[0][0], 5, a.quats, row0, cnt_rows, 4);
+  stage_rows(&sm.op[0], 1, a.opac, row0, cnt_rows, 1);
+  __syncthreads();
+  const long long i = row0 + tid;
+  const bool valid = tid < cnt_rows;
 
-  float mu[3] = {0, 0, 0}, sc[3] = {1, 1, 1}, q[4] = {1, 0, 0, 0}, op = 0.5f;
-  float shc[S * 3];
+  float mu[3] = {0, 0, 0}, sc[3] = {1, 1, 1}, q[4] = {1, 0, 0, 0};
   bool fin = false;
   if (valid) {
-    mu[0] = a.means[3 * i]; mu[1] = a.means[3 * i + 1]; mu[2] = a.means[3 * i + 2];
-    sc[0] = a.scales[3 * i]; sc[1] = a.scales[3 * i + 1]; sc[2] = a.scales[3 * i + 2];
-    q[0] = a.quats[4 * i]; q[1] = a.quats[4 * i + 1];
-    q[2] = a.quats[4 * i + 2]; q[3] = a.quats[4 * i + 3];
-    op = a.opac[i];
 #pragma unroll
-    for (int k = 0; k < S * 3; ++k) shc[k] = a.sh[(long long)S * 3 * i + k];
-    fin = all_finite(mu, 3) && all_finite(sc, 3) && all_finite(q, 4) && isfinite(op) &&
-          all_finite(shc, S * 3);
+    for (int k = 0; k < 3; ++k) { mu[k] = sm.mu[tid][k]; sc[k] = sm.sc[tid][k]; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = sm.q[tid][k];
+    fin = all_finite(mu, 3) && all_finite(sc, 3) && all_finite(q, 4) && isfinite(sm.op[tid]) &&
+          all_finite(sm.sh[tid], S * 3);
   }
   if (valid && !fin) atomicAdd(&s_nonfinite, (uint32_t)a.V);
 
-  // phase 1: visibility per view (keyed path only) -> count of records
+  // phase 1: visibility per view -> count of records (one view: the whole
+  // record is computed here and kept in registers)
   uint32_t cnt = 0;
+  Rec rec1;
   if (valid && fin) {
-    for (int v = 0; v < a.V; ++v) {
-      const ViewDev &vd = a.views[v];
+    if (ONE_VIEW) {
+      const gs_camera cam = a.cams[0];
+      const ViewDev &vd = a.views[0];
       Keyed k;
-      cnt += keyed_project(mu, sc, q, a.cams[v], a.tile, vd.tx, vd.ty, k) ? 1u : 0u;
+      if (keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) {
+        project_value<S>(a, sm, tid, i, mu, cam, vd, k, rec1);
+        cnt = 1;
+      }
+    } else {
+      for (int v = 0; v < a.V; ++v) {
+        const ViewDev &vd = a.views[v];
+        Keyed k;
+        cnt += keyed_project(mu, sc, q, a.cams[v], a.tile, vd.tx, vd.ty, k) ? 1u : 0u;
+      }
     }
   }
-  // block exclusive scan of cnt
+  // block exclusive scan of cnt, then the partition's global offset
   const int lane = tid & 31, warp = tid >> 5;
   uint32_t incl = cnt;
 #pragma unroll
@@ -436,7 +604,14 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
   __syncthreads();
   unsigned long long j = s_base + woff + (incl - cnt);
   if (cnt == 0) return;
-
+  if (ONE_VIEW) {
+    if ((long long)j >= a.max_visible) {
+      set_status(&a.hdr->status, GS_ERR_CAPACITY);
+      return;
+    }
+    write_rec(a, j, rec1, (uint32_t)i, 0u);
+    return;
+  }
   // phase 2: full projection of the visible views, written at j, j+1, ...
   for (int v = 0; v < a.V; ++v) {
     const gs_camera cam = a.cams[v];
@@ -447,93 +622,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
       set_status(&a.hdr->status, GS_ERR_CAPACITY);
       return;
     }
-    // --- compensated 2D mean ---
-    float xh, xl, yh, yl, zh, zl;
-    dot3_comp(&cam.R[0], mu, cam.t[0], xh, xl);
-    dot3_comp(&cam.R[3], mu, cam.t[1], yh, yl);
-    dot3_comp(&cam.R[6], mu, cam.t[2], zh, zl);
-    float uh, ul, vh, vl;
-    proj_comp(xh, xl, zh, zl, cam.fx, cam.cx, uh, ul);
-    proj_comp(yh, yl, zh, zl, cam.fy, cam.cy, vh, vl);
-    // --- 2D covariance from G = J W M, whitened (eigen form) ---
-    float G0[3], G1[3];
-    float T0[3], T1[3];
-#pragma unroll
-    for (int kk = 0; kk < 3; ++kk) {
-      T0[kk] = fmaf(k.j02, cam.R[6 + kk], k.j00 * cam.R[kk]);
-      T1[kk] = fmaf(k.j12, cam.R[6 + kk], k.j11 * cam.R[3 + kk]);
-    }
-#pragma unroll
-    for (int kk = 0; kk < 3; ++kk) {
-      G0[kk] = fmaf(T0[2], k.M[6 + kk], fmaf(T0[1], k.M[3 + kk], T0[0] * k.M[kk]));
-      G1[kk] = fmaf(T1[2], k.M[6 + kk], fmaf(T1[1], k.M[3 + kk], T1[0] * k.M[kk]));
-    }
-    float n0 = fmaf(G0[2], G0[2], fmaf(G0[1], G0[1], G0[0] * G0[0]));
-    float n1 = fmaf(G1[2], G1[2], fmaf(G1[1], G1[1], G1[0] * G1[0]));
-    float aa = n0 + kLowpass, cc = n1 + kLowpass;
-    float bb = fmaf(G0[2], G1[2], fmaf(G0[1], G1[1], G0[0] * G1[0]));
-    // det(G G^T + 0.3 I) = sum of squared 2x2 minors + 0.3 (|G0|^2 + |G1|^2) + 0.09
-    float det = kLowpass * kLowpass + kLowpass * (n0 + n1);
-#pragma unroll
-    for (int p0 = 0; p0 < 3; ++p0) {
-      int p1 = (p0 + 1) % 3;
-      float w = G0[p1] * G1[p0];
-      float e = fmaf(-G0[p1], G1[p0], w);
-      float f = fmaf(G0[p0], G1[p1], -w);
-      float m = f + e;
-      det = fmaf(m, m, det);
-    }
-    float hd = 0.5f * (aa - cc);
-    float hyp = sqrtf(fmaf(hd, hd, bb * bb));
-    float l1 = 0.5f * (aa + cc) + hyp;
-    float l2 = det / l1;
-    float e1x, e1y;
-    if (aa >= cc) { e1x = hd + hyp; e1y = bb; } else { e1x = bb; e1y = hyp - hd; }
-    float en = sqrtf(fmaf(e1x, e1x, e1y * e1y));
-    if (en > 0.0f) { e1x = e1x / en; e1y = e1y / en; } else { e1x = 1.0f; e1y = 0.0f; }
-    float s1 = kWhiten / sqrtf(l1), s2 = kWhiten / sqrtf(l2);
-    float4 shape = make_float4(e1x * s1, e1y * s1, -e1y * s2, e1x * s2);
-    // --- colour g(SH) at the view direction ---
-    float dx = mu[0] - vd.ccx, dy = mu[1] - vd.ccy, dz = mu[2] - vd.ccz;
-    float dn = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    float inv = dn > 0.0f ? 1.0f / dn : 0.0f;
-    float Y[16];
-    sh_basis(dx * inv, dy * inv, dz * inv, S, Y);
-    float rest[3], col[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int kk = 1; kk < S; ++kk) acc = fmaf(shc[3 * kk + ch], Y[kk], acc);
-      rest[ch] = acc;
-      col[ch] = fmaxf(0.0f, fmaf(shc[ch], Y[0], acc) + kShOffset);
-    }
-    // --- pairs kept by the foveation filter ---
-    uint32_t pairs;
-    uint8_t m = 0;
-    if (a.tile_level) {
-      m = a.bound_m[i];
-      pairs = 0;
-      const long long tb = vd.tile_base;
-      for (int y = k.y0; y <= k.y1; ++y)
-        for (int x = k.x0; x <= k.x1; ++x)
-          pairs += a.tile_level[tb + (long long)y * vd.tx + x] <= m ? 1u : 0u;
-    } else {
-      pairs = (uint32_t)((k.x1 - k.x0 + 1) * (k.y1 - k.y0 + 1));
-    }
-    a.rec_mean[j] = make_float4(uh, vh, ul, vl);
-    a.rec_shape[j] = shape;
-    a.rec_color[j] = make_float4(col[0], col[1], col[2], log2f(op));
-    if (a.rec_rest) {
-      a.rec_rest[j] = make_float4(rest[0], rest[1], rest[2], 0.0f);
-      a.rec_m[j] = m;
-    }
-    a.rec_depth[j] = __float_as_uint(k.pz);
-    a.rec_count[j] = pairs;
-    a.rec_rect[j] = make_uint2((uint32_t)k.x0 | ((uint32_t)k.x1 << 16),
-                               (uint32_t)k.y0 | ((uint32_t)k.y1 << 16));
-    a.rec_gid[j] = (uint32_t)i;
-    a.rec_view[j] = (uint32_t)v;
+    Rec r;
+    project_value<S>(a, sm, tid, i, mu, cam, vd, k, r);
+    write_rec(a, j, r, (uint32_t)i, (uint32_t)v);
     ++j;
   }
 }
@@ -568,11 +659,16 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
   a.rec_rect = region<uint2>(p, ws, R_REC_RECT);
   a.rec_m = p->bytes[R_REC_M] ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
   unsigned grid = (unsigned)((p->n + kProjThreads - 1) / kProjThreads);
+  const bool one = p->V == 1;
   switch (a.S) {
-    case 1: k_project<1><<<grid, kProjThreads, 0, s>>>(a); break;
-    case 4: k_project<4><<<grid, kProjThreads, 0, s>>>(a); break;
-    case 9: k_project<9><<<grid, kProjThreads, 0, s>>>(a); break;
-    default: k_project<16><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 1: one ? k_project<1, true><<<grid, kProjThreads, 0, s>>>(a)
+                : k_project<1, false><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 4: one ? k_project<4, true><<<grid, kProjThreads, 0, s>>>(a)
+                : k_project<4, false><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 9: one ? k_project<9, true><<<grid, kProjThreads, 0, s>>>(a)
+                : k_project<9, false><<<grid, kProjThreads, 0, s>>>(a); break;
+    default: one ? k_project<16, true><<<grid, kProjThreads, 0, s>>>(a)
+                 : k_project<16, false><<<grid, kProjThreads, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }

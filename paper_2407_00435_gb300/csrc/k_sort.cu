@@ -38,6 +38,7 @@ struct SortArgs {
   unsigned long long *lb;            // [2][max_parts][256] look-back slots
   long long max_parts;
   int passes;
+  int digit_bits;                    // bits per pass (<= 8)
   int no_skip;                       // run every pass (fixed buffer parity)
   uint32_t *status;
 };
@@ -70,11 +71,18 @@ __global__ void __launch_bounds__(256) k_hist(SortArgs a) {
     long long idx = start + it * stride;
     bool valid = idx < (long long)n;
     uint32_t key = valid ? a.first_keys[idx] : 0u;
+    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    const uint32_t dmask = (1u << a.digit_bits) - 1u;
     for (int p = 0; p < a.passes; ++p) {
-      uint32_t d = (key >> (8 * p)) & 255u;
-      uint32_t tag = valid ? d : 0x100u;
-      uint32_t peers = __match_any_sync(0xffffffffu, tag);
-      if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+      const uint32_t d = (key >> (a.digit_bits * p)) & dmask;
+      // a warp whose valid keys share the digit adds once (common for the
+      // high bytes of depth keys); otherwise every lane adds
+      const uint32_t d0 = __shfl_sync(0xffffffffu, d, __ffs(vmask | 1u) - 1);
+      if (__all_sync(0xffffffffu, !valid || d == d0)) {
+        if (lane == 0 && vmask) atomicAdd(&sh[p][d0], (uint32_t)__popc(vmask));
+      } else if (valid) {
+        atomicAdd(&sh[p][d], 1u);
+      }
     }
   }
   __syncthreads();
@@ -123,7 +131,11 @@ __global__ void __launch_bounds__(256) k_hist_scan(SortArgs a) {
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass) {
   __shared__ uint32_t s_wh[kSortThreads / 32][256];
   __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_dstart[256];
+  __shared__ uint32_t s_key[kSortPart];
+  __shared__ uint32_t s_val[kSortPart];
   __shared__ uint32_t s_part;
+  __shared__ uint32_t s_wsum[kSortThreads / 32];
   const uint32_t n = sort_n(a);
   const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
   unsigned long long *lb_next = a.lb + (long long)((pass + 1) & 1) * a.max_parts * 256;
@@ -143,7 +155,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
   uint32_t *kout = a.keys[(before + 1) & 1];
   uint32_t *vout = a.vals[(before + 1) & 1];
   const bool iota = vin == nullptr;
-  const int shift = 8 * pass;
+  const int shift = a.digit_bits * pass;
+  const uint32_t dmask = (1u << a.digit_bits) - 1u;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ltmask = lanemask_lt();
   const uint32_t *goff = a.hist + pass * 256;
@@ -168,7 +181,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
     for (int k = 0; k < kSortItems; ++k) {
       long long idx = wbase + k * 32 + lane;
       bool valid = idx < (long long)n;
-      uint32_t d = (key[k] >> shift) & 255u;
+      uint32_t d = (key[k] >> shift) & dmask;
       uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
       uint32_t before_w = valid ? s_wh[warp][d] : 0u;
       rank[k] = before_w + __popc(peers & ltmask);
@@ -207,17 +220,46 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
       }
       s_base[d] = goff[d] + (uint32_t)excl;
       lb_next[(long long)part * 256 + d] = 0ull;
+      // start of digit d inside the partition (block exclusive scan of tot)
+      uint32_t incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (lane == 31) s_wsum[warp] = incl;
+      __syncthreads();
+      uint32_t wofs = 0;
+#pragma unroll
+      for (int w = 0; w < kSortThreads / 32; ++w) wofs += w < warp ? s_wsum[w] : 0u;
+      s_dstart[d] = wofs + incl - tot;
     }
     __syncthreads();
+    // stage the partition in digit order, then write runs of equal digits
+    // to consecutive global addresses
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       long long idx = wbase + k * 32 + lane;
       if (idx < (long long)n) {
-        uint32_t d = (key[k] >> shift) & 255u;
-        uint32_t dst = s_base[d] + s_wh[warp][d] + rank[k];
+        uint32_t d = (key[k] >> shift) & dmask;
+        uint32_t lp = s_dstart[d] + s_wh[warp][d] + rank[k];
+        s_key[lp] = key[k];
+        s_val[lp] = val[k];
+      }
+    }
+    __syncthreads();
+    const long long pbase = (long long)part * kSortPart;
+    const uint32_t pcount = (uint32_t)min((long long)kSortPart, (long long)n - pbase);
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      const uint32_t lp = (uint32_t)(k * kSortThreads + tid);
+      if (lp < pcount) {
+        const uint32_t kk = s_key[lp];
+        const uint32_t d = (kk >> shift) & dmask;
+        const uint32_t dst = s_base[d] + (lp - s_dstart[d]);
         if (dst < n) {
-          kout[dst] = key[k];
-          vout[dst] = val[k];
+          kout[dst] = kk;
+          vout[dst] = s_val[lp];
         }
       }
     }
@@ -227,7 +269,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
 
 static int g_sort_blocks = 0;
 
-static cudaError_t run_sort(const SortArgs &a, cudaStream_t s) {
+static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = false) {
   if (g_sort_blocks == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -235,7 +277,7 @@ static cudaError_t run_sort(const SortArgs &a, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onesweep, kSortThreads, 0);
     g_sort_blocks = sms * (per > 0 ? per : 1);
   }
-  k_hist<<<g_sort_blocks, 256, 0, s>>>(a);
+  if (!hist_done) k_hist<<<g_sort_blocks, 256, 0, s>>>(a);
   k_hist_scan<<<1, 256, 0, s>>>(a);
   for (int p = 0; p < a.passes; ++p) k_onesweep<<<g_sort_blocks, kSortThreads, 0, s>>>(a, p);
   return cudaGetLastError();
@@ -325,35 +367,112 @@ struct EmitArgs {
   const unsigned long long *n_pairs;
   long long pair_capacity;
   uint32_t *pkey, *pval;
+  uint32_t *hist;                    // pair sort histograms [passes][256]
+  unsigned long long *lb;            // pair sort look-back buffer 0
+  int passes, digit_bits;
   uint32_t *status;
 };
 
+// Warp-synchronous: each lane takes one item of a 32-item group; items with
+// at most kSmallItem tiles are written by their own lane, larger ones by the
+// whole warp (lanes stride the rectangle, a ballot prefix gives positions).
+// The same kernel builds the pair sort's digit histograms and clears the
+// pair sort's first look-back buffer, so no separate pass reads the keys.
+constexpr uint32_t kSmallItem = 8;
+
 __global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
+  __shared__ uint32_t sh[4][256];
+  for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0u;
+  __syncthreads();
   unsigned long long nn = *a.n_items;
   const long long n = (long long)nn > a.item_capacity ? a.item_capacity : (long long)nn;
   const uint32_t *items = a.sorted_items[*a.sel];
+  const int lane = threadIdx.x & 31;
+  const uint32_t ltmask = (1u << lane) - 1u;
+  const uint32_t dmask = (1u << a.digit_bits) - 1u;
   if (blockIdx.x == 0 && threadIdx.x == 0 && (long long)*a.n_pairs > a.pair_capacity)
     set_status(a.status, GS_ERR_CAPACITY);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    const uint32_t j = items[k];
-    long long off = a.offsets[k];
-    const uint2 r = a.rect[j];
-    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-    const ViewDev &vd = a.views[a.view[j]];
-    const long long tb = vd.tile_base;
-    const uint8_t m = a.tile_level ? a.rec_m[j] : 0;
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) {
-        const long long t = tb + (long long)y * vd.tx + x;
-        if (a.tile_level && a.tile_level[t] > m) continue;
-        if (off < a.pair_capacity) {
-          a.pkey[off] = (uint32_t)t;
-          a.pval[off] = j;
+  const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+  const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  for (long long base = wid * 32; base < n; base += warps * 32) {
+    const long long k = base + lane;
+    const bool valid = k < n;
+    uint32_t j = 0, cnt = 0, off = 0, view = 0;
+    uint2 r = make_uint2(0u, 0u);
+    if (valid) {
+      j = items[k];
+      off = a.offsets[k];
+      cnt = a.count[j];
+      r = a.rect[j];
+      view = a.view[j];
+    }
+    // small items: one lane each
+    if (valid && cnt <= kSmallItem && cnt > 0) {
+      const ViewDev &vd = a.views[view];
+      const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+      const uint8_t m = a.tile_level ? a.rec_m[j] : 0;
+      long long o = off;
+      for (int y = y0; y <= y1; ++y)
+        for (int x = x0; x <= x1; ++x) {
+          const long long t = vd.tile_base + (long long)y * vd.tx + x;
+          if (a.tile_level && a.tile_level[t] > m) continue;
+          if (o < a.pair_capacity) {
+            a.pkey[o] = (uint32_t)t;
+            a.pval[o] = j;
+            for (int p = 0; p < a.passes; ++p)
+              atomicAdd(&sh[p][((uint32_t)t >> (a.digit_bits * p)) & dmask], 1u);
+          }
+          ++o;
         }
-        ++off;
+    }
+    // large items: the whole warp, one item at a time
+    uint32_t big = __ballot_sync(0xffffffffu, valid && cnt > kSmallItem);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t bj = __shfl_sync(0xffffffffu, j, src);
+      const uint32_t boff = __shfl_sync(0xffffffffu, off, src);
+      const uint32_t rx = __shfl_sync(0xffffffffu, r.x, src);
+      const uint32_t ry = __shfl_sync(0xffffffffu, r.y, src);
+      const uint32_t bview = __shfl_sync(0xffffffffu, view, src);
+      const ViewDev &vd = a.views[bview];
+      const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
+      const int w = x1 - x0 + 1;
+      const int area = w * (y1 - y0 + 1);
+      const uint8_t m = a.tile_level ? a.rec_m[bj] : 0;
+      long long run = boff;
+      for (int l0 = 0; l0 < area; l0 += 32) {
+        const int l = l0 + lane;
+        bool kept = l < area;
+        long long t = 0;
+        if (kept) {
+          t = vd.tile_base + (long long)(y0 + l / w) * vd.tx + (x0 + l % w);
+          if (a.tile_level && a.tile_level[t] > m) kept = false;
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, kept);
+        const long long o = run + __popc(b & ltmask);
+        if (kept && o < a.pair_capacity) {
+          a.pkey[o] = (uint32_t)t;
+          a.pval[o] = bj;
+          for (int p = 0; p < a.passes; ++p)
+            atomicAdd(&sh[p][((uint32_t)t >> (a.digit_bits * p)) & dmask], 1u);
+        }
+        run += __popc(b);
       }
+    }
   }
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.passes * 256; q += blockDim.x) {
+    const uint32_t c = (&sh[0][0])[q];
+    if (c) atomicAdd(&a.hist[q], c);
+  }
+  // clear the pair sort's first look-back buffer for the partitions it uses
+  unsigned long long kk = *a.n_pairs;
+  const long long K = (long long)kk > a.pair_capacity ? a.pair_capacity : (long long)kk;
+  const long long nparts = (K + kSortPart - 1) / kSortPart;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nparts * 256;
+       q += (long long)gridDim.x * blockDim.x)
+    a.lb[q] = 0ull;
 }
 
 // ---- per-tile ranges ------------------------------------------------------
@@ -410,6 +529,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   d.lb = region<unsigned long long>(p, ws, R_LOOKBACK);
   d.max_parts = max_parts;
   d.passes = 4;
+  d.digit_bits = 8;
   d.status = &hdr->status;
   e = run_sort(d, s);
   if (e != cudaSuccess) return e;
@@ -427,7 +547,9 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.n_pairs = &hdr->n_pairs;
   sa.status = &hdr->status;
   k_offsets<<<g_sort_blocks, 256, 0, s>>>(sa);
-  // 3. emit pairs
+  // 3. emit pairs (+ the pair sort's histograms)
+  const int pair_passes = (p->tile_bits + 7) / 8;
+  const int pair_bits = (p->tile_bits + pair_passes - 1) / pair_passes;
   EmitArgs ea = {};
   ea.sorted_items[0] = d.vals[0];
   ea.sorted_items[1] = d.vals[1];
@@ -445,6 +567,10 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.pair_capacity = p->max_pairs;
   ea.pkey = region<uint32_t>(p, ws, R_PKEY_A);
   ea.pval = region<uint32_t>(p, ws, R_PVAL_A);
+  ea.hist = &hdr->hist[1][0][0];
+  ea.lb = d.lb;
+  ea.passes = pair_passes;
+  ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
   k_emit<<<g_sort_blocks, 256, 0, s>>>(ea);
   // 4. stable sort of the pairs by tile
@@ -463,9 +589,10 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.tickets = &hdr->ticket[5];
   t.lb = d.lb;
   t.max_parts = max_parts;
-  t.passes = (p->tile_bits + 7) / 8;
+  t.passes = pair_passes;
+  t.digit_bits = pair_bits;
   t.status = &hdr->status;
-  e = run_sort(t, s);
+  e = run_sort(t, s, /*hist_done=*/true);
   if (e != cudaSuccess) return e;
   // 5. ranges (the pointer pair lives in the header's spare words)
   uint2 *ranges = region<uint2>(p, ws, R_RANGES);
@@ -563,6 +690,7 @@ extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_
   k_static_set_count<<<1, 1, 0, stream>>>(h, (unsigned long long)n);
   SortArgs a = {};
   a.passes = (key_bits + 7) / 8;
+  a.digit_bits = (key_bits + a.passes - 1) / a.passes;
   a.first_keys = keys_in;
   a.first_vals = vals_in;
   // every pass runs, so pass p writes buffer (p + 1) & 1: put the caller's
