@@ -56,7 +56,7 @@ extern "C" {
 typedef int32_t gs_status;
 #define GS_OK 0
 #define GS_ERR_INVALID_ARG 1 /* bad host-side argument; nothing enqueued */
-#define GS_ERR_CAPACITY 2    /* more visible items or pairs than the plan holds */
+#define GS_ERR_CAPACITY 2    /* more tile/point pairs than the plan holds */
 #define GS_ERR_TIMEOUT 3     /* a bounded device-side wait gave up */
 #define GS_ERR_CUDA 4        /* a CUDA runtime call failed */
 #define GS_ERR_UNSUPPORTED 5 /* valid but not supported (e.g. SH degree > 3) */
@@ -117,8 +117,8 @@ typedef struct gs_config {
   int32_t chunk;         /* heavy-tile chunk length in points; 0 = default, <0 = off */
   int32_t flags;         /* GS_FLAG_* */
   int32_t max_levels;    /* largest foveation L the plan must hold; 0 = 4 */
-  int64_t max_visible;   /* capacity of visible (view, point) items; 0 = N*V */
-  int64_t max_pairs;     /* capacity of tile/point pairs; 0 = 4 * max_visible */
+  int64_t reserved2;     /* unused; item slots are always N*V */
+  int64_t max_pairs;     /* capacity of tile/point pairs; 0 = 4 * N * V */
 } gs_config;
 
 #define GS_FLAG_FOVEATED 1u  /* reserve foveation state (levels, per-level params) */
@@ -221,12 +221,13 @@ gs_status gs_clear_error(const gs_plan *plan, void *ws, cudaStream_t stream);
 
 /* Location of a workspace region, for tests and debugging.  region is one
  * of GS_REGION_*; offset and bytes are relative to the workspace base.
- * Visible items j = 0..M-1 are numbered point-major: point i's visible
- * views in view order, points in index order. */
-#define GS_REGION_ITEM_GID 1     /* uint32 (M)  point index of visible item j */
-#define GS_REGION_ITEM_VIEW 2    /* uint32 (M)  view of visible item j */
-#define GS_REGION_ITEM_DEPTH 3   /* uint32 (M)  float bits of camera z */
-#define GS_REGION_ITEM_COUNT 4   /* uint32 (M)  kept tile pairs of item j */
+ * Every (view v, point i) owns the item slot j = i * V + v.  Slots of items
+ * that are not visible hold depth key 0xffffffff and a zero pair count; the
+ * other fields of such slots are unspecified. */
+#define GS_REGION_ITEM_GID 1     /* uint32 (N*V) point index of slot j */
+#define GS_REGION_ITEM_VIEW 2    /* uint32 (N*V) view of slot j */
+#define GS_REGION_ITEM_DEPTH 3   /* uint32 (N*V) float bits of camera z */
+#define GS_REGION_ITEM_COUNT 4   /* uint32 (N*V) kept tile pairs of slot j */
 #define GS_REGION_RANGES 7       /* uint32 (T,2) [start, end) per global tile */
 #define GS_REGION_TILE_LEVEL 8   /* uint8  (T)  FR filter level per global tile */
 gs_status gs_ws_region(const gs_plan *plan, int32_t region, size_t *offset,
@@ -235,7 +236,8 @@ gs_status gs_ws_region(const gs_plan *plan, int32_t region, size_t *offset,
 /* Device pointers to the K sorted pairs of the last gs_bin_sort: global
  * tile id and visible item j of each pair, ordered by (tile, depth, point
  * index).  Synchronises `stream` (the sort picks its output buffer on the
- * device).  Pointers stay valid until the next gs_bin_sort. */
+ * device).  Pointers stay valid until the next gs_bin_sort.  The item of
+ * a pair is its slot j = i * V + v (see GS_REGION_ITEM_*). */
 gs_status gs_sorted_pairs(const gs_plan *plan, const void *ws, cudaStream_t stream,
                           const uint32_t **pair_tile, const uint32_t **pair_item);
 

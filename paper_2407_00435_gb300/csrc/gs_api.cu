@@ -64,8 +64,9 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   p->tiles_total = tiles;
   p->pixels_total = pixels;
   long long items = n * (long long)V;
-  p->max_visible = c.max_visible > 0 ? (c.max_visible < items ? c.max_visible : items) : items;
-  if (p->max_visible > 0xffffffffll) return GS_ERR_INVALID_ARG;
+  // records live at fixed slots i * V + v, so every (view, point) has one
+  p->max_visible = items;
+  if (p->max_visible > 0xffffffffll) return GS_ERR_INVALID_ARG;   // slots are uint32
   long long mp = c.max_pairs > 0 ? c.max_pairs : 4 * p->max_visible;
   if (mp > 0xfffffffell) mp = 0xfffffffell;
   if (mp < 1) mp = 1;
@@ -95,9 +96,10 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   b[R_DKEY_A] = b[R_DKEY_B] = b[R_DVAL_A] = b[R_DVAL_B] = 4 * (size_t)M;
   b[R_OFFSETS] = 4 * (size_t)M;
   b[R_PKEY_A] = b[R_PKEY_B] = b[R_PVAL_A] = b[R_PVAL_B] = 4 * (size_t)K;
+  b[R_BIGQ] = 4 * (size_t)M;
   b[R_RANGES] = 8 * (size_t)T;
   b[R_WORK] = 4 * (size_t)T;
-  b[R_SCAN] = 8 * (size_t)((n + kProjThreads - 1) / kProjThreads + (M + kSortPart - 1) / kSortPart + 1);
+  b[R_SCAN] = 8 * (size_t)((M + kSortPart - 1) / kSortPart + 1);
   b[R_LOOKBACK] = 2 * 256 * 8 * (size_t)(parts > 0 ? parts : 1);
   b[R_GRAD_ITEM] = bwd ? 16 * sizeof(float) * (size_t)M : 0;
   b[R_GRAD_LV] = (bwd && fov) ? 4 * sizeof(float) * (size_t)(max_levels - 1) * (size_t)M : 0;
@@ -168,9 +170,6 @@ gs_status gs_project(gs_plan *p, void *ws, size_t ws_bytes, const gs_scene *scen
   Hdr *hdr = region<Hdr>(p, ws, R_HDR);
   // a new frame: status word, counters and tickets restart
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(Hdr), stream);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
-  const size_t proj_parts = (size_t)((p->n + kProjThreads - 1) / kProjThreads);
-  e = cudaMemsetAsync(region<char>(p, ws, R_SCAN), 0, 8 * proj_parts, stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   if ((e = launch_views(p, ws, stream)) != cudaSuccess) return GS_ERR_CUDA;
   if ((e = launch_tile_levels(p, ws, stream)) != cudaSuccess) return GS_ERR_CUDA;

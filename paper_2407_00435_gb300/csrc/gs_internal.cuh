@@ -41,15 +41,16 @@ enum Region : int {
   R_REC_DEPTH,   // u32 float bits of camera z
   R_REC_COUNT,   // u32 kept tile pairs
   R_REC_RECT,    // uint2 packed tile rect (x0 | x1 << 16, y0 | y1 << 16)
-  R_REC_GID,     // u32 point index
+  R_REC_GID,     // u32 point index (item slot j = i * V + v)
   R_REC_VIEW,    // u32 view index
   R_REC_M,       // u8 quality bound (foveated)
   R_DKEY_A, R_DKEY_B, R_DVAL_A, R_DVAL_B,   // depth sort ping-pong (M)
   R_OFFSETS,     // u32 exclusive pair offsets in depth order (M)
   R_PKEY_A, R_PKEY_B, R_PVAL_A, R_PVAL_B,   // pair sort ping-pong (K)
+  R_BIGQ,        // u32 items with many tiles, expanded by a separate kernel (M)
   R_RANGES,      // uint2 per tile
   R_WORK,        // u32 render work list (tiles, heavy first)
-  R_SCAN,        // u64 lookback slots of single-value scans
+  R_SCAN,        // u64 look-back slots of the pair-offset scan
   R_LOOKBACK,    // u64 radix lookback slots, two buffers
   R_GRAD_ITEM,   // float per item gradient scratch (backward)
   R_GRAD_LV,     // float per (level, item) gradient scratch (backward, foveated)
@@ -60,7 +61,8 @@ enum Region : int {
 struct Hdr {
   uint32_t status;
   uint32_t pad0;
-  unsigned long long n_visible;   // M (raw)
+  unsigned long long n_visible;   // M: visible (view, point) items
+  unsigned long long n_items;     // item slots N * V (visible or not)
   unsigned long long n_pairs;     // K (raw)
   unsigned long long n_nonfinite;
   unsigned long long n_evals;     // (pixel, point) evaluations of the last stats render
@@ -69,6 +71,8 @@ struct Hdr {
   uint32_t sel_depth;             // buffer holding the sorted depth order (0 = A)
   uint32_t sel_pair;              // buffer holding the sorted pairs (0 = A)
   uint32_t skip[8];               // per-pass "digit constant" flags
+  uint32_t big_count;             // items queued for the large-item emit
+  uint32_t big_ticket;            // next queued item to expand
   uint32_t hist[2][4][256];       // digit histograms: [sort][pass][digit]
 };
 

@@ -76,14 +76,16 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
   __shared__ int s_m[FOV ? NT : 1];
   __shared__ float4 s_lv[MV ? NT : 1][MV ? kMvMaxLevels - 1 : 1];
   __shared__ float s_g[NT][9];   // per batch slot: dmu(2) dQ(3) do(1) dc(3)
+  __shared__ float4 s_ea[NT], s_eb[NT];   // evaluation records (as in the forward)
   __shared__ int s_maxlast;
 
   const long long t = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const ViewDev vd = a.views[find_view(a.views, a.V, t)];
   const int local = (int)(t - vd.tile_base);
   const int tx0 = (local % vd.tx) * B, ty0 = (local / vd.tx) * B;
-  const int lx = tid % B, ly = tid / B;
+  const int lx = (warp % WarpGeom<B, 1>::kWx) * 8 + (lane & 7);
+  const int ly = (warp / WarpGeom<B, 1>::kWx) * 4 + (lane >> 3);
   const int x = tx0 + lx, y = ty0 + ly;
   const bool inside = x < vd.W && y < vd.H;
   const float px = (float)lx + 0.5f, py = (float)ly + 0.5f;
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
       const uint32_t gid = a.rec_gid[j];
       s_op[tid] = a.opac[gid];
       if (FOV) s_m[tid] = a.rec_m[j];
+      float Fmax = col.w;
       if (MV) {
         const float4 rest = a.rec_rest[j];
         for (int l = 2; l <= a.L; ++l) {
@@ -156,16 +159,25 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
           }
           // .w keeps log2 o as in the forward
           s_lv[tid][l - 2] = make_float4(c.x, c.y, c.z, a.opacity_lv ? log2f(o) : col.w);
+          Fmax = fmaxf(Fmax, s_lv[tid][l - 2].w);
         }
       }
+      float4 ea, eb;
+      make_eval(s_mean[tid].x, s_mean[tid].y, s_shape[tid], col.w,
+                warp_mask<B, 1>(s_mean[tid].x, s_mean[tid].y, s_shape[tid], Fmax), ea, eb);
+      s_ea[tid] = ea;
+      s_eb[tid] = eb;
     }
     __syncthreads();
     for (int q = (int)cnt - 1; q >= 0; --q) {
+      const float4 eb = s_eb[q];
+      if (!((__float_as_uint(eb.w) >> warp) & 1u)) continue;   // cannot reach this warp's pixels
       const int pos = (int)(lo - rg.x) + q;
       const float2 mu = s_mean[q];
       const float4 sh = s_shape[q];
-      float dx, dy, t1, t2;
-      const float gq = log2_alpha(px, py, mu, sh, 0.0f, dx, dy, t1, t2);
+      float t1, t2;
+      const float sq = eval_s(px, py, s_ea[q], eb, t1, t2);
+      const float dx = px - mu.x, dy = py - mu.y;
       const int m = FOV ? s_m[q] : 0;
       float gmx = 0.f, gmy = 0.f, gqa = 0.f, gqb = 0.f, gqc = 0.f, gop = 0.f, gcr = 0.f,
             gcg = 0.f, gcb = 0.f;
@@ -177,9 +189,9 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
         if (FOV && m < L_here) continue;
         const bool own = MV && L_here >= 2;
         const float4 c = own ? s_lv[q][L_here - 2] : s_col[q];
-        const float p = __fadd_rn(gq, c.w);
-        if (p < kLog2AlphaMin) continue;
-        const float al = alpha_of(p);
+        const float r2 = own ? __fsub_rn(c.w, kLog2AlphaMin) : eb.z;
+        if (!(sq <= r2)) continue;
+        const float al = alpha_of(__fsub_rn(c.w, sq));
         const float om = 1.0f - al;
         const float Tb = S.T / om;
         const float w = al * Tb;
@@ -255,7 +267,7 @@ struct PBwdArgs {
   const ViewDev *views;
   const unsigned long long *n_items;
   long long max_visible;
-  const uint32_t *rec_gid, *rec_view;
+  const uint32_t *rec_gid, *rec_view, *rec_depth;
   const float4 *rec_shape;
   const float *grad_item, *grad_lv;
   int L;
@@ -314,6 +326,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(PBwdArgs a) {
   const long long M = (long long)nn > a.max_visible ? a.max_visible : (long long)nn;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < M;
        j += (long long)gridDim.x * blockDim.x) {
+    if (a.rec_depth[j] == 0xffffffffu) continue;   // invisible slot
     const float *gi = a.grad_item + j * kGradItem;
     const float gmx = gi[0], gmy = gi[1], gqa = gi[2], gqb = gi[3], gqc = gi[4], gop = gi[5];
     const float gc[3] = {gi[6], gi[7], gi[8]};
@@ -585,7 +598,8 @@ cudaError_t launch_backward(const gs_plan *p, void *ws, const float *dL, const f
   b.opac = p->scene.opacities; b.sh = p->scene.sh;
   b.cams = p->cams;
   b.views = a.views;
-  b.n_items = &hdr->n_visible;
+  b.n_items = &hdr->n_items;
+  b.rec_depth = region<uint32_t>(p, ws, R_REC_DEPTH);
   b.max_visible = p->max_visible;
   b.rec_gid = a.rec_gid;
   b.rec_view = region<uint32_t>(p, ws, R_REC_VIEW);

@@ -28,7 +28,7 @@ struct FovArgs {
 
 __global__ void k_views(const gs_camera *cams, int V, int tile, FovArgs fa, int has_fov,
                         ViewDev *views, Hdr *hdr, long long tiles_total,
-                        long long pixels_total) {
+                        long long pixels_total, unsigned long long n_items) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   long long tb = 0, pb = 0;
   for (int v = 0; v < V; ++v) {
@@ -58,6 +58,7 @@ __global__ void k_views(const gs_camera *cams, int V, int tile, FovArgs fa, int 
   }
   // the device cameras must describe the image sizes the plan was made for
   if (tb != tiles_total || pb != pixels_total) set_status(&hdr->status, GS_ERR_INVALID_ARG);
+  hdr->n_items = n_items;
 }
 
 cudaError_t launch_views(const gs_plan *p, void *ws, cudaStream_t s) {
@@ -70,7 +71,8 @@ cudaError_t launch_views(const gs_plan *p, void *ws, cudaStream_t s) {
     fa.view_fov = p->fov.view_fov;
   }
   k_views<<<1, 32, 0, s>>>(p->cams, p->V, p->tile, fa, p->has_fov, region<ViewDev>(p, ws, R_VIEWS),
-                           region<Hdr>(p, ws, R_HDR), p->tiles_total, p->pixels_total);
+                           region<Hdr>(p, ws, R_HDR), p->tiles_total, p->pixels_total,
+                           (unsigned long long)p->max_visible);
   return cudaGetLastError();
 }
 
@@ -152,7 +154,6 @@ struct ProjArgs {
   const uint8_t *tile_level;   // null unless foveated
   const uint8_t *bound_m;      // null unless foveated
   Hdr *hdr;
-  unsigned long long *scan_slots;
   long long max_visible;
   float4 *rec_mean, *rec_shape, *rec_color, *rec_rest;
   uint32_t *rec_depth, *rec_count, *rec_gid, *rec_view;
@@ -518,21 +519,21 @@ __device__ __forceinline__ void write_rec(const ProjArgs &a, unsigned long long 
   a.rec_view[j] = v;
 }
 
-template <int S, bool ONE_VIEW>
+// One thread per point, looping over the views.  Records live at fixed
+// slots j = i * V + v (point-major): no compaction pass, so no look-back
+// chain.  Invisible slots get depth key 0xffffffff (they sort after every
+// visible item) and zero pairs; the number of visible items is counted with
+// one atomic per block.
+template <int S>
 __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
   __shared__ ProjSmem<S> sm;
-  __shared__ uint32_t s_part;
-  __shared__ unsigned long long s_base;
-  __shared__ uint32_t s_wsum[kProjThreads / 32];
-  __shared__ uint32_t s_nonfinite;
+  __shared__ uint32_t s_vis, s_nonfinite;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    s_part = atomicAdd(&a.hdr->ticket[0], 1u);
+    s_vis = 0;
     s_nonfinite = 0;
   }
-  __syncthreads();
-  const uint32_t part = s_part;
-  const long long row0 = (long long)part * kProjThreads;
+  const long long row0 = (long long)blockIdx.x * kProjThreads;
   const int cnt_rows = (int)min((long long)kProjThreads, a.n - row0);
   // coalesced staging of this block's points
   stage_rows(&sm.sh[0][0], ProjSmem<S>::kSh, a.sh, row0, cnt_rows, S * 3);
@@ -542,90 +543,37 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
   stage_rows(&sm.op[0], 1, a.opac, row0, cnt_rows, 1);
   __syncthreads();
   const long long i = row0 + tid;
-  const bool valid = tid < cnt_rows;
-
-  float mu[3] = {0, 0, 0}, sc[3] = {1, 1, 1}, q[4] = {1, 0, 0, 0};
-  bool fin = false;
-  if (valid) {
+  uint32_t nvis = 0;
+  if (tid < cnt_rows) {
+    float mu[3], sc[3], q[4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) { mu[k] = sm.mu[tid][k]; sc[k] = sm.sc[tid][k]; }
 #pragma unroll
     for (int k = 0; k < 4; ++k) q[k] = sm.q[tid][k];
-    fin = all_finite(mu, 3) && all_finite(sc, 3) && all_finite(q, 4) && isfinite(sm.op[tid]) &&
-          all_finite(sm.sh[tid], S * 3);
-  }
-  if (valid && !fin) atomicAdd(&s_nonfinite, (uint32_t)a.V);
-
-  // phase 1: visibility per view -> count of records (one view: the whole
-  // record is computed here and kept in registers)
-  uint32_t cnt = 0;
-  Rec rec1;
-  if (valid && fin) {
-    if (ONE_VIEW) {
-      const gs_camera cam = a.cams[0];
-      const ViewDev &vd = a.views[0];
+    const bool fin = all_finite(mu, 3) && all_finite(sc, 3) && all_finite(q, 4) &&
+                     isfinite(sm.op[tid]) && all_finite(sm.sh[tid], S * 3);
+    if (!fin) atomicAdd(&s_nonfinite, (uint32_t)a.V);
+    for (int v = 0; v < a.V; ++v) {
+      const long long j = i * a.V + v;
+      const gs_camera cam = a.cams[v];
+      const ViewDev &vd = a.views[v];
       Keyed k;
-      if (keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) {
-        project_value<S>(a, sm, tid, i, mu, cam, vd, k, rec1);
-        cnt = 1;
-      }
-    } else {
-      for (int v = 0; v < a.V; ++v) {
-        const ViewDev &vd = a.views[v];
-        Keyed k;
-        cnt += keyed_project(mu, sc, q, a.cams[v], a.tile, vd.tx, vd.ty, k) ? 1u : 0u;
+      if (fin && keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) {
+        Rec r;
+        project_value<S>(a, sm, tid, i, mu, cam, vd, k, r);
+        write_rec(a, (unsigned long long)j, r, (uint32_t)i, (uint32_t)v);
+        ++nvis;
+      } else {
+        a.rec_depth[j] = 0xffffffffu;
+        a.rec_count[j] = 0u;
       }
     }
   }
-  // block exclusive scan of cnt, then the partition's global offset
-  const int lane = tid & 31, warp = tid >> 5;
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) s_wsum[warp] = incl;
+  if (nvis) atomicAdd(&s_vis, nvis);
   __syncthreads();
-  uint32_t woff = 0, total = 0;
-#pragma unroll
-  for (int w = 0; w < kProjThreads / 32; ++w) {
-    uint32_t t = s_wsum[w];
-    if (w < warp) woff += t;
-    total += t;
-  }
   if (tid == 0) {
-    unsigned long long excl = lookback_single(a.scan_slots, part, total, &a.hdr->status);
-    s_base = excl;
-    const uint32_t nparts = (uint32_t)((a.n + kProjThreads - 1) / kProjThreads);
-    if (part == nparts - 1) a.hdr->n_visible = excl + total;
+    if (s_vis) atomicAdd(&a.hdr->n_visible, (unsigned long long)s_vis);
     if (s_nonfinite) atomicAdd(&a.hdr->n_nonfinite, (unsigned long long)s_nonfinite);
-  }
-  __syncthreads();
-  unsigned long long j = s_base + woff + (incl - cnt);
-  if (cnt == 0) return;
-  if (ONE_VIEW) {
-    if ((long long)j >= a.max_visible) {
-      set_status(&a.hdr->status, GS_ERR_CAPACITY);
-      return;
-    }
-    write_rec(a, j, rec1, (uint32_t)i, 0u);
-    return;
-  }
-  // phase 2: full projection of the visible views, written at j, j+1, ...
-  for (int v = 0; v < a.V; ++v) {
-    const gs_camera cam = a.cams[v];
-    const ViewDev &vd = a.views[v];
-    Keyed k;
-    if (!keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) continue;
-    if ((long long)j >= a.max_visible) {
-      set_status(&a.hdr->status, GS_ERR_CAPACITY);
-      return;
-    }
-    Rec r;
-    project_value<S>(a, sm, tid, i, mu, cam, vd, k, r);
-    write_rec(a, j, r, (uint32_t)i, (uint32_t)v);
-    ++j;
   }
 }
 
@@ -646,7 +594,6 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
   a.tile_level = p->has_fov ? region<uint8_t>(p, ws, R_TILE_LEVEL) : nullptr;
   a.bound_m = p->has_fov ? p->fov.bound_m : nullptr;
   a.hdr = region<Hdr>(p, ws, R_HDR);
-  a.scan_slots = region<unsigned long long>(p, ws, R_SCAN);
   a.max_visible = p->max_visible;
   a.rec_mean = region<float4>(p, ws, R_REC_MEAN);
   a.rec_shape = region<float4>(p, ws, R_REC_SHAPE);
@@ -659,16 +606,11 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
   a.rec_rect = region<uint2>(p, ws, R_REC_RECT);
   a.rec_m = p->bytes[R_REC_M] ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
   unsigned grid = (unsigned)((p->n + kProjThreads - 1) / kProjThreads);
-  const bool one = p->V == 1;
   switch (a.S) {
-    case 1: one ? k_project<1, true><<<grid, kProjThreads, 0, s>>>(a)
-                : k_project<1, false><<<grid, kProjThreads, 0, s>>>(a); break;
-    case 4: one ? k_project<4, true><<<grid, kProjThreads, 0, s>>>(a)
-                : k_project<4, false><<<grid, kProjThreads, 0, s>>>(a); break;
-    case 9: one ? k_project<9, true><<<grid, kProjThreads, 0, s>>>(a)
-                : k_project<9, false><<<grid, kProjThreads, 0, s>>>(a); break;
-    default: one ? k_project<16, true><<<grid, kProjThreads, 0, s>>>(a)
-                 : k_project<16, false><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 1: k_project<1><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 4: k_project<4><<<grid, kProjThreads, 0, s>>>(a); break;
+    case 9: k_project<9><<<grid, kProjThreads, 0, s>>>(a); break;
+    default: k_project<16><<<grid, kProjThreads, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }

@@ -206,15 +206,33 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
         st_release_u64(slot, kFlagPre | tot);
       } else {
         st_release_u64(slot, kFlagAgg | tot);
+        // walk back kLbVec slots per step: the loads of one step are
+        // independent, so the chain costs one memory latency per kLbVec
+        // predecessors
+        constexpr int kLbVec = 16;
         long long q = (long long)part - 1;
         int spins = 0;
-        while (q >= 0) {
-          unsigned long long wv = ld_acquire_u64(lb_cur + q * 256 + d);
-          unsigned long long f = wv >> 62;
-          if (f == 2ull) { excl += wv & kValMask; break; }
-          if (f == 1ull) { excl += wv & kValMask; --q; continue; }
-          if (++spins > kSpinLimit) { set_status(a.status, GS_ERR_TIMEOUT); break; }
-          __nanosleep(20);
+        bool done = false;
+        while (!done && q >= 0) {
+          unsigned long long wv[kLbVec];
+#pragma unroll
+          for (int v = 0; v < kLbVec; ++v)
+            wv[v] = q - v >= 0 ? ld_relaxed_u64(lb_cur + (q - v) * 256 + d) : (kFlagPre | 0ull);
+          int used = 0;
+#pragma unroll
+          for (int v = 0; v < kLbVec; ++v) {
+            if (done || used < v) continue;       // stopped earlier in this step
+            const unsigned long long f = wv[v] >> 62;
+            if (f == 0ull) continue;               // not ready: retry from here
+            excl += wv[v] & kValMask;
+            if (f == 2ull) done = true;
+            used = v + 1;
+          }
+          q -= used;
+          if (!done && used < kLbVec) {
+            if (++spins > kSpinLimit) { set_status(a.status, GS_ERR_TIMEOUT); break; }
+            __nanosleep(20);
+          }
         }
         st_release_u64(slot, kFlagPre | (excl + tot));
       }
@@ -268,6 +286,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
 }
 
 static int g_sort_blocks = 0;
+static int g_stream_blocks = 0;   // grid of the streaming kernels (emit, offsets, ranges, hist)
 
 static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = false) {
   if (g_sort_blocks == 0) {
@@ -276,8 +295,9 @@ static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onesweep, kSortThreads, 0);
     g_sort_blocks = sms * (per > 0 ? per : 1);
+    g_stream_blocks = sms * 8;
   }
-  if (!hist_done) k_hist<<<g_sort_blocks, 256, 0, s>>>(a);
+  if (!hist_done) k_hist<<<g_stream_blocks, 256, 0, s>>>(a);
   k_hist_scan<<<1, 256, 0, s>>>(a);
   for (int p = 0; p < a.passes; ++p) k_onesweep<<<g_sort_blocks, kSortThreads, 0, s>>>(a, p);
   return cudaGetLastError();
@@ -334,10 +354,12 @@ __global__ void __launch_bounds__(256) k_offsets(ScanArgs a) {
       if (w < warp) woff += s_w[w];
       total += s_w[w];
     }
-    if (tid == 0) {
-      unsigned long long ex = lookback_single(a.slots, part, total, a.status);
-      s_base = ex;
-      if ((long long)part == nparts - 1) *a.n_pairs = ex + total;
+    if (warp == 0) {
+      unsigned long long ex = lookback_single_warp(a.slots, part, total, a.status);
+      if (lane == 0) {
+        s_base = ex;
+        if ((long long)part == nparts - 1) *a.n_pairs = ex + total;
+      }
     }
     __syncthreads();
     unsigned long long run = s_base + woff + incl - tsum;
@@ -367,33 +389,59 @@ struct EmitArgs {
   const unsigned long long *n_pairs;
   long long pair_capacity;
   uint32_t *pkey, *pval;
+  uint32_t *bigq;                    // queue of items with more than kBigItem tiles
+  uint32_t *big_count, *big_ticket;
   uint32_t *hist;                    // pair sort histograms [passes][256]
   unsigned long long *lb;            // pair sort look-back buffer 0
   int passes, digit_bits;
   uint32_t *status;
 };
 
-// Warp-synchronous: each lane takes one item of a 32-item group; items with
-// at most kSmallItem tiles are written by their own lane, larger ones by the
-// whole warp (lanes stride the rectangle, a ballot prefix gives positions).
-// The same kernel builds the pair sort's digit histograms and clears the
-// pair sort's first look-back buffer, so no separate pass reads the keys.
+// Warp-synchronous: each lane takes one item of a 32-item group.  The
+// group's pairs occupy one contiguous output range; when it holds at most
+// kStage pairs they are assembled in shared memory (small items by their own
+// lane, large ones by the whole warp) and written back with coalesced
+// stores, the pair sort's digit histograms being taken during that flush.
+// Wider groups write directly.  The kernel also clears the pair sort's
+// first look-back buffer, so no separate pass reads the keys.
 constexpr uint32_t kSmallItem = 8;
+constexpr uint32_t kBigItem = 64;   // larger items go to k_emit_big
+constexpr int kStage = 768;
+constexpr int kEmitThreads = 128;
 
-__global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
+__device__ __forceinline__ void hist_add_warp(uint32_t (*sh)[256], bool on, uint32_t t,
+                                              int passes, int bits, uint32_t dmask, int lane) {
+  const uint32_t m = __ballot_sync(0xffffffffu, on);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t dg = (t >> (bits * p)) & dmask;
+    const uint32_t d0 = __shfl_sync(0xffffffffu, dg, leader);
+    if (__all_sync(0xffffffffu, !on || dg == d0)) {
+      if (lane == leader) atomicAdd(&sh[p][d0], (uint32_t)__popc(m));
+    } else if (on) {
+      atomicAdd(&sh[p][dg], 1u);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
   __shared__ uint32_t sh[4][256];
+  __shared__ uint32_t s_t[kEmitThreads / 32][kStage];
+  __shared__ uint32_t s_v[kEmitThreads / 32][kStage];
   for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0u;
   __syncthreads();
   unsigned long long nn = *a.n_items;
   const long long n = (long long)nn > a.item_capacity ? a.item_capacity : (long long)nn;
   const uint32_t *items = a.sorted_items[*a.sel];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const uint32_t ltmask = (1u << lane) - 1u;
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
   if (blockIdx.x == 0 && threadIdx.x == 0 && (long long)*a.n_pairs > a.pair_capacity)
     set_status(a.status, GS_ERR_CAPACITY);
   const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-  const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + wl;
+  uint32_t *st = s_t[wl], *sv = s_v[wl];
   for (long long base = wid * 32; base < n; base += warps * 32) {
     const long long k = base + lane;
     const bool valid = k < n;
@@ -406,6 +454,24 @@ __global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
       r = a.rect[j];
       view = a.view[j];
     }
+    // items with more than kBigItem tiles are queued for k_emit_big, whose
+    // warps take them one at a time (they cluster in depth order and would
+    // otherwise leave a few warps with most of the work)
+    const bool huge = valid && cnt > kBigItem;
+    const uint32_t hb = __ballot_sync(0xffffffffu, huge);
+    const bool any_huge = hb != 0u;
+    if (any_huge) {
+      // one queue reservation per warp
+      uint32_t base = 0;
+      if (lane == __ffs(hb) - 1) base = atomicAdd(a.big_count, (uint32_t)__popc(hb));
+      base = __shfl_sync(0xffffffffu, base, __ffs(hb) - 1);
+      if (huge) a.bigq[base + __popc(hb & ltmask)] = (uint32_t)k;
+    }
+    // the group's output range [g0, g1)
+    const uint32_t g0 = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t last = 31 - __clz(__ballot_sync(0xffffffffu, valid));
+    const uint32_t g1 = __shfl_sync(0xffffffffu, off + cnt, last);
+    const bool staged = !any_huge && g1 - g0 <= (uint32_t)kStage;
     // small items: one lane each
     if (valid && cnt <= kSmallItem && cnt > 0) {
       const ViewDev &vd = a.views[view];
@@ -416,7 +482,10 @@ __global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
         for (int x = x0; x <= x1; ++x) {
           const long long t = vd.tile_base + (long long)y * vd.tx + x;
           if (a.tile_level && a.tile_level[t] > m) continue;
-          if (o < a.pair_capacity) {
+          if (staged) {
+            st[o - g0] = (uint32_t)t;
+            sv[o - g0] = j;
+          } else if (o < a.pair_capacity) {
             a.pkey[o] = (uint32_t)t;
             a.pval[o] = j;
             for (int p = 0; p < a.passes; ++p)
@@ -426,7 +495,7 @@ __global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
         }
     }
     // large items: the whole warp, one item at a time
-    uint32_t big = __ballot_sync(0xffffffffu, valid && cnt > kSmallItem);
+    uint32_t big = __ballot_sync(0xffffffffu, valid && cnt > kSmallItem && cnt <= kBigItem);
     while (big) {
       const int src = __ffs(big) - 1;
       big &= big - 1;
@@ -449,16 +518,40 @@ __global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
           t = vd.tile_base + (long long)(y0 + l / w) * vd.tx + (x0 + l % w);
           if (a.tile_level && a.tile_level[t] > m) kept = false;
         }
+        // every lane takes part in the ballots (never inside && or ?:)
         const uint32_t b = __ballot_sync(0xffffffffu, kept);
         const long long o = run + __popc(b & ltmask);
-        if (kept && o < a.pair_capacity) {
-          a.pkey[o] = (uint32_t)t;
-          a.pval[o] = bj;
-          for (int p = 0; p < a.passes; ++p)
-            atomicAdd(&sh[p][((uint32_t)t >> (a.digit_bits * p)) & dmask], 1u);
+        if (staged) {
+          if (kept) {
+            st[o - g0] = (uint32_t)t;
+            sv[o - g0] = bj;
+          }
+        } else {
+          const bool wr = kept && o < a.pair_capacity;
+          if (wr) {
+            a.pkey[o] = (uint32_t)t;
+            a.pval[o] = bj;
+          }
+          hist_add_warp(sh, wr, (uint32_t)t, a.passes, a.digit_bits, dmask, lane);
         }
         run += __popc(b);
       }
+    }
+    // coalesced flush of a staged group
+    if (staged) {
+      __syncwarp();
+      for (uint32_t l0 = 0; l0 < g1 - g0; l0 += 32) {
+        const uint32_t l = l0 + lane;
+        const long long o = (long long)g0 + l;
+        const bool wr = l < g1 - g0 && o < a.pair_capacity;
+        const uint32_t t = wr ? st[l] : 0u;
+        if (wr) {
+          a.pkey[o] = t;
+          a.pval[o] = sv[l];
+        }
+        hist_add_warp(sh, wr, t, a.passes, a.digit_bits, dmask, lane);
+      }
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -473,6 +566,56 @@ __global__ void __launch_bounds__(256) k_emit(EmitArgs a) {
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nparts * 256;
        q += (long long)gridDim.x * blockDim.x)
     a.lb[q] = 0ull;
+}
+
+// Items with more than kBigItem tiles: the warps of the grid stride over the
+// queue (no shared ticket to contend on) and write each item's tiles 32 at a
+// time (ballot prefix for the kept ones).
+__global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
+  __shared__ uint32_t sh[4][256];
+  for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0u;
+  __syncthreads();
+  const uint32_t nbig = *a.big_count;
+  const uint32_t *items = a.sorted_items[*a.sel];
+  const int lane = threadIdx.x & 31;
+  const uint32_t ltmask = (1u << lane) - 1u;
+  const uint32_t dmask = (1u << a.digit_bits) - 1u;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  for (uint32_t qi = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); qi < nbig; qi += warps) {
+    const uint32_t k = a.bigq[qi];
+    const uint32_t j = items[k];
+    const uint32_t off = a.offsets[k];
+    const uint2 r = a.rect[j];
+    const ViewDev &vd = a.views[a.view[j]];
+    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+    const int w = x1 - x0 + 1;
+    const int area = w * (y1 - y0 + 1);
+    const uint8_t m = a.tile_level ? a.rec_m[j] : 0;
+    long long run = off;
+    for (int l0 = 0; l0 < area; l0 += 32) {
+      const int l = l0 + lane;
+      bool kept = l < area;
+      long long t = 0;
+      if (kept) {
+        t = vd.tile_base + (long long)(y0 + l / w) * vd.tx + (x0 + l % w);
+        if (a.tile_level && a.tile_level[t] > m) kept = false;
+      }
+      const uint32_t b = __ballot_sync(0xffffffffu, kept);
+      const long long o = run + __popc(b & ltmask);
+      const bool wr = kept && o < a.pair_capacity;
+      if (wr) {
+        a.pkey[o] = (uint32_t)t;
+        a.pval[o] = j;
+      }
+      hist_add_warp(sh, wr, (uint32_t)t, a.passes, a.digit_bits, dmask, lane);
+      run += __popc(b);
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.passes * 256; q += blockDim.x) {
+    const uint32_t c = (&sh[0][0])[q];
+    if (c) atomicAdd(&a.hist[q], c);
+  }
 }
 
 // ---- per-tile ranges ------------------------------------------------------
@@ -500,9 +643,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(&hdr->ticket[1], 0, sizeof(hdr->ticket) - sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  const long long proj_parts = (p->n + kProjThreads - 1) / kProjThreads;
   const long long off_parts = (p->max_visible + kSortPart - 1) / kSortPart;
-  e = cudaMemsetAsync(region<unsigned long long>(p, ws, R_SCAN) + proj_parts, 0,
+  e = cudaMemsetAsync(region<unsigned long long>(p, ws, R_SCAN), 0,
                       sizeof(unsigned long long) * (size_t)off_parts, s);
   if (e != cudaSuccess) return e;
   if (p->n == 0) {
@@ -520,7 +662,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   d.keys[1] = region<uint32_t>(p, ws, R_DKEY_B);
   d.vals[0] = region<uint32_t>(p, ws, R_DVAL_A);
   d.vals[1] = region<uint32_t>(p, ws, R_DVAL_B);
-  d.count = &hdr->n_visible;
+  d.count = &hdr->n_items;          // every slot; invisible ones sort last
   d.capacity = p->max_visible;
   d.sel = &hdr->sel_depth;
   d.hist = &hdr->hist[0][0][0];
@@ -542,11 +684,11 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.n_items = &hdr->n_visible;
   sa.capacity = p->max_visible;
   sa.offsets = region<uint32_t>(p, ws, R_OFFSETS);
-  sa.slots = region<unsigned long long>(p, ws, R_SCAN) + proj_parts;
+  sa.slots = region<unsigned long long>(p, ws, R_SCAN);
   sa.ticket = &hdr->ticket[9];
   sa.n_pairs = &hdr->n_pairs;
   sa.status = &hdr->status;
-  k_offsets<<<g_sort_blocks, 256, 0, s>>>(sa);
+  k_offsets<<<g_stream_blocks, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
   const int pair_passes = (p->tile_bits + 7) / 8;
   const int pair_bits = (p->tile_bits + pair_passes - 1) / pair_passes;
@@ -572,7 +714,13 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.passes = pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
-  k_emit<<<g_sort_blocks, 256, 0, s>>>(ea);
+  ea.bigq = region<uint32_t>(p, ws, R_BIGQ);
+  ea.big_count = &hdr->big_count;
+  ea.big_ticket = &hdr->big_ticket;
+  e = cudaMemsetAsync(&hdr->big_count, 0, 2 * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  k_emit<<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
+  k_emit_big<<<g_stream_blocks, 256, 0, s>>>(ea);
   // 4. stable sort of the pairs by tile
   SortArgs t = {};
   t.first_keys = ea.pkey;
@@ -598,7 +746,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   uint2 *ranges = region<uint2>(p, ws, R_RANGES);
   e = cudaMemsetAsync(ranges, 0, p->bytes[R_RANGES], s);
   if (e != cudaSuccess) return e;
-  k_ranges<<<g_sort_blocks, 256, 0, s>>>(t.keys[0], t.keys[1], &hdr->sel_pair, &hdr->n_pairs,
+  k_ranges<<<g_stream_blocks, 256, 0, s>>>(t.keys[0], t.keys[1], &hdr->sel_pair, &hdr->n_pairs,
                                          p->max_pairs, ranges);
   return cudaGetLastError();
 }

@@ -17,19 +17,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// log2(alpha) before the clamp, for a pixel at tile-local (px, py), a point
-// with tile-local mean mu, whitening rows sh = (w1x, w1y, w2x, w2y) and
-// F = log2(opacity):  F - t1^2 - t2^2 with t = W (p - mu).
-__device__ __forceinline__ float log2_alpha(float px, float py, float2 mu, float4 sh, float F,
-                                            float &dx, float &dy, float &t1, float &t2) {
-  dx = __fsub_rn(px, mu.x);
-  dy = __fsub_rn(py, mu.y);
-  t1 = __fmaf_rn(dx, sh.x, __fmul_rn(dy, sh.y));
-  t2 = __fmaf_rn(dx, sh.z, __fmul_rn(dy, sh.w));
-  const float g = __fmaf_rn(-t1, t1, -__fmul_rn(t2, t2));
-  return __fadd_rn(g, F);
-}
-
 __device__ __forceinline__ float alpha_of(float p) {
   return fminf(kAlphaMax, ex2_approx(p));
 }
@@ -65,6 +52,101 @@ __device__ __forceinline__ void pixel_level(const ViewDev &vd, int L, float band
       wband = fminf(1.0f, fmaxf(0.0f, (sqrtf(d2) - vd.R[lvl - 2]) / band));
     }
   }
+}
+
+// Warp layout inside a tile: each warp covers an 8 x (4 PX) block of
+// pixels, PX = pixels per thread stacked 4 rows apart (16x16 tile, PX = 1:
+// 2 x 4 warps; PX = 2: 2 x 2 warps).
+template <int B, int PX>
+struct WarpGeom {
+  static constexpr int kWx = B / 8;                  // warps across
+  static constexpr int kRows = 4 * PX;               // pixel rows per warp
+  static constexpr int kWarps = B * B / (32 * PX);
+};
+
+// Which warps of the tile the point can reach: the bounding box of the
+// region log2(alpha) >= floor - 1e-3 (an ellipse |W d|^2 <= F - floor +
+// 1e-3), widened by 1e-4 relative + 1e-4 px, against each warp's pixel
+// centres.  A pixel the FP32 evaluation would blend always lies inside, so
+// culling never changes a decision.
+template <int B, int PX>
+__device__ __forceinline__ uint32_t warp_mask(float mx, float my, float4 sh, float Fmax) {
+  using G = WarpGeom<B, PX>;
+  const float r2 = Fmax - kLog2AlphaMin + 1e-3f;
+  if (!(r2 > 0.0f)) return 0u;
+  const float det = fabsf(sh.x * sh.w - sh.y * sh.z);
+  const float sr = sqrtf(r2) / det;
+  const float hx = sr * sqrtf(sh.y * sh.y + sh.w * sh.w) * 1.0001f + 1e-4f;
+  const float hy = sr * sqrtf(sh.x * sh.x + sh.z * sh.z) * 1.0001f + 1e-4f;
+  uint32_t mask = 0u;
+#pragma unroll
+  for (int w = 0; w < G::kWarps; ++w) {
+    const float x0 = 8.0f * (w % G::kWx) + 0.5f, y0 = (float)(G::kRows * (w / G::kWx)) + 0.5f;
+    const bool hit = (mx - hx <= x0 + 7.0f) && (mx + hx >= x0) &&
+                     (my - hy <= y0 + (float)(G::kRows - 1)) && (my + hy >= y0);
+    mask |= hit ? (1u << w) : 0u;
+  }
+  return mask;
+}
+
+// Exact version of warp_mask: the point can reach warp w only if the
+// minimum of s(p) = |W (p - mu)|^2 over the rectangle spanned by the warp's
+// pixel centres is at most F - floor (+1e-3 + 1e-4 relative slack).  The
+// minimum of this convex quadratic is 0 inside, else on an edge, where it is
+// a 1D quadratic minimised in closed form and clamped to the edge.
+template <int B, int PX>
+__device__ __forceinline__ uint32_t warp_mask_exact(float mx, float my, float4 sh, float Fmax) {
+  using G = WarpGeom<B, PX>;
+  const float r2 = Fmax - kLog2AlphaMin;
+  if (!(r2 > -1e-3f)) return 0u;
+  const float lim = r2 + 1e-3f + 1e-4f * fabsf(r2);
+  const float Qa = sh.x * sh.x + sh.z * sh.z;
+  const float Qb = sh.x * sh.y + sh.z * sh.w;
+  const float Qc = sh.y * sh.y + sh.w * sh.w;
+  const float ia = 1.0f / Qa, ic = 1.0f / Qc;
+  auto f = [&](float dx, float dy) { return Qa * dx * dx + 2.0f * Qb * dx * dy + Qc * dy * dy; };
+  uint32_t mask = 0u;
+#pragma unroll
+  for (int w = 0; w < G::kWarps; ++w) {
+    const float x0 = 8.0f * (w % G::kWx) + 0.5f, x1 = x0 + 7.0f;
+    const float y0 = (float)(G::kRows * (w / G::kWx)) + 0.5f, y1 = y0 + (float)(G::kRows - 1);
+    float best;
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) {
+      best = 0.0f;
+    } else {
+      // vertical edges x = x0, x1: dy* = -Qb dx / Qc, clamped
+      float dxa = x0 - mx, dxb = x1 - mx;
+      float dya = fminf(fmaxf(-Qb * dxa * ic, y0 - my), y1 - my);
+      float dyb = fminf(fmaxf(-Qb * dxb * ic, y0 - my), y1 - my);
+      // horizontal edges y = y0, y1
+      float dyc = y0 - my, dyd = y1 - my;
+      float dxc = fminf(fmaxf(-Qb * dyc * ia, x0 - mx), x1 - mx);
+      float dxd = fminf(fmaxf(-Qb * dyd * ia, x0 - mx), x1 - mx);
+      best = fminf(fminf(f(dxa, dya), f(dxb, dyb)), fminf(f(dxc, dyc), f(dxd, dyd)));
+    }
+    mask |= best * 0.9999f <= lim ? (1u << w) : 0u;
+  }
+  return mask;
+}
+
+// Evaluation record of one point in a tile: whitened offsets t = W p + c
+// (p the tile-local pixel centre), so t = W (p - mu) with c = -W mu.
+//   a = (w1x, w1y, c1, w2x), b = (w2y, c2, F - floor, warp mask bits)
+__device__ __forceinline__ void make_eval(float mx, float my, float4 sh, float F, uint32_t mask,
+                                          float4 &a, float4 &b) {
+  const float c1 = -__fmaf_rn(sh.x, mx, __fmul_rn(sh.y, my));
+  const float c2 = -__fmaf_rn(sh.z, mx, __fmul_rn(sh.w, my));
+  a = make_float4(sh.x, sh.y, c1, sh.z);
+  b = make_float4(sh.w, c2, __fsub_rn(F, kLog2AlphaMin), __uint_as_float(mask));
+}
+
+// |t|^2 at pixel (px, py); the point can blend iff s <= F - floor, and then
+// alpha = min(0.99, 2^(F - s)).
+__device__ __forceinline__ float eval_s(float px, float py, float4 a, float4 b, float &t1,
+                                        float &t2) {
+  t1 = __fmaf_rn(a.x, px, __fmaf_rn(a.y, py, a.z));
+  t2 = __fmaf_rn(a.w, px, __fmaf_rn(b.x, py, b.y));
+  return __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
 }
 
 }  // namespace gs

@@ -58,7 +58,7 @@ class gs_fov(C.Structure):
 
 class gs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("chunk", C.c_int32), ("flags", C.c_int32),
-                ("max_levels", C.c_int32), ("max_visible", C.c_int64), ("max_pairs", C.c_int64)]
+                ("max_levels", C.c_int32), ("reserved2", C.c_int64), ("max_pairs", C.c_int64)]
 
 
 class gs_counters(C.Structure):
@@ -210,14 +210,14 @@ class Renderer:
     """
 
     def __init__(self, n, sh_degree, cams, tile=16, foveated=False, backward=False,
-                 max_pairs=0, max_visible=0, max_levels=0, chunk=0, device="cuda"):
+                 max_pairs=0, max_levels=0, chunk=0, device="cuda"):
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cams_np = np.asarray(cams, np.float32).reshape(-1, 20)
         self.V = len(self.cams_np)
         self.device = device
         self.cfg = gs_config(tile, chunk, (GS_FLAG_FOVEATED if foveated else 0)
                              | (GS_FLAG_BACKWARD if backward else 0), max_levels,
-                             max_visible, max_pairs)
+                             0, max_pairs)
         self.plan = C.create_string_buffer(int(_lib.gs_plan_size()))
         self._cams_h = cams_host(self.cams_np)
         gs_plan_init(self.plan, self.n, self.sh_degree, self._cams_h, self.V, self.cfg)

@@ -24,28 +24,36 @@ def gpu_bins(gs, r):
     code, c = r.counters()
     assert code == gs.GS_OK, c
     M, K = int(c["n_visible"]), int(c["n_pairs"])
-    gid = r.region(gs.GS_REGION_ITEM_GID, torch.int32, M).cpu().numpy().astype(np.int64)
-    view = r.region(gs.GS_REGION_ITEM_VIEW, torch.int32, M).cpu().numpy().astype(np.int64)
-    depth = r.region(gs.GS_REGION_ITEM_DEPTH, torch.int32, M).cpu().numpy().view(np.uint32)
-    count = r.region(gs.GS_REGION_ITEM_COUNT, torch.int32, M).cpu().numpy().view(np.uint32)
+    S = r.n * r.V                       # item slots j = i * V + v
+    gid = r.region(gs.GS_REGION_ITEM_GID, torch.int32, S).cpu().numpy().astype(np.int64)
+    view = r.region(gs.GS_REGION_ITEM_VIEW, torch.int32, S).cpu().numpy().astype(np.int64)
+    depth = r.region(gs.GS_REGION_ITEM_DEPTH, torch.int32, S).cpu().numpy().view(np.uint32)
+    count = r.region(gs.GS_REGION_ITEM_COUNT, torch.int32, S).cpu().numpy().view(np.uint32)
+    vis = depth != 0xFFFFFFFF
+    assert int(vis.sum()) == M
+    j = np.arange(S)
+    # a visible slot holds its own point and view
+    np.testing.assert_array_equal(gid[vis], j[vis] // r.V)
+    np.testing.assert_array_equal(view[vis], j[vis] % r.V)
+    assert np.all(count[~vis] == 0)
     pt, pi = r.sorted_pairs(K)
     pt = pt.cpu().numpy().view(np.uint32).astype(np.uint64)
     pi = pi.cpu().numpy().astype(np.int64)
     ranges = r.region(gs.GS_REGION_RANGES, torch.int32, 2 * r.T_tiles).cpu().numpy().view(np.uint32).reshape(-1, 2)
-    return dict(M=M, K=K, gid=gid, view=view, depth=depth, count=count, pair_tile=pt,
+    return dict(M=M, K=K, gid=gid, view=view, depth=depth, count=count, vis=vis, pair_tile=pt,
                 pair_item=pi, ranges=ranges, nonfinite=int(c["n_nonfinite"]))
 
 
 def check_bins_exact(gb, ob, n):
-    # visible items, point-major order
-    vis_items = np.nonzero(ob.vis == 1)[0]           # v*n + i, view-major
-    v_o, i_o = vis_items // n, vis_items % n
-    order = np.lexsort((v_o, i_o))                   # point-major
-    assert gb["M"] == len(vis_items)
-    np.testing.assert_array_equal(gb["gid"], i_o[order])
-    np.testing.assert_array_equal(gb["view"], v_o[order])
-    np.testing.assert_array_equal(gb["depth"], ob.dbits[vis_items[order]])
-    np.testing.assert_array_equal(gb["count"], ob.counts[vis_items[order]])
+    # visible items: slot j = i * V + v on the GPU, v * n + i in the oracle
+    V = len(gb["vis"]) // n if n else 1
+    ov = (ob.vis == 1).reshape(V, n).T.reshape(-1)     # oracle visibility, slot order
+    np.testing.assert_array_equal(gb["vis"], ov)
+    assert gb["M"] == int(ov.sum())
+    slots = np.nonzero(ov)[0]
+    oracle_item = (slots % V) * n + slots // V
+    np.testing.assert_array_equal(gb["depth"][slots], ob.dbits[oracle_item])
+    np.testing.assert_array_equal(gb["count"][slots], ob.counts[oracle_item])
     # sorted pairs: key = tile << 32 | depth bits, value = v*n + i
     assert gb["K"] == ob.K
     j = gb["pair_item"]

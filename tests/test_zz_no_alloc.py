@@ -38,11 +38,11 @@ def _reference_pairs(gs, wl):
     sc = gs.scene_to_device(wl.scene)
     r = gs.Renderer(wl.scene.n, wl.scene.sh_degree, wl.cams)
     c = r.fit(sc)
-    M, K = int(c["n_visible"]), int(c["n_pairs"])
+    K = int(c["n_pairs"])
     pt, pi = r.sorted_pairs(K)
     tile = pt.cpu().numpy().view(np.uint32)
     item = pi.cpu().numpy().view(np.uint32)
-    depth = r.region(gs.GS_REGION_ITEM_DEPTH, torch.int32, M).cpu().numpy().view(np.uint32)
+    depth = r.region(gs.GS_REGION_ITEM_DEPTH, torch.int32, r.n * r.V).cpu().numpy().view(np.uint32)
     emit = np.lexsort((tile, item, depth[item]))
     bits = max(1, int(r.T_tiles - 1).bit_length())
     return tile, item, tile[emit].copy(), item[emit].copy(), bits
