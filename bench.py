@@ -119,6 +119,40 @@ OPS_PER_EVAL = 10
 OPS_PER_BLEND = 8
 
 
+RENDER_SOURCES = ("paper_2407_00435_gb300/csrc/k_render.cu", "paper_2407_00435_gb300/csrc/raster.cuh")
+RENDER_PROFILE = "profiles/render_plain_1080p_n1M.md"
+
+
+def render_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in RENDER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic():
+    """DRAM bytes per launch of the render kernel from the committed ncu
+    summary, or None when the kernel's sources changed since the capture."""
+    try:
+        lines = open(os.path.join(ROOT, RENDER_PROFILE)).read().splitlines()
+    except OSError:
+        return None, None
+    kv = {}
+    for ln in lines:
+        ln = ln.strip().lstrip("-* ").strip()
+        if ":" in ln and ln.startswith(("kernel_source_sha1", "dram_bytes_per_launch")):
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha1") != render_sources_sha1():
+        return None, kv.get("kernel_source_sha1")
+    try:
+        return int(float(kv["dram_bytes_per_launch"])), kv["kernel_source_sha1"]
+    except (KeyError, ValueError):
+        return None, None
+
+
 class L2Flusher:
     def __init__(self, torch):
         self.buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -227,9 +261,11 @@ def gpu_arm(args):
     mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_tops = N_SM * FP32_LANES * mhz * 1e6 / 1e12
     achieved_tops = (OPS_PER_EVAL * n_evals + OPS_PER_BLEND * n_blends) / (render_ms * 1e-3) / 1e12
+    traffic, _ = captured_traffic()
     roofline = {"bound": "alu", "kernel": "k_render", "achieved": round(achieved_tops, 3),
                 "peak": round(peak_tops, 3), "unit": "TFLOP/s (FP32 lane-ops)",
-                "frac": round(achieved_tops / peak_tops, 4), "traffic": None,
+                "frac": round(achieved_tops / peak_tops, 4), "traffic": traffic,
+                "traffic_source": RENDER_PROFILE if traffic else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src} sm_max_mhz)",
                 "render_ms": round(render_ms, 4)}
 
