@@ -117,7 +117,8 @@ typedef struct gs_config {
   int32_t chunk;         /* heavy-tile chunk length in points; 0 = default, <0 = off */
   int32_t flags;         /* GS_FLAG_* */
   int32_t max_levels;    /* largest foveation L the plan must hold; 0 = 4 */
-  int64_t reserved2;     /* unused; item slots are always N*V */
+  int32_t radix_bits;    /* digit width of the pair sort's passes, 4..8; 0 = balanced <= 8 */
+  int32_t reserved2;
   int64_t max_pairs;     /* capacity of tile/point pairs; 0 = 4 * N * V */
 } gs_config;
 

@@ -48,6 +48,8 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   p->V = V;
   p->tile = c.tile;
   p->chunk = c.chunk;
+  if (c.radix_bits != 0 && (c.radix_bits < 4 || c.radix_bits > 8)) return GS_ERR_INVALID_ARG;
+  p->radix_bits = c.radix_bits;
   p->flags = (uint32_t)c.flags;
   long long tiles = 0, pixels = 0;
   for (int v = 0; v < V; ++v) {

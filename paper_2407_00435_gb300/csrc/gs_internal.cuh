@@ -111,6 +111,7 @@ struct gs_plan {
   int64_t tiles_total, pixels_total;
   int64_t max_visible, max_pairs;
   int32_t tile_bits;
+  int32_t radix_bits;     // requested digit width of the pair sort (0 = balanced)
   int32_t last_fov;       // last render was foveated
   size_t off[gs::R_COUNT_];
   size_t bytes[gs::R_COUNT_];

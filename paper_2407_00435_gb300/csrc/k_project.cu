@@ -147,6 +147,7 @@ cudaError_t launch_tile_levels(const gs_plan *p, void *ws, cudaStream_t s) {
 // --------------------------------------------------------------------------
 struct ProjArgs {
   long long n;
+  int aligned16;               // every parameter array starts on 16 bytes
   int V, S, tile;
   const float *means, *scales, *quats, *opac, *sh;
   const gs_camera *cams;
@@ -372,13 +373,16 @@ __device__ __forceinline__ bool all_finite(const float *p, int n) {
 // Padded shared-memory rows (odd strides: no bank conflicts when every
 // thread reads element k of its own row).
 template <int S>
-struct ProjSmem {
+struct __align__(16) ProjSmem {
   static constexpr int kSh = (S * 3) | 1;
-  float sh[kProjThreads][kSh];
-  float mu[kProjThreads][3];
+  float mu[kProjThreads][3];     // 16-byte aligned: TMA destinations first
   float sc[kProjThreads][3];
-  float q[kProjThreads][5];
+  float qraw[kProjThreads * 4];
   float op[kProjThreads];
+  // SH rows with an odd stride; the TMA copy lands unpadded at the start of
+  // the same buffer and is re-laid out in place
+  float sh[kProjThreads][kSh];
+  float q[kProjThreads][5];
 };
 
 // Coalesced load of `cnt` consecutive rows of `width` floats from global
@@ -405,6 +409,49 @@ __device__ __forceinline__ void stage_rows(float *dst, int stride, const float *
     for (int f = threadIdx.x; f < total; f += blockDim.x)
       dst[(f / width) * stride + f % width] = g[f];
   }
+}
+
+// ---- TMA bulk copies (cp.async.bulk) with an mbarrier ---------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on phase `parity`; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (int it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(32);
+  }
+  return false;
 }
 
 struct Rec {
@@ -533,14 +580,64 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
     s_vis = 0;
     s_nonfinite = 0;
   }
+  __shared__ __align__(8) uint64_t s_bar;
   const long long row0 = (long long)blockIdx.x * kProjThreads;
   const int cnt_rows = (int)min((long long)kProjThreads, a.n - row0);
-  // coalesced staging of this block's points
-  stage_rows(&sm.sh[0][0], ProjSmem<S>::kSh, a.sh, row0, cnt_rows, S * 3);
-  stage_rows(&sm.mu[0][0], 3, a.means, row0, cnt_rows, 3);
-  stage_rows(&sm.sc[0][0], 3, a.scales, row0, cnt_rows, 3);
-  stage_rows(&sm.q[0][0], 5, a.quats, row0, cnt_rows, 4);
-  stage_rows(&sm.op[0], 1, a.opac, row0, cnt_rows, 1);
+  // Full blocks whose source chunks are 16-byte aligned are fetched by the
+  // TMA engine (cp.async.bulk, one thread issues five copies); the SH rows
+  // are then re-laid out into odd-stride rows.  Other blocks load with
+  // ordinary coalesced loads.
+  const bool tma = cnt_rows == kProjThreads && a.aligned16;
+  if (tma) {
+    if (tid == 0) {
+      mbar_init(&s_bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      constexpr uint32_t bsh = kProjThreads * S * 3 * 4, b3 = kProjThreads * 3 * 4;
+      constexpr uint32_t bq = kProjThreads * 4 * 4, bo = kProjThreads * 4;
+      mbar_expect_tx(&s_bar, bsh + 2 * b3 + bq + bo);
+      bulk_g2s(&sm.sh[0][0], a.sh + row0 * S * 3, bsh, &s_bar);
+      bulk_g2s(&sm.mu[0][0], a.means + row0 * 3, b3, &s_bar);
+      bulk_g2s(&sm.sc[0][0], a.scales + row0 * 3, b3, &s_bar);
+      bulk_g2s(&sm.qraw[0], a.quats + row0 * 4, bq, &s_bar);
+      bulk_g2s(&sm.op[0], a.opac + row0, bo, &s_bar);
+    }
+    const bool landed = mbar_wait_bounded(&s_bar, 0);
+    if (__syncthreads_or(!landed)) {
+      // give up together: record it, wait (bounded) for the copies still in
+      // flight into this block's shared memory, then leave
+      if (tid == 0) set_status(&a.hdr->status, GS_ERR_TIMEOUT);
+      mbar_wait_bounded(&s_bar, 0);
+      return;
+    }
+    // in-place re-layout of the SH rows: each thread pulls its own unpadded
+    // row into registers, then writes it back with the odd stride
+    float row[S * 3];
+    const float *raw = &sm.sh[0][0] + tid * (S * 3);
+    if constexpr ((S * 3) % 4 == 0) {
+#pragma unroll
+      for (int k = 0; k < S * 3; k += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(raw + k);
+        row[k] = v.x; row[k + 1] = v.y; row[k + 2] = v.z; row[k + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < S * 3; ++k) row[k] = raw[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < S * 3; ++k) sm.sh[tid][k] = row[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sm.q[tid][k] = sm.qraw[tid * 4 + k];
+  } else {
+    stage_rows(&sm.sh[0][0], ProjSmem<S>::kSh, a.sh, row0, cnt_rows, S * 3);
+    stage_rows(&sm.mu[0][0], 3, a.means, row0, cnt_rows, 3);
+    stage_rows(&sm.sc[0][0], 3, a.scales, row0, cnt_rows, 3);
+    stage_rows(&sm.q[0][0], 5, a.quats, row0, cnt_rows, 4);
+    stage_rows(&sm.op[0], 1, a.opac, row0, cnt_rows, 1);
+  }
   __syncthreads();
   const long long i = row0 + tid;
   uint32_t nvis = 0;
@@ -590,6 +687,8 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
   a.opac = p->scene.opacities;
   a.sh = p->scene.sh;
   a.cams = p->cams;
+  auto al16 = [](const void *q) { return ((uintptr_t)q & 15) == 0; };
+  a.aligned16 = al16(a.means) && al16(a.scales) && al16(a.quats) && al16(a.opac) && al16(a.sh);
   a.views = region<ViewDev>(p, ws, R_VIEWS);
   a.tile_level = p->has_fov ? region<uint8_t>(p, ws, R_TILE_LEVEL) : nullptr;
   a.bound_m = p->has_fov ? p->fov.bound_m : nullptr;

@@ -589,15 +589,20 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
     const ViewDev &vd = a.views[a.view[j]];
     const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
     const int w = x1 - x0 + 1;
-    const int area = w * (y1 - y0 + 1);
     const uint8_t m = a.tile_level ? a.rec_m[j] : 0;
     long long run = off;
-    for (int l0 = 0; l0 < area; l0 += 32) {
-      const int l = l0 + lane;
-      bool kept = l < area;
+    // row by row, 32 tiles of a row at a time (no division per tile)
+    for (int y = y0, x = 0; y <= y1; x += 32) {
+      if (x >= w) {
+        x = -32;
+        ++y;
+        continue;
+      }
+      const int xx = x + lane;
+      bool kept = xx < w;
       long long t = 0;
       if (kept) {
-        t = vd.tile_base + (long long)(y0 + l / w) * vd.tx + (x0 + l % w);
+        t = vd.tile_base + (long long)y * vd.tx + (x0 + xx);
         if (a.tile_level && a.tile_level[t] > m) kept = false;
       }
       const uint32_t b = __ballot_sync(0xffffffffu, kept);
@@ -690,7 +695,11 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.status = &hdr->status;
   k_offsets<<<g_stream_blocks, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
-  const int pair_passes = (p->tile_bits + 7) / 8;
+  // digit width: the requested one, else the balanced width of the fewest
+  // passes of at most 8 bits
+  const int want = p->radix_bits > 0 ? p->radix_bits : 8;
+  int pair_passes = (p->tile_bits + want - 1) / want;
+  if (pair_passes > 4) pair_passes = 4;   // histogram storage holds four passes
   const int pair_bits = (p->tile_bits + pair_passes - 1) / pair_passes;
   EmitArgs ea = {};
   ea.sorted_items[0] = d.vals[0];
