@@ -114,11 +114,14 @@ typedef struct gs_fov {
 /* Plan options.  Zero-initialised fields take the defaults given. */
 typedef struct gs_config {
   int32_t tile;          /* tile edge in pixels: 16 (default) or 8 */
-  int32_t chunk;         /* heavy-tile chunk length in points; 0 = default, <0 = off */
+  int32_t chunk;         /* heavy-tile chunk length in points, 64..2^24; <= 0 = whole
+                            tiles (default).  See gs_render. */
   int32_t flags;         /* GS_FLAG_* */
   int32_t max_levels;    /* largest foveation L the plan must hold; 0 = 4 */
   int32_t radix_bits;    /* digit width of the pair sort's passes, 4..8; 0 = balanced <= 8 */
-  int32_t reserved2;
+  int32_t chunk_slots;   /* chunk slots the workspace holds for the chunked render;
+                            0 = enough for any split (capped at max(tiles + 64, 65536)).
+                            Tiles that do not fit are rendered whole. */
   int64_t max_pairs;     /* capacity of tile/point pairs; 0 = 4 * N * V */
 } gs_config;
 
@@ -184,7 +187,14 @@ gs_status gs_bin_sort(gs_plan *plan, void *ws, cudaStream_t stream);
  *                  pixels_blended, pixels_dominated, summed over the views
  *                  (cost statistics of Sec. 3.2: Comp_i and Val_i).
  * bg is host memory (3 floats).  All views of the plan must be plain (the
- * plan's fov, if any, is ignored). */
+ * plan's fov, if any, is ignored).
+ * Work distribution: with the plan's chunk <= 0 one block composites each
+ * tile.  With chunk > 0 persistent blocks take work from a queue: a tile
+ * with more than `chunk` pairs is split into chunks composited in parallel
+ * from T = 1 and merged in list order by (C1, T1) o (C2, T2) = (C1 + T1 C2,
+ * T1 T2); the chunk in which the early stop falls is re-walked from the
+ * incoming transmittance, so the stop rule above holds exactly.  Renders
+ * with stats always walk whole tiles.  Results agree to float rounding. */
 gs_status gs_render(gs_plan *plan, void *ws, const float bg[3], float *rgb,
                     float *T_final, int32_t *last, uint32_t *stats,
                     cudaStream_t stream);

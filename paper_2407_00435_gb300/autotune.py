@@ -24,9 +24,10 @@ from .gs import GsError, Renderer
 DEFAULT_CANDIDATES = [
     {"tile": 16, "radix_bits": 0, "chunk": 0},
     {"tile": 16, "radix_bits": 7, "chunk": 0},
-    {"tile": 16, "radix_bits": 6, "chunk": 0},
+    {"tile": 16, "radix_bits": 0, "chunk": 1024},
+    {"tile": 16, "radix_bits": 0, "chunk": 2048},
     {"tile": 8, "radix_bits": 0, "chunk": 0},
-    {"tile": 8, "radix_bits": 7, "chunk": 0},
+    {"tile": 8, "radix_bits": 0, "chunk": 512},
 ]
 
 

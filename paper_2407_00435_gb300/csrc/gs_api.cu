@@ -47,7 +47,8 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   p->sh_degree = sh_degree;
   p->V = V;
   p->tile = c.tile;
-  p->chunk = c.chunk;
+  if (c.chunk > 0 && (c.chunk < 64 || c.chunk > (1 << 24))) return GS_ERR_INVALID_ARG;
+  p->chunk = c.chunk > 0 ? c.chunk : 0;
   if (c.radix_bits != 0 && (c.radix_bits < 4 || c.radix_bits > 8)) return GS_ERR_INVALID_ARG;
   p->radix_bits = c.radix_bits;
   p->flags = (uint32_t)c.flags;
@@ -100,7 +101,23 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   b[R_PKEY_A] = b[R_PKEY_B] = b[R_PVAL_A] = b[R_PVAL_B] = 4 * (size_t)K;
   b[R_BIGQ] = 4 * (size_t)M;
   b[R_RANGES] = 8 * (size_t)T;
-  b[R_WORK] = 4 * (size_t)T;
+  // chunked render: a tile of len > chunk pairs takes ceil(len / chunk) <=
+  // 2 len / chunk slots, so 2 K / chunk slots always suffice; capped
+  // (tiles beyond the cap are rendered whole)
+  if (c.chunk_slots < 0) return GS_ERR_INVALID_ARG;
+  if (p->chunk > 0) {
+    long long cap = 2 * K / p->chunk + 1;
+    const long long lim = T + 64 > 65536 ? T + 64 : 65536;
+    if (cap > lim) cap = lim;
+    if (c.chunk_slots > 0) cap = c.chunk_slots;
+    p->chunk_cap = cap;
+  }
+  const size_t nacc = fov ? 2 : 1;
+  const size_t tpx = (size_t)c.tile * (size_t)c.tile;
+  b[R_WORK] = 8 * (size_t)p->chunk_cap;
+  b[R_CHUNK_TILE] = p->chunk > 0 ? 16 * (size_t)T : 0;
+  b[R_CHUNK_PART] = 16 * nacc * tpx * (size_t)p->chunk_cap;
+  b[R_CHUNK_LAST] = 4 * nacc * tpx * (size_t)p->chunk_cap;
   b[R_SCAN] = 8 * (size_t)((M + kSortPart - 1) / kSortPart + 1);
   b[R_LOOKBACK] = 2 * 256 * 8 * (size_t)(parts > 0 ? parts : 1);
   b[R_GRAD_ITEM] = bwd ? 16 * sizeof(float) * (size_t)M : 0;

@@ -49,7 +49,11 @@ enum Region : int {
   R_PKEY_A, R_PKEY_B, R_PVAL_A, R_PVAL_B,   // pair sort ping-pong (K)
   R_BIGQ,        // u32 items with many tiles, expanded by a separate kernel (M)
   R_RANGES,      // uint2 per tile
-  R_WORK,        // u32 render work list (tiles, heavy first)
+  R_WORK,        // uint2 chunk slots of the chunked render: (tile, chunk index)
+  R_CHUNK_TILE,  // uint4 per tile: (first chunk slot or none, chunks finished,
+                 //   first chunk that stopped every pixel, -)
+  R_CHUNK_PART,  // float4 per (slot, accumulator, pixel): partial (r, g, b, T)
+  R_CHUNK_LAST,  // i32 per (slot, accumulator, pixel): partial last position
   R_SCAN,        // u64 look-back slots of the pair-offset scan
   R_LOOKBACK,    // u64 radix lookback slots, two buffers
   R_GRAD_ITEM,   // float per item gradient scratch (backward)
@@ -74,6 +78,9 @@ struct Hdr {
   uint32_t big_count;             // items queued for the large-item emit
   uint32_t big_ticket;            // next queued item to expand
   uint32_t hist[2][4][256];       // digit histograms: [sort][pass][digit]
+  unsigned long long queue;       // next work item of the chunked render
+  uint32_t n_slots;               // chunk slots requested by the chunk plan
+  uint32_t pad1;
 };
 
 // Per-view constants, computed on the device from the cameras.
@@ -112,6 +119,7 @@ struct gs_plan {
   int64_t max_visible, max_pairs;
   int32_t tile_bits;
   int32_t radix_bits;     // requested digit width of the pair sort (0 = balanced)
+  int64_t chunk_cap;      // chunk slots of the chunked render (0 = whole tiles only)
   int32_t last_fov;       // last render was foveated
   size_t off[gs::R_COUNT_];
   size_t bytes[gs::R_COUNT_];

@@ -42,7 +42,20 @@ struct RenderArgs {
   int32_t *last;
   uint32_t *stats;   // (4, N) or null
   unsigned long long *n_evals, *n_blends;
+  // heavy-tile chunking (persistent work queue)
+  int chunk;                     // points per chunk
+  long long tiles;
+  const uint2 *chunk_list;       // per slot: (tile, chunk index); y = kNoChunk: unused
+  uint4 *chunk_tile;             // per tile: (first slot or kNoChunk, chunks finished,
+                                 //   first chunk whose pixels all stopped, -)
+  float4 *part_ct;               // per (slot, accumulator, pixel): (r, g, b, +-T)
+  int32_t *part_last;            // per (slot, accumulator, pixel): last blended position
+  unsigned long long ch_cap;     // chunk slots held by the workspace
+  const uint32_t *n_slots;       // chunk slots requested by k_chunk_plan
+  unsigned long long *queue;     // next work item
 };
+
+constexpr uint32_t kNoChunk = 0xffffffffu;
 
 struct Acc {
   float r, g, b, T;
@@ -76,89 +89,94 @@ __device__ __forceinline__ void prefetch(const RenderArgs &a, const uint32_t *va
   r.m = FOV ? (int)a.rec_m[j] : 0;
 }
 
-// One block per tile, B*B/PX threads, PX pixels per thread (4 rows apart),
-// batches of up to kBatch points staged in shared memory.
-template <int B, bool FOV, bool MV, bool STATS, int PX>
-__global__ void __launch_bounds__(B * B / PX, 1024 / (B * B / PX)) k_render(RenderArgs a) {
-  constexpr int NT = B * B / PX;
-  constexpr int NB = 2 * NT < kBatch ? 2 * NT : kBatch;   // points per batch
-  constexpr int SPT = NB / NT;                           // points staged per thread
-  using G = WarpGeom<B, PX>;
-  __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
-  __shared__ uint32_t s_gid[STATS ? NB : 1];
-  __shared__ int s_m[FOV ? NB : 1];
-  __shared__ float4 s_lv[MV ? NB : 1][MV ? kMaxLv : 1];
-  __shared__ uint32_t s_cnt[STATS ? NB : 1];
-  // per-warp ordered lists of the batch slots that can reach the warp
-  constexpr int NWS = NT / 32;                           // staging warps
-  __shared__ uint16_t s_list[G::kWarps][NB];
-  __shared__ uint16_t s_wcnt[G::kWarps][SPT * NWS];
-  __shared__ uint16_t s_woff[G::kWarps][SPT * NWS + 1];
+// Block-uniform description of the current work item, kept in shared
+// memory so that it does not occupy registers across the walks.
+struct ItemSm {
+  long long t;                       // tile
+  unsigned long long slot, first;    // this chunk's slot, the tile's first slot
+  uint32_t nc, cc, c;                // chunks of the tile (0: whole), chunk being merged,
+                                     //   this item's chunk
+  uint32_t begin, end, origin;       // walked range, first pair of the tile
+  int vidx, tx0, ty0;                // view, tile origin in pixels
+  int merging;
+};
 
-  const long long t = blockIdx.x;
+// Shared memory of one render block: the records of one batch (structure
+// of arrays) and the per-warp ordered lists of the batch slots that can
+// reach each warp.
+template <int B, bool FOV, bool MV, bool STATS, int PX>
+struct RSmem {
+  static constexpr int NT = B * B / PX;                   // threads
+  static constexpr int NB = 2 * NT < kBatch ? 2 * NT : kBatch;   // points per batch
+  static constexpr int SPT = NB / NT;                     // points staged per thread
+  static constexpr int NWS = NT / 32;                     // staging warps
+  static constexpr int NW = WarpGeom<B, PX>::kWarps;
+  float4 a[NB], b[NB], c[NB];
+  uint32_t gid[STATS ? NB : 1];
+  int m[FOV ? NB : 1];
+  float4 lv[MV ? NB : 1][MV ? kMaxLv : 1];
+  uint32_t cnt[STATS ? NB : 1];
+  uint16_t list[NW][NB];
+  uint16_t wcnt[NW][SPT * NWS];
+  uint16_t woff[NW][SPT * NWS + 1];
+  unsigned long long item;   // work-queue item broadcast
+  int flag;                  // last chunk of a tile to arrive
+  int abort;                 // an earlier chunk of the tile stopped every pixel
+  ItemSm it;
+};
+
+// Per-thread pixel state used by the walk (PX pixels 4 rows apart).
+template <int PX>
+struct Pix {
+  float px, py[PX];   // tile-local pixel centre
+  int lvl[PX];        // foveation level
+};
+
+// Composites the sorted points [begin, end) of a tile front to back into
+// every accumulator that is not done.  List positions (`last`) are reported
+// relative to `origin`, the first pair of the tile.  Starts and ends with a
+// block-wide barrier, so the shared batch buffers can be reused right after.
+template <int B, bool FOV, bool MV, bool STATS, int PX>
+__device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STATS, PX> &sm,
+                                     const uint32_t *vals, int tx0, int ty0, uint32_t begin,
+                                     uint32_t end, uint32_t origin, const Pix<PX> &pp,
+                                     Acc (&A)[PX], Acc (&Bq)[PX], float (&dom_w)[PX],
+                                     uint32_t (&dom_gid)[PX], uint32_t &n_blend,
+                                     uint32_t (&walk_end)[PX], const uint32_t *stop_c = nullptr,
+                                     uint32_t my_c = 0) {
+  using S = RSmem<B, FOV, MV, STATS, PX>;
+  constexpr int NT = S::NT, NB = S::NB, SPT = S::SPT, NWS = S::NWS;
+  using G = WarpGeom<B, PX>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const ViewDev vd = a.views[find_view(a.views, a.V, t)];
-  const int local = (int)(t - vd.tile_base);
-  const int tx0 = (local % vd.tx) * B, ty0 = (local / vd.tx) * B;
-  const int lx = (warp % G::kWx) * 8 + (lane & 7);
-  const int ly0 = (warp / G::kWx) * G::kRows + (lane >> 3);
-  int x[PX], y[PX], lvl[PX];
-  bool inside[PX], in_band[PX];
-  float py[PX], wband[PX];
-  Acc A[PX], Bq[PX];
-  float dom_w[PX];
-  uint32_t dom_gid[PX];
-  const float px = (float)lx + 0.5f;
-#pragma unroll
-  for (int k = 0; k < PX; ++k) {
-    const int ly = ly0 + 4 * k;
-    x[k] = tx0 + lx;
-    y[k] = ty0 + ly;
-    inside[k] = x[k] < vd.W && y[k] < vd.H;
-    py[k] = (float)ly + 0.5f;
-    lvl[k] = 1;
-    in_band[k] = false;
-    wband[k] = 1.0f;
-    if (FOV) pixel_level(vd, a.L, a.band, x[k], y[k], lvl[k], in_band[k], wband[k]);
-    A[k] = Acc{0.f, 0.f, 0.f, 1.f, -1, !inside[k]};
-    Bq[k] = Acc{0.f, 0.f, 0.f, 1.f, -1, !(inside[k] && in_band[k])};
-    dom_w[k] = -1.0f;
-    dom_gid[k] = 0;
-  }
-  uint32_t n_blend = 0;
-  uint32_t walk_end[PX];                 // list positions walked until the stop
-#pragma unroll
-  for (int k = 0; k < PX; ++k) walk_end[k] = 0;
   auto all_done_here = [&]() {
     bool d = true;
 #pragma unroll
     for (int k = 0; k < PX; ++k) d = d && A[k].done && Bq[k].done;
     return d;
   };
-
-  const uint2 rg = a.ranges[t];
-  const uint32_t *vals = *a.sel ? a.pval_b : a.pval_a;
   if (STATS)
-    for (int q = tid; q < NB; q += NT) s_cnt[q] = 0;
+    for (int q = tid; q < NB; q += NT) sm.cnt[q] = 0;
   Pre pre[SPT];
 #pragma unroll
   for (int u = 0; u < SPT; ++u)
-    prefetch<FOV>(a, vals, rg.x + tid + u * NT, rg.x + tid + u * NT < rg.y, pre[u]);
+    prefetch<FOV>(a, vals, begin + tid + u * NT, begin + tid + u * NT < end, pre[u]);
 
-  for (uint32_t b = rg.x;; b += NB) {
+  for (uint32_t b = begin;; b += NB) {
+    // a chunk stops early once an earlier chunk of its tile has stopped
+    // every pixel: the merge never reads what would follow
+    if (stop_c && tid == 0 && *(const volatile uint32_t *)stop_c < my_c) sm.abort = 1;
     const int all_done = __syncthreads_count(all_done_here()) == NT;
-    if (STATS && b > rg.x) {
+    if (STATS && b > begin) {
       for (int q = tid; q < NB; q += NT) {
-        const uint32_t c = s_cnt[q];
+        const uint32_t c = sm.cnt[q];
         if (c) {
-          atomicAdd(&a.stats[2 * a.n + s_gid[q]], c);
-          atomicAdd(&a.stats[a.n + s_gid[q]], 1u);
-          s_cnt[q] = 0;
+          atomicAdd(&a.stats[2 * a.n + sm.gid[q]], c);
+          atomicAdd(&a.stats[a.n + sm.gid[q]], 1u);
+          sm.cnt[q] = 0;
         }
       }
     }
-    if (all_done || b >= rg.y) break;
-    const uint32_t cnt = min((uint32_t)NB, rg.y - b);
+    if (all_done || b >= end || (stop_c && sm.abort)) break;
     uint32_t wm[SPT];
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
@@ -180,18 +198,18 @@ __global__ void __launch_bounds__(B * B / PX, 1024 / (B * B / PX)) k_render(Rend
             c.y = fmaxf(0.0f, fmaf(kY00, dc[1], rest.y) + kShOffset);
             c.z = fmaxf(0.0f, fmaf(kY00, dc[2], rest.z) + kShOffset);
           }
-          s_lv[q][l - 2] = make_float4(c.x, c.y, c.z, F);
+          sm.lv[q][l - 2] = make_float4(c.x, c.y, c.z, F);
           Fmax = fmaxf(Fmax, F);
         }
       }
       wm[u] = warp_mask_exact<B, PX>(mx, my, pre[u].shape, Fmax);
       float4 ea, eb;
       make_eval(mx, my, pre[u].shape, pre[u].color.w, wm[u], ea, eb);
-      s_a[q] = ea;
-      s_b[q] = eb;
-      s_c[q] = pre[u].color;
-      if (STATS) s_gid[q] = pre[u].gid;
-      if (FOV) s_m[q] = pre[u].m;
+      sm.a[q] = ea;
+      sm.b[q] = eb;
+      sm.c[q] = pre[u].color;
+      if (STATS) sm.gid[q] = pre[u].gid;
+      if (FOV) sm.m[q] = pre[u].m;
     }
     // ordered compaction of the slots per target warp: ballot prefixes
     // inside each staging warp, then prefix sums over (u, staging warp)
@@ -202,72 +220,73 @@ __global__ void __launch_bounds__(B * B / PX, 1024 / (B * B / PX)) k_render(Rend
       for (int w = 0; w < G::kWarps; ++w) {
         const uint32_t bal = __ballot_sync(0xffffffffu, (wm[u] >> w) & 1u);
         pfx[u][w] = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) s_wcnt[w][u * NWS + warp] = (uint16_t)__popc(bal);
+        if (lane == 0) sm.wcnt[w][u * NWS + warp] = (uint16_t)__popc(bal);
       }
     __syncthreads();
     if (tid < G::kWarps) {
       uint32_t run = 0;
       for (int e = 0; e < SPT * NWS; ++e) {
-        s_woff[tid][e] = (uint16_t)run;
-        run += s_wcnt[tid][e];
+        sm.woff[tid][e] = (uint16_t)run;
+        run += sm.wcnt[tid][e];
       }
-      s_woff[tid][SPT * NWS] = (uint16_t)run;
+      sm.woff[tid][SPT * NWS] = (uint16_t)run;
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < SPT; ++u)
 #pragma unroll
       for (int w = 0; w < G::kWarps; ++w)
-        if ((wm[u] >> w) & 1u) s_list[w][s_woff[w][u * NWS + warp] + pfx[u][w]] = (uint16_t)(tid + u * NT);
+        if ((wm[u] >> w) & 1u)
+          sm.list[w][sm.woff[w][u * NWS + warp] + pfx[u][w]] = (uint16_t)(tid + u * NT);
     __syncthreads();
     // prefetch the next batch while this one is composited
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
       const uint32_t k = b + NB + tid + u * NT;
-      prefetch<FOV>(a, vals, k, k < rg.y, pre[u]);
+      prefetch<FOV>(a, vals, k, k < end, pre[u]);
     }
     if (!all_done_here()) {
-      const int nlist = s_woff[warp][SPT * NWS];
+      const int nlist = sm.woff[warp][SPT * NWS];
       for (int li = 0; li < nlist; ++li) {
-        const uint32_t q = s_list[warp][li];
-        const float4 sb = s_b[q];
-        const float4 sa = s_a[q];
-        const int m = FOV ? s_m[q] : 0;
+        const uint32_t q = sm.list[warp][li];
+        const float4 sb = sm.b[q];
+        const float4 sa = sm.a[q];
+        const int m = FOV ? sm.m[q] : 0;
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
           float t1, t2;
-          const float sq = eval_s(px, py[k], sa, sb, t1, t2);
+          const float sq = eval_s(pp.px, pp.py[k], sa, sb, t1, t2);
           // accumulator A: the pixel's own level
-          if (!A[k].done && (!FOV || m >= lvl[k])) {
-            const bool own = MV && lvl[k] >= 2;
-            const float F = own ? s_lv[q][lvl[k] - 2].w : s_c[q].w;
+          if (!A[k].done && (!FOV || m >= pp.lvl[k])) {
+            const bool own = MV && pp.lvl[k] >= 2;
+            const float F = own ? sm.lv[q][pp.lvl[k] - 2].w : sm.c[q].w;
             const float r2 = own ? __fsub_rn(F, kLog2AlphaMin) : sb.z;
             if (sq <= r2) {
               const float al = alpha_of(__fsub_rn(F, sq));
               const float Tn = A[k].T * (1.0f - al);
               if (Tn < kTMin) {
                 A[k].done = true;
-                walk_end[k] = b + q - rg.x + 1;
+                walk_end[k] = b + q - origin + 1;
               } else {
-                const float4 c = own ? s_lv[q][lvl[k] - 2] : s_c[q];
+                const float4 c = own ? sm.lv[q][pp.lvl[k] - 2] : sm.c[q];
                 const float w = al * A[k].T;
                 A[k].r = fmaf(w, c.x, A[k].r);
                 A[k].g = fmaf(w, c.y, A[k].g);
                 A[k].b = fmaf(w, c.z, A[k].b);
                 A[k].T = Tn;
-                A[k].last = (int)(b + q - rg.x);
+                A[k].last = (int)(b + q - origin);
                 if (STATS) {
                   ++n_blend;
-                  atomicAdd(&s_cnt[q], 1u);
-                  if (w > dom_w[k]) { dom_w[k] = w; dom_gid[k] = s_gid[q]; }
+                  atomicAdd(&sm.cnt[q], 1u);
+                  if (w > dom_w[k]) { dom_w[k] = w; dom_gid[k] = sm.gid[q]; }
                 }
               }
             }
           }
           // accumulator B: the better level inside a blend band
-          if (FOV && !Bq[k].done && m >= lvl[k] - 1) {
-            const bool own = MV && lvl[k] >= 3;
-            const float F = own ? s_lv[q][lvl[k] - 3].w : s_c[q].w;
+          if (FOV && !Bq[k].done && m >= pp.lvl[k] - 1) {
+            const bool own = MV && pp.lvl[k] >= 3;
+            const float F = own ? sm.lv[q][pp.lvl[k] - 3].w : sm.c[q].w;
             const float r2 = own ? __fsub_rn(F, kLog2AlphaMin) : sb.z;
             if (sq <= r2) {
               const float al = alpha_of(__fsub_rn(F, sq));
@@ -275,13 +294,13 @@ __global__ void __launch_bounds__(B * B / PX, 1024 / (B * B / PX)) k_render(Rend
               if (Tn < kTMin) {
                 Bq[k].done = true;
               } else {
-                const float4 c = own ? s_lv[q][lvl[k] - 3] : s_c[q];
+                const float4 c = own ? sm.lv[q][pp.lvl[k] - 3] : sm.c[q];
                 const float w = al * Bq[k].T;
                 Bq[k].r = fmaf(w, c.x, Bq[k].r);
                 Bq[k].g = fmaf(w, c.y, Bq[k].g);
                 Bq[k].b = fmaf(w, c.z, Bq[k].b);
                 Bq[k].T = Tn;
-                Bq[k].last = (int)(b + q - rg.x);
+                Bq[k].last = (int)(b + q - origin);
               }
             }
           }
@@ -290,13 +309,233 @@ __global__ void __launch_bounds__(B * B / PX, 1024 / (B * B / PX)) k_render(Rend
       }
     }
   }
+}
+
+// Folds the partial result (C_c, T_c) of chunk c into an accumulator that
+// has composited chunks 0..c-1:  (C, T) o (C_c, T_c) = (C + T C_c, T T_c).
+// A chunk walked from T = 1 stops when its own T would drop below 1e-4;
+// with the incoming T the true stop can only come earlier, so a chunk that
+// stopped (T_c stored negated), or whose product crosses 1e-4, has to be
+// re-walked from the incoming state: returns true then.  With nothing
+// composited before (T == 1) the chunk's own walk is already exact.
+__device__ __forceinline__ bool merge_chunk(Acc &X, float4 part, int plast) {
+  if (X.done) return false;
+  const float Tc = fabsf(part.w);
+  const bool stopped = part.w < 0.0f;
+  if (X.T == 1.0f) {
+    X.r = part.x;
+    X.g = part.y;
+    X.b = part.z;
+    X.T = Tc;
+    if (plast >= 0) X.last = plast;
+    X.done = stopped;
+    return false;
+  }
+  if (stopped || X.T * Tc < kTMin) return true;
+  X.r = fmaf(X.T, part.x, X.r);
+  X.g = fmaf(X.T, part.y, X.g);
+  X.b = fmaf(X.T, part.z, X.b);
+  X.T = X.T * Tc;
+  if (plast >= 0) X.last = plast;
+  return false;
+}
+
+// Image position and foveation of pixel k of this thread in a tile.
+template <int B, bool FOV, int PX>
+__device__ __forceinline__ void pixel_of(const RenderArgs &a, const ViewDev &vd, int tx0, int ty0,
+                                         int k, int &x, int &y, int &lvl, bool &inside,
+                                         bool &in_band, float &wband) {
+  using G = WarpGeom<B, PX>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  x = tx0 + (warp % G::kWx) * 8 + (lane & 7);
+  y = ty0 + (warp / G::kWx) * G::kRows + (lane >> 3) + 4 * k;
+  inside = x < vd.W && y < vd.H;
+  lvl = 1;
+  in_band = false;
+  wband = 1.0f;
+  if (FOV) pixel_level(vd, a.L, a.band, x, y, lvl, in_band, wband);
+}
+
+// One work item: the whole tile t (nc == 0), or chunk c of the nc chunks of
+// a heavy tile, whose partial result goes to chunk slot `slot`.  The last
+// chunk of a tile to finish merges all of them and writes the pixels.
+template <int B, bool FOV, bool MV, bool STATS, int PX, bool CHUNK>
+__device__ __forceinline__ void render_item(const RenderArgs &a,
+                                            RSmem<B, FOV, MV, STATS, PX> &sm,
+                                            const uint32_t *vals, long long t, uint32_t c,
+                                            unsigned long long slot, uint32_t nc) {
+  using G = WarpGeom<B, PX>;
+  constexpr int NACC = FOV ? 2 : 1;
+  constexpr size_t BB = (size_t)B * B;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lx = (warp % G::kWx) * 8 + (lane & 7);
+  const int ly0 = (warp / G::kWx) * G::kRows + (lane >> 3);
+  Pix<PX> pp;
+  Acc A[PX], Bq[PX];
+  float dom_w[PX];
+  uint32_t dom_gid[PX];
+  uint32_t inb = 0;                // bits: inside k, in band PX + k
+  uint32_t begin, end, origin;
+  int tx0, ty0;
+  {
+    const int vidx = find_view(a.views, a.V, t);
+    const ViewDev vd = a.views[vidx];
+    const int local = (int)(t - vd.tile_base);
+    tx0 = (local % vd.tx) * B;
+    ty0 = (local / vd.tx) * B;
+    const uint2 rg = a.ranges[t];
+    origin = rg.x;
+    begin = rg.x;
+    end = rg.y;
+    if (CHUNK && nc) {
+      begin = rg.x + c * (uint32_t)a.chunk;
+      end = min(rg.y, begin + (uint32_t)a.chunk);
+    }
+    pp.px = (float)lx + 0.5f;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+      int x, y;
+      bool inside, in_band;
+      float wband;
+      pixel_of<B, FOV, PX>(a, vd, tx0, ty0, k, x, y, pp.lvl[k], inside, in_band, wband);
+      pp.py[k] = (float)(ly0 + 4 * k) + 0.5f;
+      inb |= (inside ? 1u : 0u) << k;
+      inb |= (inside && in_band ? 1u : 0u) << (PX + k);
+      A[k] = Acc{0.f, 0.f, 0.f, 1.f, -1, !inside};
+      Bq[k] = Acc{0.f, 0.f, 0.f, 1.f, -1, !(inside && in_band)};
+      dom_w[k] = -1.0f;
+      dom_gid[k] = 0;
+    }
+    if (CHUNK && tid == 0) {
+      sm.abort = 0;
+      sm.it.t = t;
+      sm.it.slot = slot;
+      sm.it.nc = nc;
+      sm.it.c = c;
+      sm.it.vidx = vidx;
+      sm.it.tx0 = tx0;
+      sm.it.ty0 = ty0;
+      sm.it.origin = origin;
+      sm.it.end = rg.y;
+      sm.it.merging = 0;
+    }
+  }
+  uint32_t n_blend = 0;
+  uint32_t walk_end[PX];                 // list positions walked until the stop
+#pragma unroll
+  for (int k = 0; k < PX; ++k) walk_end[k] = 0;
+
+  // One walk call site (the loop keeps a single inlined copy): the item's
+  // own walk, then, for the last chunk of a heavy tile to finish, the merge
+  // with its re-walks of the chunks in which an early stop falls.  Item
+  // constants are re-read from shared memory after each walk.
+  uint32_t fix = 0, keep = 0;      // per accumulator bits: k (A), PX + k (B)
+  const uint32_t *stop_c = (CHUNK && nc && c > 0) ? &a.chunk_tile[t].z : nullptr;
+  for (;;) {
+    walk<B, FOV, MV, STATS, PX>(a, sm, vals, tx0, ty0, begin, end, origin, pp, A, Bq, dom_w,
+                                dom_gid, n_blend, walk_end, stop_c, c);
+    stop_c = nullptr;   // re-walks of the merge run to their stop
+    if (!CHUNK) break;
+    const uint32_t inc = sm.it.nc;
+    if (inc == 0) break;
+    uint32_t cc;
+    if (!sm.it.merging) {
+      // partial result of this chunk; T negated where the chunk's walk stopped
+      const unsigned long long sl = sm.it.slot;
+      const bool aborted = sm.abort;
+      bool all_stopped = true;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) all_stopped = all_stopped && A[k].done && Bq[k].done;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) {
+        if (aborted || !((inb >> k) & 1u)) continue;
+        const size_t i = sl * NACC * BB + (size_t)((ly0 + 4 * k) * B + lx);
+        a.part_ct[i] = make_float4(A[k].r, A[k].g, A[k].b, A[k].done ? -A[k].T : A[k].T);
+        a.part_last[i] = A[k].last;
+        if (FOV && ((inb >> (PX + k)) & 1u)) {
+          a.part_ct[i + BB] =
+              make_float4(Bq[k].r, Bq[k].g, Bq[k].b, Bq[k].done ? -Bq[k].T : Bq[k].T);
+          a.part_last[i + BB] = Bq[k].last;
+        }
+      }
+      __threadfence();
+      all_stopped = __syncthreads_and(all_stopped) && !aborted;
+      if (tid == 0) {
+        const long long tt = sm.it.t;
+        if (all_stopped) atomicMin(&a.chunk_tile[tt].z, sm.it.c);
+        sm.flag = atomicAdd(&a.chunk_tile[tt].y, 1u) == inc - 1;
+        sm.it.first = a.chunk_tile[tt].x;
+        sm.it.merging = 1;
+      }
+      __syncthreads();
+      if (!sm.flag) return;
+      __threadfence();
+      // last to arrive: merge the chunks in list order
+      cc = 0;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) {
+        A[k] = Acc{0.f, 0.f, 0.f, 1.f, -1, !((inb >> k) & 1u)};
+        Bq[k] = Acc{0.f, 0.f, 0.f, 1.f, -1, !((inb >> (PX + k)) & 1u)};
+      }
+    } else {
+      // chunk cc re-walked: accumulators that sat it out resume their state
+#pragma unroll
+      for (int k = 0; k < PX; ++k) {
+        if (!((fix >> k) & 1u)) A[k].done = (keep >> k) & 1u;
+        if (!((fix >> (PX + k)) & 1u)) Bq[k].done = (keep >> (PX + k)) & 1u;
+      }
+      cc = sm.it.cc + 1;
+    }
+    const unsigned long long fs = sm.it.first;
+    bool rewalk = false;
+    for (; cc < inc; ++cc) {
+      fix = 0;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) {
+        const size_t i = (fs + cc) * NACC * BB + (size_t)((ly0 + 4 * k) * B + lx);
+        if (!A[k].done && merge_chunk(A[k], __ldcg(&a.part_ct[i]), __ldcg(&a.part_last[i])))
+          fix |= 1u << k;
+        if (FOV && !Bq[k].done &&
+            merge_chunk(Bq[k], __ldcg(&a.part_ct[i + BB]), __ldcg(&a.part_last[i + BB])))
+          fix |= 1u << (PX + k);
+      }
+      if (__syncthreads_or(fix != 0)) {
+        rewalk = true;
+        break;
+      }
+    }
+    if (!rewalk) break;
+    // re-walk chunk cc for the accumulators whose stop falls inside it
+    keep = 0;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+      keep |= (A[k].done ? 1u : 0u) << k;
+      keep |= (Bq[k].done ? 1u : 0u) << (PX + k);
+      A[k].done = !((fix >> k) & 1u);
+      Bq[k].done = !((fix >> (PX + k)) & 1u);
+    }
+    if (tid == 0) sm.it.cc = cc;
+    tx0 = sm.it.tx0;
+    ty0 = sm.it.ty0;
+    origin = sm.it.origin;
+    begin = origin + cc * (uint32_t)a.chunk;
+    end = min(sm.it.end, begin + (uint32_t)a.chunk);
+  }
+
+  // output
+  const ViewDev vd = a.views[CHUNK ? sm.it.vidx : find_view(a.views, a.V, t)];
+  if (CHUNK) {
+    tx0 = sm.it.tx0;
+    ty0 = sm.it.ty0;
+  }
   if (STATS) {
     // block totals of list positions walked until the stop (the same count
     // with or without culling) and of blends (accumulator A)
+    const uint2 rg = a.ranges[t];
     unsigned long long e = 0, bl2 = n_blend;
 #pragma unroll
     for (int k = 0; k < PX; ++k)
-      if (inside[k]) e += (A[k].done && walk_end[k] > 0) ? walk_end[k] : (rg.y - rg.x);
+      if ((inb >> k) & 1u) e += (A[k].done && walk_end[k] > 0) ? walk_end[k] : (rg.y - rg.x);
     for (int o = 16; o > 0; o >>= 1) {
       e += __shfl_xor_sync(0xffffffffu, e, o);
       bl2 += __shfl_xor_sync(0xffffffffu, bl2, o);
@@ -308,22 +547,26 @@ __global__ void __launch_bounds__(B * B / PX, 1024 / (B * B / PX)) k_render(Rend
   }
 #pragma unroll
   for (int k = 0; k < PX; ++k) {
-    if (!inside[k]) continue;
-    const long long pix = vd.pix_base + (long long)y[k] * vd.W + x[k];
+    int x, y, lvl;
+    bool inside, in_band;
+    float wband;
+    pixel_of<B, FOV, PX>(a, vd, tx0, ty0, k, x, y, lvl, inside, in_band, wband);
+    if (!inside) continue;
+    const long long pix = vd.pix_base + (long long)y * vd.W + x;
     float r = fmaf(A[k].T, a.bg0, A[k].r), g = fmaf(A[k].T, a.bg1, A[k].g),
           bl = fmaf(A[k].T, a.bg2, A[k].b);
     if (FOV) {
-      if (in_band[k]) {
+      if (in_band) {
         const float rb = fmaf(Bq[k].T, a.bg0, Bq[k].r), gb = fmaf(Bq[k].T, a.bg1, Bq[k].g),
                     bb = fmaf(Bq[k].T, a.bg2, Bq[k].b);
-        r = fmaf(wband[k], r - rb, rb);
-        g = fmaf(wband[k], g - gb, gb);
-        bl = fmaf(wband[k], bl - bb, bb);
+        r = fmaf(wband, r - rb, rb);
+        g = fmaf(wband, g - gb, gb);
+        bl = fmaf(wband, bl - bb, bb);
       }
       a.T[2 * pix] = A[k].T;
-      a.T[2 * pix + 1] = in_band[k] ? Bq[k].T : 1.0f;
+      a.T[2 * pix + 1] = in_band ? Bq[k].T : 1.0f;
       a.last[2 * pix] = A[k].last;
-      a.last[2 * pix + 1] = in_band[k] ? Bq[k].last : -1;
+      a.last[2 * pix + 1] = in_band ? Bq[k].last : -1;
     } else {
       a.T[pix] = A[k].T;
       a.last[pix] = A[k].last;
@@ -332,6 +575,66 @@ __global__ void __launch_bounds__(B * B / PX, 1024 / (B * B / PX)) k_render(Rend
     a.rgb[3 * pix + 1] = g;
     a.rgb[3 * pix + 2] = bl;
     if (STATS && A[k].last >= 0) atomicAdd(&a.stats[3 * a.n + dom_gid[k]], 1u);
+  }
+}
+
+// Whole tiles (CHUNK = false): one block per tile.  Chunked (CHUNK = true):
+// persistent blocks take work items from a queue -- first the chunks of the
+// heavy tiles, then the remaining tiles in order.
+template <int B, bool FOV, bool MV, bool STATS, int PX, bool CHUNK>
+__global__ void __launch_bounds__(B * B / PX, (CHUNK ? 768 : 1024) / (B * B / PX))
+    k_render(RenderArgs a) {
+  __shared__ RSmem<B, FOV, MV, STATS, PX> sm;
+  const uint32_t *vals = *a.sel ? a.pval_b : a.pval_a;
+  if (!CHUNK) {
+    render_item<B, FOV, MV, STATS, PX, false>(a, sm, vals, blockIdx.x, 0, 0, 0);
+    return;
+  }
+  const unsigned long long ns = min((unsigned long long)*a.n_slots, a.ch_cap);
+  const unsigned long long total = ns + (unsigned long long)a.tiles;
+  for (;;) {
+    if (threadIdx.x == 0) sm.item = atomicAdd(a.queue, 1ull);
+    __syncthreads();
+    const unsigned long long item = sm.item;
+    __syncthreads();
+    if (item >= total) break;
+    if (item < ns) {
+      const uint2 cl = a.chunk_list[item];
+      if (cl.y == kNoChunk) continue;   // slot of a tile that did not fit
+      const uint2 rg = a.ranges[cl.x];
+      const uint32_t nc = (rg.y - rg.x + (uint32_t)a.chunk - 1) / (uint32_t)a.chunk;
+      render_item<B, FOV, MV, STATS, PX, true>(a, sm, vals, cl.x, cl.y, item, nc);
+    } else {
+      const long long t = (long long)(item - ns);
+      if (a.chunk_tile[t].x != kNoChunk) continue;   // rendered as chunks
+      render_item<B, FOV, MV, STATS, PX, true>(a, sm, vals, t, 0, 0, 0);
+    }
+  }
+}
+
+// Work list of the chunked render: a tile longer than `chunk` points gets
+// ceil(len / chunk) consecutive chunk slots.  Tiles that do not fit the
+// slot capacity are rendered whole (their slots are marked unused).
+__global__ void k_chunk_plan(const uint2 *ranges, long long tiles, uint32_t chunk,
+                             unsigned long long cap, uint32_t *n_slots, uint4 *chunk_tile,
+                             uint2 *chunk_list) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tiles;
+       t += (long long)gridDim.x * blockDim.x) {
+    const uint2 rg = ranges[t];
+    const uint32_t len = rg.y - rg.x;
+    uint32_t first = kNoChunk;
+    if (len > chunk) {
+      const uint32_t nc = (len + chunk - 1) / chunk;
+      const unsigned long long b = atomicAdd(n_slots, nc);
+      if (b + nc <= cap) {
+        first = (uint32_t)b;
+        for (uint32_t c = 0; c < nc; ++c) chunk_list[b + c] = make_uint2((uint32_t)t, c);
+      } else {
+        for (unsigned long long s = b; s < b + nc && s < cap; ++s)
+          chunk_list[s] = make_uint2((uint32_t)t, kNoChunk);
+      }
+    }
+    chunk_tile[t] = make_uint4(first, 0u, kNoChunk, 0u);
   }
 }
 
@@ -349,24 +652,40 @@ __global__ void k_tiles_touched(const uint32_t *count, const uint32_t *gid,
 }
 
 template <int B, bool FOV, bool MV, bool STATS>
-static void launch_t(const RenderArgs &a, long long tiles, cudaStream_t s) {
+static void launch_t(const RenderArgs &a, long long tiles, bool chunked, int num_sms,
+                     cudaStream_t s) {
   // plain views: two pixels per thread; foveated: one (two accumulators)
   constexpr int PX = FOV ? 1 : 2;
-  k_render<B, FOV, MV, STATS, PX><<<(unsigned)tiles, B * B / PX, 0, s>>>(a);
+  constexpr int NT = B * B / PX;
+  if (STATS || !chunked) {
+    k_render<B, FOV, MV, STATS, PX, false><<<(unsigned)tiles, NT, 0, s>>>(a);
+    return;
+  }
+  // persistent blocks: as many as stay resident
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<B, FOV, MV, false, PX, true>,
+                                                      NT, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+  }
+  unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)(num_sms > 0 ? num_sms : 1);
+  const unsigned long long items = a.ch_cap + (unsigned long long)tiles;
+  if (grid > items) grid = items;
+  k_render<B, FOV, MV, false, PX, true><<<(unsigned)grid, NT, 0, s>>>(a);
 }
 
 template <int B>
 static void launch_b(const RenderArgs &a, bool fov, bool mv, bool stats, long long tiles,
-                     cudaStream_t s) {
+                     bool chunked, int num_sms, cudaStream_t s) {
   if (!fov) {
-    if (stats) launch_t<B, false, false, true>(a, tiles, s);
-    else launch_t<B, false, false, false>(a, tiles, s);
+    if (stats) launch_t<B, false, false, true>(a, tiles, chunked, num_sms, s);
+    else launch_t<B, false, false, false>(a, tiles, chunked, num_sms, s);
   } else if (!mv) {
-    if (stats) launch_t<B, true, false, true>(a, tiles, s);
-    else launch_t<B, true, false, false>(a, tiles, s);
+    if (stats) launch_t<B, true, false, true>(a, tiles, chunked, num_sms, s);
+    else launch_t<B, true, false, false>(a, tiles, chunked, num_sms, s);
   } else {
-    if (stats) launch_t<B, true, true, true>(a, tiles, s);
-    else launch_t<B, true, true, false>(a, tiles, s);
+    if (stats) launch_t<B, true, true, true>(a, tiles, chunked, num_sms, s);
+    else launch_t<B, true, true, false>(a, tiles, chunked, num_sms, s);
   }
 }
 
@@ -412,8 +731,30 @@ cudaError_t launch_render(const gs_plan *p, void *ws, bool fov, const float bg[3
   a.n_evals = &hdr->n_evals;
   a.n_blends = &hdr->n_blends;
   const bool mv = fov && p->fov_mv;
-  if (p->tile == 16) launch_b<16>(a, fov, mv, stats != nullptr, p->tiles_total, s);
-  else launch_b<8>(a, fov, mv, stats != nullptr, p->tiles_total, s);
+  // heavy-tile chunking (not for statistics renders, whose per-point
+  // counters need each tile walked once, in order)
+  const bool chunked = p->chunk > 0 && !stats && p->bytes[R_CHUNK_PART] > 0;
+  if (chunked) {
+    a.chunk = p->chunk;
+    a.tiles = p->tiles_total;
+    a.chunk_list = region<uint2>(p, ws, R_WORK);
+    a.chunk_tile = region<uint4>(p, ws, R_CHUNK_TILE);
+    a.part_ct = region<float4>(p, ws, R_CHUNK_PART);
+    a.part_last = region<int32_t>(p, ws, R_CHUNK_LAST);
+    a.ch_cap = (unsigned long long)p->chunk_cap;
+    a.n_slots = &hdr->n_slots;
+    a.queue = &hdr->queue;
+    cudaError_t e = cudaMemsetAsync(&hdr->queue, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const long long T = p->tiles_total;
+    const unsigned blocks = (unsigned)((T + 255) / 256 < 4096 ? (T + 255) / 256 : 4096);
+    k_chunk_plan<<<blocks, 256, 0, s>>>(a.ranges, T, (uint32_t)p->chunk, a.ch_cap, &hdr->n_slots,
+                                        a.chunk_tile, region<uint2>(p, ws, R_WORK));
+  }
+  if (p->tile == 16)
+    launch_b<16>(a, fov, mv, stats != nullptr, p->tiles_total, chunked, p->num_sms, s);
+  else
+    launch_b<8>(a, fov, mv, stats != nullptr, p->tiles_total, chunked, p->num_sms, s);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ class gs_fov(C.Structure):
 
 class gs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("chunk", C.c_int32), ("flags", C.c_int32),
-                ("max_levels", C.c_int32), ("radix_bits", C.c_int32), ("reserved2", C.c_int32),
+                ("max_levels", C.c_int32), ("radix_bits", C.c_int32), ("chunk_slots", C.c_int32),
                 ("max_pairs", C.c_int64)]
 
 
@@ -211,14 +211,15 @@ class Renderer:
     """
 
     def __init__(self, n, sh_degree, cams, tile=16, foveated=False, backward=False,
-                 max_pairs=0, max_levels=0, chunk=0, radix_bits=0, device="cuda"):
+                 max_pairs=0, max_levels=0, chunk=0, radix_bits=0, chunk_slots=0,
+                 device="cuda"):
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cams_np = np.asarray(cams, np.float32).reshape(-1, 20)
         self.V = len(self.cams_np)
         self.device = device
         self.cfg = gs_config(tile, chunk, (GS_FLAG_FOVEATED if foveated else 0)
                              | (GS_FLAG_BACKWARD if backward else 0), max_levels,
-                             radix_bits, 0, max_pairs)
+                             radix_bits, chunk_slots, max_pairs)
         self.plan = C.create_string_buffer(int(_lib.gs_plan_size()))
         self._cams_h = cams_host(self.cams_np)
         gs_plan_init(self.plan, self.n, self.sh_degree, self._cams_h, self.V, self.cfg)
@@ -311,6 +312,8 @@ class Renderer:
         # pair sort (scan + passes), ranges
         sort = 0 if self.n == 0 else 6 + 1 + 2 + (1 + passes) + 1
         render = 1 + (1 if stats and self.n > 0 else 0)
+        if self.cfg.chunk > 0 and not stats and self.T_tiles > 0:
+            render += 1     # work list of the chunked render
         return project + sort + render
 
     def counters(self, stream=None):

@@ -37,7 +37,18 @@ def test_plan_init_validates_on_host(lib):
     assert lib.gs_plan_init(plan, -1, 0, cams, 1, None) == gs.GS_ERR_INVALID_ARG
     bad = gs.gs_config(12, 0, 0, 0, 0, 0)
     assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(bad)) == gs.GS_ERR_INVALID_ARG
+    for cfg in (gs.gs_config(16, 0, 0, 0, 3, 0, 0),      # digit width below 4
+                gs.gs_config(16, 0, 0, 0, 9, 0, 0),      # digit width above 8
+                gs.gs_config(16, 32, 0, 0, 0, 0, 0),     # chunk below 64 points
+                gs.gs_config(16, 256, 0, 0, 0, -1, 0)):  # negative chunk slots
+        assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(cfg)) == gs.GS_ERR_INVALID_ARG
+    lib.gs_workspace_size.argtypes = [C.c_void_p]
+    lib.gs_workspace_size.restype = C.c_size_t
+    # chunking reserves its slots; a plan without it does not
+    assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(gs.gs_config(16, 256, 0, 0, 0, 0, 0))) == gs.GS_OK
+    ws_chunked = lib.gs_workspace_size(plan)
     assert lib.gs_plan_init(plan, 100, 0, cams, 1, None) == gs.GS_OK
+    assert lib.gs_workspace_size(plan) < ws_chunked
     lib.gs_plan_tiles.argtypes = [C.c_void_p]
     lib.gs_plan_tiles.restype = C.c_int64
     lib.gs_plan_pixels.argtypes = [C.c_void_p]
