@@ -86,7 +86,6 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   const long long M = p->max_visible > 0 ? p->max_visible : 1;
   const long long K = p->max_pairs;
   const long long T = tiles > 0 ? tiles : 1;
-  const long long parts = ((M > K ? M : K) + kSortPart - 1) / kSortPart;
   size_t b[R_COUNT_] = {};
   b[R_HDR] = sizeof(Hdr);
   b[R_VIEWS] = sizeof(ViewDev) * (size_t)V;
@@ -118,8 +117,10 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   b[R_CHUNK_TILE] = p->chunk > 0 ? 16 * (size_t)T : 0;
   b[R_CHUNK_PART] = 16 * nacc * tpx * (size_t)p->chunk_cap;
   b[R_CHUNK_LAST] = 4 * nacc * tpx * (size_t)p->chunk_cap;
-  b[R_SCAN] = 8 * (size_t)((M + kSortPart - 1) / kSortPart + 1);
-  b[R_LOOKBACK] = 2 * 256 * 8 * (size_t)(parts > 0 ? parts : 1);
+  // block table of the reduce-then-scan sort (grid <= SMs x resident blocks)
+  p->sort_blocks = (p->num_sms > 0 ? p->num_sms : 160) * kSortBlocksPerSm;
+  if (p->sort_blocks > kSortMaxBlocks) p->sort_blocks = kSortMaxBlocks;
+  b[R_BSUM] = (256 * sizeof(uint32_t) * kSortSub + sizeof(unsigned long long)) * (size_t)p->sort_blocks;
   b[R_GRAD_ITEM] = bwd ? 16 * sizeof(float) * (size_t)M : 0;
   b[R_GRAD_LV] = (bwd && fov) ? 4 * sizeof(float) * (size_t)(max_levels - 1) * (size_t)M : 0;
   size_t off = 0;

@@ -54,8 +54,8 @@ enum Region : int {
                  //   first chunk that stopped every pixel, -)
   R_CHUNK_PART,  // float4 per (slot, accumulator, pixel): partial (r, g, b, T)
   R_CHUNK_LAST,  // i32 per (slot, accumulator, pixel): partial last position
-  R_SCAN,        // u64 look-back slots of the pair-offset scan
-  R_LOOKBACK,    // u64 radix lookback slots, two buffers
+  R_BSUM,        // u32 [G][256] per-block digit counts of a sort pass, then
+                 //   u64 [G] per-block sums of the pair-offset scan
   R_GRAD_ITEM,   // float per item gradient scratch (backward)
   R_GRAD_LV,     // float per (level, item) gradient scratch (backward, foveated)
   R_COUNT_
@@ -71,7 +71,7 @@ struct Hdr {
   unsigned long long n_nonfinite;
   unsigned long long n_evals;     // (pixel, point) evaluations of the last stats render
   unsigned long long n_blends;    // blends of the last stats render
-  uint32_t ticket[32];            // partition tickets of lookback kernels
+  uint32_t ticket[32];            // work tickets (projection)
   uint32_t sel_depth;             // buffer holding the sorted depth order (0 = A)
   uint32_t sel_pair;              // buffer holding the sorted pairs (0 = A)
   uint32_t skip[8];               // per-pass "digit constant" flags
@@ -104,6 +104,9 @@ constexpr int kSpinLimit = 1 << 20;   // bounded waits (about a second), then GS
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortPart = kSortThreads * kSortItems;   // 4096 keys per partition
+constexpr int kSortBlocksPerSm = 8;   // most sort blocks resident per SM (sizes the block table)
+constexpr int kSortMaxBlocks = 1024;  // grid cap of the sort's downsweep
+constexpr int kSortSub = 4;           // upsweep sub-ranges per downsweep block
 constexpr int kProjThreads = 128;
 
 }  // namespace gs
@@ -120,6 +123,7 @@ struct gs_plan {
   int32_t tile_bits;
   int32_t radix_bits;     // requested digit width of the pair sort (0 = balanced)
   int64_t chunk_cap;      // chunk slots of the chunked render (0 = whole tiles only)
+  int32_t sort_blocks;    // rows of the sort's block table (grid upper bound)
   int32_t last_fov;       // last render was foveated
   size_t off[gs::R_COUNT_];
   size_t bytes[gs::R_COUNT_];

@@ -8,19 +8,27 @@
 // Together they order the pairs by (tile, depth, point index), the same
 // order as one stable sort of (tile << 32 | depth) keys.
 //
-// Each radix pass is a single "onesweep" kernel: persistent blocks take
-// 4096-key partitions by atomic ticket, rank digits inside each warp with
-// __match_any_sync, publish per-digit partition counts and look back over
-// their predecessors (decoupled look-back, bounded spin) to get global
-// positions, then scatter.  A pass whose digit is the same for all keys is
-// skipped on the device.
+// Each radix pass is reduce-then-scan over a fixed grid of G blocks, block b
+// owning one contiguous range of 4096-key partitions:
+//   upsweep    per-block digit counts of the range            (reads keys)
+//   scan       per digit, exclusive scan over the G blocks, plus the
+//              digit's global start                            (G x 256)
+//   downsweep  the block walks its partitions in order with a running
+//              per-digit carry (next partition prefetched by bulk copy):
+//              rank digits inside each warp (peer lanes by one ballot per
+//              digit bit), stage the partition in digit order in shared
+//              memory, write runs of equal digits contiguously.
+// No block waits for another (no look-back chain, no spin).  The global
+// histograms of every pass come from one read of the keys (or from the
+// emit); a pass whose digit is the same for all keys is skipped on the
+// device.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
 
 #include "gs_internal.cuh"
-#include "lookback.cuh"
+#include "tma.cuh"
 
 namespace gs {
 
@@ -34,9 +42,8 @@ struct SortArgs {
   uint32_t *sel;                     // out: buffer index holding the result
   uint32_t *hist;                    // [4][256] digit histograms -> offsets
   uint32_t *skip;                    // [4] pass skipped (constant digit)
-  uint32_t *tickets;                 // [4] partition tickets
-  unsigned long long *lb;            // [2][max_parts][256] look-back slots
-  long long max_parts;
+  uint32_t *bsum;                    // [G][256] per-block digit counts -> bases
+  int blocks;                        // G, the grid of upsweep and downsweep
   int passes;
   int digit_bits;                    // bits per pass (<= 8)
   int no_skip;                       // run every pass (fixed buffer parity)
@@ -55,34 +62,76 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// ---- histograms of every pass in one read; also resets tickets and the
-// first look-back buffer -------------------------------------------------
+// Partition ranges: downsweep block b of G owns partitions [b q, (b + 1) q),
+// q = ceil(parts / G).  The upsweep splits each block's key range into
+// kSortSub equal pieces (it only counts, so any split is fine); row s of
+// the block table belongs to piece s % kSortSub of block s / kSortSub.
+__device__ __forceinline__ void block_parts(uint32_t n, int G, int b, long long &p0, long long &p1) {
+  const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
+  const long long q = (nparts + G - 1) / G;
+  p0 = (long long)b * q < nparts ? (long long)b * q : nparts;
+  p1 = p0 + q < nparts ? p0 + q : nparts;
+}
+
+__device__ __forceinline__ void sub_keys(uint32_t n, int G, long long s, long long &k0,
+                                         long long &k1) {
+  long long p0, p1;
+  block_parts(n, G, (int)(s / kSortSub), p0, p1);
+  const long long b0 = p0 * kSortPart;
+  const long long b1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
+  const long long len = b1 > b0 ? b1 - b0 : 0;
+  const long long j = s % kSortSub;
+  k0 = b0 + len * j / kSortSub;
+  k1 = b0 + len * (j + 1) / kSortSub;
+}
+
+// Input buffers of pass `pass`: the first executed pass reads the caller's
+// arrays, later ones the ping-pong buffer the previous executed pass wrote.
+__device__ __forceinline__ int passes_before(const SortArgs &a, int pass) {
+  int before = 0;
+  for (int p = 0; p < pass; ++p) before += a.skip[p] ? 0 : 1;
+  return before;
+}
+
+// Adds digit d of the valid lanes to a shared histogram; a warp whose
+// valid lanes share one digit (common for the high bytes of depth keys)
+// adds once.
+__device__ __forceinline__ void warp_count(uint32_t *h, bool valid, uint32_t d, int lane) {
+  const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+  if (!vmask) return;
+  const uint32_t d0 = __shfl_sync(0xffffffffu, d, __ffs(vmask) - 1);
+  if (__all_sync(0xffffffffu, !valid || d == d0)) {
+    if (lane == __ffs(vmask) - 1) atomicAdd(&h[d0], (uint32_t)__popc(vmask));
+  } else if (valid) {
+    atomicAdd(&h[d], 1u);
+  }
+}
+
+// ---- histograms of every pass in one read of the keys ---------------------
+constexpr int kHistUnroll = 8;
+
 __global__ void __launch_bounds__(256) k_hist(SortArgs a) {
   __shared__ uint32_t sh[4][256];
   const uint32_t n = sort_n(a);
   for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  // warp-uniform trip count so that __match_any_sync sees the full warp
-  const long long start = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long iters = ((long long)n + stride - 1) / stride;
-  for (long long it = 0; it < iters; ++it) {
-    long long idx = start + it * stride;
-    bool valid = idx < (long long)n;
-    uint32_t key = valid ? a.first_keys[idx] : 0u;
-    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-    const uint32_t dmask = (1u << a.digit_bits) - 1u;
-    for (int p = 0; p < a.passes; ++p) {
-      const uint32_t d = (key >> (a.digit_bits * p)) & dmask;
-      // a warp whose valid keys share the digit adds once (common for the
-      // high bytes of depth keys); otherwise every lane adds
-      const uint32_t d0 = __shfl_sync(0xffffffffu, d, __ffs(vmask | 1u) - 1);
-      if (__all_sync(0xffffffffu, !valid || d == d0)) {
-        if (lane == 0 && vmask) atomicAdd(&sh[p][d0], (uint32_t)__popc(vmask));
-      } else if (valid) {
-        atomicAdd(&sh[p][d], 1u);
-      }
+  const long long stride = (long long)gridDim.x * blockDim.x * kHistUnroll;
+  const uint32_t dmask = (1u << a.digit_bits) - 1u;
+  // warp-uniform trip count so that the warp votes see the full warp
+  for (long long base = (long long)blockIdx.x * blockDim.x * kHistUnroll; base < (long long)n;
+       base += stride) {
+    uint32_t key[kHistUnroll];
+#pragma unroll
+    for (int u = 0; u < kHistUnroll; ++u) {
+      const long long idx = base + u * blockDim.x + threadIdx.x;
+      key[u] = idx < (long long)n ? a.first_keys[idx] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kHistUnroll; ++u) {
+      const bool valid = base + u * blockDim.x + threadIdx.x < (long long)n;
+      for (int p = 0; p < a.passes; ++p)
+        warp_count(sh[p], valid, (key[u] >> (a.digit_bits * p)) & dmask, lane);
     }
   }
   __syncthreads();
@@ -90,10 +139,6 @@ __global__ void __launch_bounds__(256) k_hist(SortArgs a) {
     uint32_t c = (&sh[0][0])[q];
     if (c) atomicAdd(&a.hist[q], c);
   }
-  // reset look-back buffer 0 for the partitions this sort will use
-  const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
-  for (long long q = start; q < nparts * 256; q += stride) a.lb[q] = 0ull;
-  if (blockIdx.x == 0 && threadIdx.x < 4) a.tickets[threadIdx.x] = 0u;
 }
 
 // exclusive scan of each pass's histogram; constant-digit passes skipped
@@ -127,157 +172,256 @@ __global__ void __launch_bounds__(256) k_hist_scan(SortArgs a) {
   if (t == 0) *a.sel = (uint32_t)(executed & 1);
 }
 
-// ---- one onesweep pass -----------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass) {
-  __shared__ uint32_t s_wh[kSortThreads / 32][256];
-  __shared__ uint32_t s_base[256];
-  __shared__ uint32_t s_dstart[256];
-  __shared__ uint32_t s_key[kSortPart];
-  __shared__ uint32_t s_val[kSortPart];
-  __shared__ uint32_t s_part;
-  __shared__ uint32_t s_wsum[kSortThreads / 32];
+// ---- upsweep: digit counts of each sub-range (kSortSub x G blocks) ------------
+constexpr int kUpUnroll = 8;
+
+__global__ void __launch_bounds__(kSortThreads) k_upsweep(SortArgs a, int pass) {
+  __shared__ uint32_t s_h[kSortThreads / 32][256];
+  if (a.skip[pass]) return;
   const uint32_t n = sort_n(a);
-  const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
-  unsigned long long *lb_next = a.lb + (long long)((pass + 1) & 1) * a.max_parts * 256;
-  if (a.skip[pass]) {
-    // keep the next pass's look-back buffer clean even though this one idles
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nparts * 256;
-         q += stride)
-      lb_next[q] = 0ull;
-    return;
+  const int before = passes_before(a, pass);
+  const uint32_t *kin = before == 0 ? a.first_keys : ((before & 1) ? a.keys[1] : a.keys[0]);
+  const int shift = a.digit_bits * pass;
+  const uint32_t dmask = (1u << a.digit_bits) - 1u;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int q = tid; q < (kSortThreads / 32) * 256; q += kSortThreads) (&s_h[0][0])[q] = 0u;
+  __syncthreads();
+  long long k0, k1;
+  sub_keys(n, a.blocks, blockIdx.x, k0, k1);
+  constexpr int kStep = kSortThreads * kUpUnroll;
+  for (long long base = k0; base < k1; base += kStep) {
+    uint32_t key[kUpUnroll];
+#pragma unroll
+    for (int u = 0; u < kUpUnroll; ++u) {
+      const long long idx = base + u * kSortThreads + tid;
+      key[u] = idx < k1 ? kin[idx] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kUpUnroll; ++u) {
+      const long long idx = base + u * kSortThreads + tid;
+      warp_count(s_h[warp], idx < k1, (key[u] >> shift) & dmask, lane);
+    }
   }
-  unsigned long long *lb_cur = a.lb + (long long)(pass & 1) * a.max_parts * 256;
-  int before = 0;
-  for (int p = 0; p < pass; ++p) before += a.skip[p] ? 0 : 1;
-  const uint32_t *kin = before == 0 ? a.first_keys : a.keys[before & 1];
-  const uint32_t *vin = before == 0 ? a.first_vals : a.vals[before & 1];
-  uint32_t *kout = a.keys[(before + 1) & 1];
-  uint32_t *vout = a.vals[(before + 1) & 1];
+  __syncthreads();
+  uint32_t tot = 0;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) tot += s_h[w][tid];
+  a.bsum[(long long)blockIdx.x * 256 + tid] = tot;
+}
+
+// ---- scan: bsum[s][d] <- global start of digit d + its count in
+// sub-ranges < s.  One block per 32 digits; warp w owns a run of rows,
+// read kScanChunk rows at a time (independent loads).
+constexpr int kScanThreads = 1024;
+constexpr int kScanChunk = 16;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pass) {
+  __shared__ uint32_t s_p[kScanThreads / 32][32];
+  if (a.skip[pass]) return;
+  constexpr int NW = kScanThreads / 32;
+  const int R = kSortSub * a.blocks;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = blockIdx.x * 32 + lane;
+  const int rows = (R + NW - 1) / NW;
+  const int r0 = warp * rows;
+  const int r1 = r0 + rows < R ? r0 + rows : R;
+  uint32_t sum = 0;
+  for (int c = r0; c < r1; c += kScanChunk) {
+    uint32_t v[kScanChunk];
+#pragma unroll
+    for (int i = 0; i < kScanChunk; ++i) v[i] = c + i < r1 ? a.bsum[(long long)(c + i) * 256 + d] : 0u;
+#pragma unroll
+    for (int i = 0; i < kScanChunk; ++i) sum += v[i];
+  }
+  s_p[warp][lane] = sum;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t run = a.hist[pass * 256 + d];
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t c = s_p[w][lane];
+      s_p[w][lane] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  uint32_t run = s_p[warp][lane];
+  for (int c = r0; c < r1; c += kScanChunk) {
+    uint32_t v[kScanChunk];
+#pragma unroll
+    for (int i = 0; i < kScanChunk; ++i) v[i] = c + i < r1 ? a.bsum[(long long)(c + i) * 256 + d] : 0u;
+#pragma unroll
+    for (int i = 0; i < kScanChunk; ++i) {
+      if (c + i < r1) a.bsum[(long long)(c + i) * 256 + d] = run;
+      run += v[i];
+    }
+  }
+}
+
+// ---- downsweep: rank, stage in digit order, scatter -----------------------
+// Each block walks its partitions in order.  While one partition is ranked
+// and scattered, the next one's keys and values are already on their way
+// into the other half of a double buffer by two bulk copies (thread 0
+// issues them; an mbarrier per half counts the bytes in).  Partitions that
+// are not full, or inputs that are not 16-byte aligned, are read with plain
+// loads instead.
+struct DownSmem {
+  uint32_t in_k[2][kSortPart];
+  uint32_t in_v[2][kSortPart];
+  uint32_t key[kSortPart];            // staging in digit order
+  uint32_t val[kSortPart];
+  uint32_t wh[kSortThreads / 32][256];
+  uint32_t base[256], carry[256], dstart[256];
+  uint32_t wsum[kSortThreads / 32];
+  uint64_t bar[2];
+};
+
+__global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int pass) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  DownSmem &sm = *reinterpret_cast<DownSmem *>(dyn_smem);
+  if (a.skip[pass]) return;
+  const uint32_t n = sort_n(a);
+  const int before = passes_before(a, pass);
+  const bool odd = (before & 1) != 0;   // (no dynamic indexing of the parameter arrays)
+  const uint32_t *kin = before == 0 ? a.first_keys : (odd ? a.keys[1] : a.keys[0]);
+  const uint32_t *vin = before == 0 ? a.first_vals : (odd ? a.vals[1] : a.vals[0]);
+  uint32_t *kout = odd ? a.keys[0] : a.keys[1];
+  uint32_t *vout = odd ? a.vals[0] : a.vals[1];
   const bool iota = vin == nullptr;
   const int shift = a.digit_bits * pass;
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ltmask = lanemask_lt();
-  const uint32_t *goff = a.hist + pass * 256;
-
-  for (;;) {
-    if (tid == 0) s_part = atomicAdd(&a.tickets[pass], 1u);
-    for (int q = tid; q < (kSortThreads / 32) * 256; q += kSortThreads) (&s_wh[0][0])[q] = 0u;
-    __syncthreads();
-    const uint32_t part = s_part;
-    if ((long long)part >= nparts) break;
-    const long long wbase = (long long)part * kSortPart + warp * (32 * kSortItems);
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-      long long idx = wbase + k * 32 + lane;
-      bool valid = idx < (long long)n;
-      key[k] = valid ? kin[idx] : 0u;
-      val[k] = valid ? (iota ? (uint32_t)idx : vin[idx]) : 0u;
+  long long p0, p1;
+  block_parts(n, a.blocks, blockIdx.x, p0, p1);
+  if (p0 >= p1) return;
+  sm.carry[tid] = a.bsum[(long long)blockIdx.x * kSortSub * 256 + tid];   // 256 threads = digits
+  const bool aligned = ((uintptr_t)kin & 15u) == 0 && (iota || ((uintptr_t)vin & 15u) == 0);
+  const long long full = (long long)n / kSortPart;   // partitions [0, full) hold 4096 keys
+  constexpr uint32_t kBytes = kSortPart * sizeof(uint32_t);
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // block-uniform bookkeeping of the two halves: copies issued / consumed
+  uint32_t issued0 = 0, issued1 = 0, used0 = 0, used1 = 0;
+  auto issue = [&](long long part, int h) {
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(&sm.bar[h], iota ? kBytes : 2 * kBytes);
+      bulk_g2s(sm.in_k[h], kin + part * kSortPart, kBytes, &sm.bar[h]);
+      if (!iota) bulk_g2s(sm.in_v[h], vin + part * kSortPart, kBytes, &sm.bar[h]);
     }
-    // warp-level stable ranking (original order = (k, lane))
+    if (h) ++issued1; else ++issued0;
+  };
+  if (aligned && p0 < full) issue(p0, 0);
+  int h = 0;
+  for (long long part = p0; part < p1; ++part, h ^= 1) {
+    const bool bulk = aligned && part < full;
+    // the other half was last read before the barrier ending the previous
+    // partition: refill it with the next partition
+    if (part + 1 < p1 && aligned && part + 1 < full) issue(part + 1, h ^ 1);
+    for (int q = tid; q < (kSortThreads / 32) * 256; q += kSortThreads) (&sm.wh[0][0])[q] = 0u;
+    const long long wbase = part * kSortPart + warp * (32 * kSortItems);
+    const int lbase = warp * (32 * kSortItems);
+    uint32_t key[kSortItems], rank[kSortItems];
+    if (bulk) {
+      const uint32_t u = h ? used1 : used0;
+      const bool landed = mbar_wait_bounded(&sm.bar[h], u & 1u);
+      if (h) ++used1; else ++used0;
+      if (__syncthreads_or(!landed)) {
+        // give up: record it, let the copies in flight land, leave
+        if (tid == 0) set_status(a.status, GS_ERR_TIMEOUT);
+        if (issued0 > used0) mbar_wait_bounded(&sm.bar[0], used0 & 1u);
+        if (issued1 > used1) mbar_wait_bounded(&sm.bar[1], used1 & 1u);
+        return;
+      }
+#pragma unroll
+      for (int k = 0; k < kSortItems; ++k) key[k] = sm.in_k[h][lbase + k * 32 + lane];
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSortItems; ++k) {
+        const long long idx = wbase + k * 32 + lane;
+        key[k] = idx < (long long)n ? kin[idx] : 0u;
+      }
+    }
+    __syncthreads();
+    // warp-level stable ranking (original order = (k, lane)); the lanes
+    // holding the same digit are found with one ballot per digit bit
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       long long idx = wbase + k * 32 + lane;
       bool valid = idx < (long long)n;
       uint32_t d = (key[k] >> shift) & dmask;
-      uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
-      uint32_t before_w = valid ? s_wh[warp][d] : 0u;
+      uint32_t peers = __ballot_sync(0xffffffffu, valid);
+      if (!valid) peers = ~peers;
+#pragma unroll
+      for (int bit = 0; bit < 8; ++bit) {
+        if (bit < a.digit_bits) {
+          const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+          peers &= ((d >> bit) & 1u) ? bb : ~bb;
+        }
+      }
+      uint32_t before_w = valid ? sm.wh[warp][d] : 0u;
       rank[k] = before_w + __popc(peers & ltmask);
       __syncwarp();
-      if (valid && (__ffs(peers) - 1) == lane) s_wh[warp][d] = before_w + __popc(peers);
+      if (valid && (__ffs(peers) - 1) == lane) sm.wh[warp][d] = before_w + __popc(peers);
       __syncwarp();
     }
     __syncthreads();
-    // per digit: warp offsets inside the partition, then look-back
+    // per digit: warp offsets inside the partition, the running base, and
+    // the digit's start inside the partition (block exclusive scan)
     {
-      const int d = tid;  // kSortThreads == 256 digits
+      const int d = tid;
       uint32_t tot = 0;
 #pragma unroll
       for (int w = 0; w < kSortThreads / 32; ++w) {
-        uint32_t c = s_wh[w][d];
-        s_wh[w][d] = tot;
+        uint32_t c = sm.wh[w][d];
+        sm.wh[w][d] = tot;
         tot += c;
       }
-      unsigned long long *slot = lb_cur + (long long)part * 256 + d;
-      unsigned long long excl = 0;
-      if (part == 0) {
-        st_release_u64(slot, kFlagPre | tot);
-      } else {
-        st_release_u64(slot, kFlagAgg | tot);
-        // walk back kLbVec slots per step: the loads of one step are
-        // independent, so the chain costs one memory latency per kLbVec
-        // predecessors
-        constexpr int kLbVec = 16;
-        long long q = (long long)part - 1;
-        int spins = 0;
-        bool done = false;
-        while (!done && q >= 0) {
-          unsigned long long wv[kLbVec];
-#pragma unroll
-          for (int v = 0; v < kLbVec; ++v)
-            wv[v] = q - v >= 0 ? ld_relaxed_u64(lb_cur + (q - v) * 256 + d) : (kFlagPre | 0ull);
-          int used = 0;
-#pragma unroll
-          for (int v = 0; v < kLbVec; ++v) {
-            if (done || used < v) continue;       // stopped earlier in this step
-            const unsigned long long f = wv[v] >> 62;
-            if (f == 0ull) continue;               // not ready: retry from here
-            excl += wv[v] & kValMask;
-            if (f == 2ull) done = true;
-            used = v + 1;
-          }
-          q -= used;
-          if (!done && used < kLbVec) {
-            if (++spins > kSpinLimit) { set_status(a.status, GS_ERR_TIMEOUT); break; }
-            __nanosleep(20);
-          }
-        }
-        st_release_u64(slot, kFlagPre | (excl + tot));
-      }
-      s_base[d] = goff[d] + (uint32_t)excl;
-      lb_next[(long long)part * 256 + d] = 0ull;
-      // start of digit d inside the partition (block exclusive scan of tot)
+      sm.base[d] = sm.carry[d];
+      sm.carry[d] += tot;
       uint32_t incl = tot;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
       }
-      if (lane == 31) s_wsum[warp] = incl;
+      if (lane == 31) sm.wsum[warp] = incl;
       __syncthreads();
       uint32_t wofs = 0;
 #pragma unroll
-      for (int w = 0; w < kSortThreads / 32; ++w) wofs += w < warp ? s_wsum[w] : 0u;
-      s_dstart[d] = wofs + incl - tot;
+      for (int w = 0; w < kSortThreads / 32; ++w) wofs += w < warp ? sm.wsum[w] : 0u;
+      sm.dstart[d] = wofs + incl - tot;
     }
     __syncthreads();
     // stage the partition in digit order, then write runs of equal digits
     // to consecutive global addresses
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-      long long idx = wbase + k * 32 + lane;
+      const long long idx = wbase + k * 32 + lane;
       if (idx < (long long)n) {
         uint32_t d = (key[k] >> shift) & dmask;
-        uint32_t lp = s_dstart[d] + s_wh[warp][d] + rank[k];
-        s_key[lp] = key[k];
-        s_val[lp] = val[k];
+        uint32_t lp = sm.dstart[d] + sm.wh[warp][d] + rank[k];
+        sm.key[lp] = key[k];
+        sm.val[lp] = iota ? (uint32_t)idx : (bulk ? sm.in_v[h][lbase + k * 32 + lane] : vin[idx]);
       }
     }
     __syncthreads();
-    const long long pbase = (long long)part * kSortPart;
+    const long long pbase = part * kSortPart;
     const uint32_t pcount = (uint32_t)min((long long)kSortPart, (long long)n - pbase);
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       const uint32_t lp = (uint32_t)(k * kSortThreads + tid);
       if (lp < pcount) {
-        const uint32_t kk = s_key[lp];
+        const uint32_t kk = sm.key[lp];
         const uint32_t d = (kk >> shift) & dmask;
-        const uint32_t dst = s_base[d] + (lp - s_dstart[d]);
+        const uint32_t dst = sm.base[d] + (lp - sm.dstart[d]);
         if (dst < n) {
           kout[dst] = kk;
-          vout[dst] = s_val[lp];
+          vout[dst] = sm.val[lp];
         }
       }
     }
@@ -287,23 +431,45 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortArgs a, int pass)
 
 static int g_sort_blocks = 0;
 static int g_stream_blocks = 0;   // grid of the streaming kernels (emit, offsets, ranges, hist)
+static std::mutex g_grid_mu;
+static bool g_smem_attr[64] = {};
 
-static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = false) {
-  if (g_sort_blocks == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onesweep, kSortThreads, 0);
-    g_sort_blocks = sms * (per > 0 ? per : 1);
-    g_stream_blocks = sms * 8;
+static void init_grids() {
+  std::lock_guard<std::mutex> lock(g_grid_mu);
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  // the downsweep's shared memory exceeds the default 48 KB: opt in on
+  // every device that sorts
+  if (dev >= 0 && dev < 64 && !g_smem_attr[dev]) {
+    cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmem));
+    g_smem_attr[dev] = true;
   }
-  if (!hist_done) k_hist<<<g_stream_blocks, 256, 0, s>>>(a);
+  if (g_sort_blocks) return;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_downsweep, kSortThreads, sizeof(DownSmem));
+  if (sms < 1) sms = 1;
+  if (per > kSortBlocksPerSm) per = kSortBlocksPerSm;
+  g_sort_blocks = sms * (per > 0 ? per : 1);
+  g_stream_blocks = sms * 8;
+}
+
+// Runs every pass of one sort.  a.blocks must be set (at most the rows of
+// a.bsum).
+static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = false) {
+  if (!hist_done) k_hist<<<a.blocks, 256, 0, s>>>(a);
   k_hist_scan<<<1, 256, 0, s>>>(a);
-  for (int p = 0; p < a.passes; ++p) k_onesweep<<<g_sort_blocks, kSortThreads, 0, s>>>(a, p);
+  const unsigned scan_blocks = (1u << a.digit_bits) > 32 ? (1u << a.digit_bits) / 32 : 1u;
+  for (int p = 0; p < a.passes; ++p) {
+    k_upsweep<<<kSortSub * a.blocks, kSortThreads, 0, s>>>(a, p);
+    k_scan_blocks<<<scan_blocks, kScanThreads, 0, s>>>(a, p);
+    k_downsweep<<<a.blocks, kSortThreads, sizeof(DownSmem), s>>>(a, p);
+  }
   return cudaGetLastError();
 }
 
 // ---- exclusive scan of pair counts in depth order -> emit offsets --------
+// Reduce-then-scan over the same fixed block ranges as the sort passes.
 struct ScanArgs {
   const uint32_t *sorted_items[2];
   const uint32_t *sel;
@@ -311,33 +477,92 @@ struct ScanArgs {
   const unsigned long long *n_items;
   long long capacity;
   uint32_t *offsets;
-  unsigned long long *slots;
-  uint32_t *ticket;
+  unsigned long long *bsum;         // [G] block sums -> block bases
+  int blocks;
   unsigned long long *n_pairs;
-  uint32_t *status;
 };
 
-__global__ void __launch_bounds__(256) k_offsets(ScanArgs a) {
-  __shared__ uint32_t s_part;
-  __shared__ unsigned long long s_w[8];
-  __shared__ unsigned long long s_base;
+__device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
   unsigned long long nn = *a.n_items;
-  const uint32_t n = (uint32_t)((long long)nn > a.capacity ? a.capacity : (long long)nn);
-  const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
-  const uint32_t *items = a.sorted_items[*a.sel];
+  return (uint32_t)((long long)nn > a.capacity ? a.capacity : (long long)nn);
+}
+
+__global__ void __launch_bounds__(256) k_offsets_up(ScanArgs a) {
+  __shared__ unsigned long long s_w[8];
+  const uint32_t n = scan_n(a);
+  const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
+  long long p0, p1;
+  block_parts(n, a.blocks, blockIdx.x, p0, p1);
+  const long long k0 = p0 * kSortPart;
+  const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
+  unsigned long long sum = 0;
+  for (long long base = k0; base < k1; base += 256 * 16) {
+    uint32_t c[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const long long idx = base + u * 256 + threadIdx.x;
+      c[u] = idx < k1 ? a.count[items[idx]] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) sum += c[u];
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    a.bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_offsets_scan(ScanArgs a) {
+  __shared__ unsigned long long s_w[32];
+  const int G = a.blocks;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (G + 1023) / 1024;
+  const int r0 = threadIdx.x * per < G ? threadIdx.x * per : G;
+  const int r1 = r0 + per < G ? r0 + per : G;
+  unsigned long long local = 0;
+  for (int r = r0; r < r1; ++r) local += a.bsum[r];
+  unsigned long long incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  unsigned long long woff = 0, total = 0;
+  for (int w = 0; w < 32; ++w) {
+    if (w < warp) woff += s_w[w];
+    total += s_w[w];
+  }
+  unsigned long long run = woff + incl - local;
+  for (int r = r0; r < r1; ++r) {
+    const unsigned long long c = a.bsum[r];
+    a.bsum[r] = run;
+    run += c;
+  }
+  if (threadIdx.x == 0) *a.n_pairs = total;
+}
+
+__global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
+  __shared__ unsigned long long s_w[8];
+  __shared__ unsigned long long s_carry;
+  const uint32_t n = scan_n(a);
+  const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (;;) {
-    if (tid == 0) s_part = atomicAdd(a.ticket, 1u);
-    __syncthreads();
-    const uint32_t part = s_part;
-    if ((long long)part >= nparts) break;
-    const long long base = (long long)part * kSortPart + (long long)tid * 16;
-    unsigned long long c[16];
+  long long p0, p1;
+  block_parts(n, a.blocks, blockIdx.x, p0, p1);
+  if (tid == 0) s_carry = a.bsum[blockIdx.x];
+  for (long long part = p0; part < p1; ++part) {
+    const long long base = part * kSortPart + (long long)tid * 16;
+    uint32_t c[16];
     unsigned long long tsum = 0;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       long long idx = base + k;
-      c[k] = idx < (long long)n ? a.count[items[idx]] : 0ull;
+      c[k] = idx < (long long)n ? a.count[items[idx]] : 0u;
       tsum += c[k];
     }
     unsigned long long incl = tsum;
@@ -354,15 +579,7 @@ __global__ void __launch_bounds__(256) k_offsets(ScanArgs a) {
       if (w < warp) woff += s_w[w];
       total += s_w[w];
     }
-    if (warp == 0) {
-      unsigned long long ex = lookback_single_warp(a.slots, part, total, a.status);
-      if (lane == 0) {
-        s_base = ex;
-        if ((long long)part == nparts - 1) *a.n_pairs = ex + total;
-      }
-    }
-    __syncthreads();
-    unsigned long long run = s_base + woff + incl - tsum;
+    unsigned long long run = s_carry + woff + incl - tsum;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       long long idx = base + k;
@@ -370,6 +587,7 @@ __global__ void __launch_bounds__(256) k_offsets(ScanArgs a) {
       run += c[k];
     }
     __syncthreads();
+    if (tid == 0) s_carry += total;
   }
 }
 
@@ -392,7 +610,6 @@ struct EmitArgs {
   uint32_t *bigq;                    // queue of items with more than kBigItem tiles
   uint32_t *big_count, *big_ticket;
   uint32_t *hist;                    // pair sort histograms [passes][256]
-  unsigned long long *lb;            // pair sort look-back buffer 0
   int passes, digit_bits;
   uint32_t *status;
 };
@@ -402,8 +619,7 @@ struct EmitArgs {
 // kStage pairs they are assembled in shared memory (small items by their own
 // lane, large ones by the whole warp) and written back with coalesced
 // stores, the pair sort's digit histograms being taken during that flush.
-// Wider groups write directly.  The kernel also clears the pair sort's
-// first look-back buffer, so no separate pass reads the keys.
+// Wider groups write directly.
 constexpr uint32_t kSmallItem = 8;
 constexpr uint32_t kBigItem = 64;   // larger items go to k_emit_big
 constexpr int kStage = 768;
@@ -433,7 +649,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
   __syncthreads();
   unsigned long long nn = *a.n_items;
   const long long n = (long long)nn > a.item_capacity ? a.item_capacity : (long long)nn;
-  const uint32_t *items = a.sorted_items[*a.sel];
+  const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const uint32_t ltmask = (1u << lane) - 1u;
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
@@ -559,13 +775,6 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
     const uint32_t c = (&sh[0][0])[q];
     if (c) atomicAdd(&a.hist[q], c);
   }
-  // clear the pair sort's first look-back buffer for the partitions it uses
-  unsigned long long kk = *a.n_pairs;
-  const long long K = (long long)kk > a.pair_capacity ? a.pair_capacity : (long long)kk;
-  const long long nparts = (K + kSortPart - 1) / kSortPart;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nparts * 256;
-       q += (long long)gridDim.x * blockDim.x)
-    a.lb[q] = 0ull;
 }
 
 // Items with more than kBigItem tiles: the warps of the grid stride over the
@@ -576,7 +785,7 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
   for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0u;
   __syncthreads();
   const uint32_t nbig = *a.big_count;
-  const uint32_t *items = a.sorted_items[*a.sel];
+  const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
   const int lane = threadIdx.x & 31;
   const uint32_t ltmask = (1u << lane) - 1u;
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
@@ -624,6 +833,8 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
 }
 
 // ---- per-tile ranges ------------------------------------------------------
+constexpr int kRangeUnroll = 8;
+
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t *key_a, const uint32_t *key_b,
                                                 const uint32_t *sel,
                                                 const unsigned long long *n_pairs,
@@ -631,34 +842,42 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *key_a, const uin
   unsigned long long nn = *n_pairs;
   const long long n = (long long)nn > capacity ? capacity : (long long)nn;
   const uint32_t *key = *sel ? key_b : key_a;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const uint32_t t = key[p];
-    if (p == 0 || key[p - 1] != t) ranges[t].x = (uint32_t)p;
-    if (p == n - 1 || key[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+  const long long stride = (long long)gridDim.x * blockDim.x * kRangeUnroll;
+  for (long long base = (long long)blockIdx.x * blockDim.x * kRangeUnroll; base < n;
+       base += stride) {
+    uint32_t k[kRangeUnroll], kp[kRangeUnroll], kn[kRangeUnroll];
+#pragma unroll
+    for (int u = 0; u < kRangeUnroll; ++u) {
+      const long long p = base + u * blockDim.x + threadIdx.x;
+      k[u] = p < n ? key[p] : 0u;
+      kp[u] = (p > 0 && p < n) ? key[p - 1] : ~0u;
+      kn[u] = p + 1 < n ? key[p + 1] : ~0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kRangeUnroll; ++u) {
+      const long long p = base + u * blockDim.x + threadIdx.x;
+      if (p >= n) continue;
+      if (p == 0 || kp[u] != k[u]) ranges[k[u]].x = (uint32_t)p;
+      if (p == n - 1 || kn[u] != k[u]) ranges[k[u]].y = (uint32_t)(p + 1);
+    }
   }
 }
 
 cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   Hdr *hdr = region<Hdr>(p, ws, R_HDR);
   cudaError_t e;
-  // histograms and tickets of this stage start from zero (ticket 0 belongs
-  // to the projection)
+  init_grids();
+  // histograms of this stage start from zero
   e = cudaMemsetAsync(&hdr->hist[0][0][0], 0, sizeof(hdr->hist), s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(&hdr->ticket[1], 0, sizeof(hdr->ticket) - sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  const long long off_parts = (p->max_visible + kSortPart - 1) / kSortPart;
-  e = cudaMemsetAsync(region<unsigned long long>(p, ws, R_SCAN), 0,
-                      sizeof(unsigned long long) * (size_t)off_parts, s);
   if (e != cudaSuccess) return e;
   if (p->n == 0) {
     // nothing visible: empty ranges
     e = cudaMemsetAsync(region<uint2>(p, ws, R_RANGES), 0, p->bytes[R_RANGES], s);
     return e;
   }
-  const long long max_parts =
-      ((p->max_visible > p->max_pairs ? p->max_visible : p->max_pairs) + kSortPart - 1) / kSortPart;
+  // grid of the reduce-then-scan kernels, at most the rows the plan holds
+  const int G = g_sort_blocks < p->sort_blocks ? g_sort_blocks : p->sort_blocks;
+  uint32_t *bsum = region<uint32_t>(p, ws, R_BSUM);
   // 1. depth sort of the visible items
   SortArgs d = {};
   d.first_keys = region<uint32_t>(p, ws, R_REC_DEPTH);
@@ -672,9 +891,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   d.sel = &hdr->sel_depth;
   d.hist = &hdr->hist[0][0][0];
   d.skip = &hdr->skip[0];
-  d.tickets = &hdr->ticket[1];
-  d.lb = region<unsigned long long>(p, ws, R_LOOKBACK);
-  d.max_parts = max_parts;
+  d.bsum = bsum;
+  d.blocks = G;
   d.passes = 4;
   d.digit_bits = 8;
   d.status = &hdr->status;
@@ -689,11 +907,12 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.n_items = &hdr->n_visible;
   sa.capacity = p->max_visible;
   sa.offsets = region<uint32_t>(p, ws, R_OFFSETS);
-  sa.slots = region<unsigned long long>(p, ws, R_SCAN);
-  sa.ticket = &hdr->ticket[9];
+  sa.bsum = reinterpret_cast<unsigned long long *>(bsum + (size_t)p->sort_blocks * kSortSub * 256);
+  sa.blocks = G;
   sa.n_pairs = &hdr->n_pairs;
-  sa.status = &hdr->status;
-  k_offsets<<<g_stream_blocks, 256, 0, s>>>(sa);
+  k_offsets_up<<<G, 256, 0, s>>>(sa);
+  k_offsets_scan<<<1, 1024, 0, s>>>(sa);
+  k_offsets_down<<<G, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
   // digit width: the requested one, else the balanced width of the fewest
   // passes of at most 8 bits
@@ -719,7 +938,6 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.pkey = region<uint32_t>(p, ws, R_PKEY_A);
   ea.pval = region<uint32_t>(p, ws, R_PVAL_A);
   ea.hist = &hdr->hist[1][0][0];
-  ea.lb = d.lb;
   ea.passes = pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
@@ -743,9 +961,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.sel = &hdr->sel_pair;
   t.hist = &hdr->hist[1][0][0];
   t.skip = &hdr->skip[4];
-  t.tickets = &hdr->ticket[5];
-  t.lb = d.lb;
-  t.max_parts = max_parts;
+  t.bsum = bsum;
+  t.blocks = G;
   t.passes = pair_passes;
   t.digit_bits = pair_bits;
   t.status = &hdr->status;
@@ -774,21 +991,20 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
 namespace {
 
 constexpr long long kStaticMax = GS_STATIC_SORT_MAX_PAIRS;
-constexpr long long kStaticParts = (kStaticMax + kSortPart - 1) / kSortPart;
+constexpr int kStaticBlocks = 1024;   // rows of the block-count table
 
 struct StaticHdr {
   unsigned long long count;
   uint32_t hist[4][256];
   uint32_t skip[4];
-  uint32_t tickets[4];
   uint32_t sel;
   uint32_t status;
 };
 
 constexpr size_t kStaticHdrBytes = (sizeof(StaticHdr) + 255) & ~size_t(255);
 constexpr size_t kStaticTmpBytes = 2 * sizeof(uint32_t) * (size_t)kStaticMax;   // keys + values
-constexpr size_t kStaticLbBytes = 2 * 256 * sizeof(unsigned long long) * (size_t)kStaticParts;
-constexpr size_t kStaticBytes = kStaticHdrBytes + kStaticTmpBytes + kStaticLbBytes;
+constexpr size_t kStaticBsumBytes = 256 * sizeof(uint32_t) * kSortSub * (size_t)kStaticBlocks;
+constexpr size_t kStaticBytes = kStaticHdrBytes + kStaticTmpBytes + kStaticBsumBytes;
 
 // The scratch itself.  Host code must not take this symbol's address
 // directly (that would be a host-side stand-in); it asks the runtime for the
@@ -841,7 +1057,8 @@ extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_
   StaticHdr *h = reinterpret_cast<StaticHdr *>(base);
   uint32_t *tmp_k = reinterpret_cast<uint32_t *>(base + kStaticHdrBytes);
   uint32_t *tmp_v = tmp_k + kStaticMax;
-  unsigned long long *lb = reinterpret_cast<unsigned long long *>(base + kStaticHdrBytes + kStaticTmpBytes);
+  uint32_t *bsum = reinterpret_cast<uint32_t *>(base + kStaticHdrBytes + kStaticTmpBytes);
+  init_grids();
   // the array keeps the previous call's contents: clear what must start at 0
   if (cudaMemsetAsync(h, 0, sizeof(StaticHdr), stream) != cudaSuccess) return GS_ERR_CUDA;
   k_static_set_count<<<1, 1, 0, stream>>>(h, (unsigned long long)n);
@@ -862,9 +1079,8 @@ extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_
   a.sel = &h->sel;
   a.hist = &h->hist[0][0];
   a.skip = &h->skip[0];
-  a.tickets = &h->tickets[0];
-  a.lb = lb;
-  a.max_parts = kStaticParts;
+  a.bsum = bsum;
+  a.blocks = g_sort_blocks < kStaticBlocks ? g_sort_blocks : kStaticBlocks;
   a.no_skip = 1;
   a.status = &h->status;
   return run_sort(a, stream) == cudaSuccess ? GS_OK : GS_ERR_CUDA;

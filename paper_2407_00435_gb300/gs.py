@@ -308,9 +308,10 @@ class Renderer:
         want = self.cfg.radix_bits or 8
         passes = min(4, (tile_bits + want - 1) // want)
         project = 1 + (1 if fov else 0) + (1 if self.n > 0 else 0)
-        # depth sort (hist, scan, 4 passes), offsets, emit + large-item emit,
-        # pair sort (scan + passes), ranges
-        sort = 0 if self.n == 0 else 6 + 1 + 2 + (1 + passes) + 1
+        # depth sort (hist, scan, 4 passes of upsweep + scan + downsweep),
+        # offsets (upsweep, scan, downsweep), emit + large-item emit, pair
+        # sort (scan + 3 kernels per pass), ranges
+        sort = 0 if self.n == 0 else (2 + 4 * 3) + 3 + 2 + (1 + 3 * passes) + 1
         render = 1 + (1 if stats and self.n > 0 else 0)
         if self.cfg.chunk > 0 and not stats and self.T_tiles > 0:
             render += 1     # work list of the chunked render
