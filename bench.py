@@ -203,7 +203,7 @@ def gpu_arm(args):
     # ---- headline: plain forward, 1080p, 1M points, SH3 ---------------------
     wl = synth.workload(1)
     sc = gs.scene_to_device(wl.scene)
-    r = gs.Renderer(wl.scene.n, wl.scene.sh_degree, wl.cams)
+    r = gs.Renderer(wl.scene.n, wl.scene.sh_degree, wl.cams, tight=True)
     c = r.fit(sc)
     out = r.alloc_outputs(stats=True)
     r.render(out)                                   # untimed: exact counts
@@ -293,7 +293,23 @@ def gpu_arm(args):
     P_head = r.P
     extras = {}
     if not args.no_extras:
-        del r, sc, dev, host, out
+        del r, dev, host, out
+        torch.cuda.empty_cache()
+        # the same frame with the plain 3-sigma rectangle support, for reference
+        rr = gs.Renderer(wl.scene.n, wl.scene.sh_degree, wl.cams)
+        cr = rr.fit(sc)
+        outr = rr.alloc_outputs()
+
+        def rect_frame():
+            rr.project(sc)
+            rr.bin_sort()
+            rr.render(outr)
+
+        ms_rect = _ms(torch, rect_frame, max(3, min(args.steps, 10)), 2, flush)
+        extras["rect_support"] = {"fps": round(1000.0 / ms_rect, 2),
+                                  "pairs_K": int(cr["n_pairs"]),
+                                  "tight_speedup": round(ms_rect / ms, 3)}
+        del rr, outr, sc
         torch.cuda.empty_cache()
         steps_x = max(3, min(args.steps, 10))
         for name, fn in (("foveated_stereo", extra_foveated), ("fwd_bwd", extra_fwd_bwd),
@@ -311,6 +327,8 @@ def gpu_arm(args):
         "data": "synthetic (seeded blob-mixture scene; the paper's datasets are not available)",
         "config": {"workload": wl.name, "points": wl.scene.n, "sh_degree": 3,
                    "resolution": "1920x1080", "tile": 16, "views_per_step": 1,
+                   "support": "tight: tiles of the 3-sigma rectangle that the alpha >= 1/255 "
+                              "ellipse reaches (same image)",
                    "pairs_K": int(c["n_pairs"]), "visible": int(c["n_visible"]),
                    "l2": "flushed between steps (256 MB write) and scene 236 MB > L2",
                    "parallelism": f"replicas x{world}"},
@@ -341,13 +359,13 @@ def extra_foveated(torch, gs, synth, flush, steps):
     wl = synth.workload(2)
     sc = gs.scene_to_device(wl.scene)
     f = gs.fov_to_device(wl.fov)
-    rf = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True)
+    rf = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True, tight=True)
     cf = rf.fit(sc, f)
     of = rf.alloc_outputs(fov=True, stats=True)
     rf.render(of, fov=True)
     _, cntf = rf.counters()
     of = rf.alloc_outputs(fov=True)
-    rp = gs.Renderer(wl.scene.n, 3, wl.cams)
+    rp = gs.Renderer(wl.scene.n, 3, wl.cams, tight=True)
     cp = rp.fit(sc)
     op = rp.alloc_outputs()
 
@@ -384,9 +402,10 @@ def extra_fwd_bwd(torch, gs, synth, flush, steps):
     V = len(wl.cams)
     rng = np.random.default_rng(1003)
     target = torch.from_numpy(rng.uniform(0, 1, (V * 1024 * 1024, 3)).astype(np.float32)).cuda()
-    rb = gs.Renderer(wl.scene.n, 3, wl.cams, backward=True)
+    rb = gs.Renderer(wl.scene.n, 3, wl.cams, backward=True, tight=True)
     rb.fit(sc)
-    per = [gs.Renderer(wl.scene.n, 3, wl.cams[v:v + 1], backward=True) for v in range(V)]
+    per = [gs.Renderer(wl.scene.n, 3, wl.cams[v:v + 1], backward=True, tight=True)
+           for v in range(V)]
     for r in per:
         r.fit(sc)
     g = {k: torch.empty_like(v) for k, v in sc.items()}
@@ -437,11 +456,19 @@ def extra_fwd_bwd(torch, gs, synth, flush, steps):
 
 def extra_batched(torch, gs, synth, flush, steps):
     """6M points, 64 views of uneven sizes, half foveated: project + sort +
-    render of all views as one CUDA graph (one render launch for all tiles)."""
+    render of all views as one CUDA graph (one render launch for all tiles),
+    with the plan options picked by the autotuner."""
+    from paper_2407_00435_gb300.autotune import autotune
     wl = synth.workload(4)
     sc = gs.scene_to_device(wl.scene)
     f = gs.fov_to_device(wl.fov)
-    r = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True)
+    cands = [{"tile": 16, "radix_bits": 0, "chunk": 0}, {"tile": 16, "radix_bits": 7, "chunk": 0},
+             {"tile": 16, "radix_bits": 0, "chunk": 2048}, {"tile": 8, "radix_bits": 0, "chunk": 0}]
+    tune = autotune(sc, wl.scene.n, 3, wl.cams, f, candidates=cands, frames=2, warmup=1,
+                    tight=True)
+    opt = tune["options"]
+    r = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True, tight=True, tile=opt["tile"],
+                    radix_bits=opt["radix_bits"], chunk=opt["chunk"])
     c = r.fit(sc, f, headroom=1.05)
     out = r.alloc_outputs(fov=True)
 
@@ -468,7 +495,8 @@ def extra_batched(torch, gs, synth, flush, steps):
            "ms_per_batch": round(ms, 3), "views_per_s": round(len(wl.cams) * 1000 / ms, 2),
            "gpix_per_s": round(r.P / ms / 1e6, 3), "pairs": int(c["n_pairs"]),
            "visible": int(c["n_visible"]), "status": int(code),
-           "kernel_launches_in_graph": r.launches_per_frame(fov=True)}
+           "kernel_launches_in_graph": r.launches_per_frame(fov=True),
+           "autotuned": opt, "autotune_trials": tune["trials"]}
     del r, sc, graph
     torch.cuda.empty_cache()
     return res

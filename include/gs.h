@@ -127,6 +127,12 @@ typedef struct gs_config {
 
 #define GS_FLAG_FOVEATED 1u  /* reserve foveation state (levels, per-level params) */
 #define GS_FLAG_BACKWARD 2u  /* reserve per-item gradient scratch for gs_render_backward */
+#define GS_FLAG_TIGHT 4u     /* opacity-aware tight support: of each point's 3-sigma tile
+                                rectangle keep only the tiles whose pixel-centre rectangle
+                                meets the ellipse where alpha can reach 1/255 (an upper
+                                bound of 2 ln(255 o) on the Mahalanobis distance, o the
+                                largest opacity of any level).  Same image, shorter tile
+                                lists.  Rectangles of more than 256 tiles keep all tiles. */
 
 /* Counters read back by gs_get_error. */
 typedef struct gs_counters {

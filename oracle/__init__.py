@@ -22,6 +22,7 @@ _SRC = os.path.join(_HERE, "gs_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 ORC_NVAL = 15
+ORC_SUPP = 6            # tight-support record: keyed u, v, covariance a b c, tau
 (ORC_U, ORC_V, ORC_CA, ORC_CB, ORC_CC, ORC_R, ORC_G, ORC_B, ORC_RR, ORC_RG,
  ORC_RB, ORC_DEPTH, ORC_SA, ORC_SB, ORC_SC) = range(15)
 
@@ -63,13 +64,15 @@ def lib():
         build()
         L = C.CDLL(_LIB)
         p = C.c_void_p
-        L.orc_keyed_project.argtypes = [C.c_int, p, p, p, p, p, C.c_int, C.c_int, p, C.c_int, p, p, p]
+        L.orc_keyed_project.argtypes = [C.c_int, p, p, p, p, p, C.c_int, C.c_int, p, C.c_int, p, p,
+                                        p, p, p]
         L.orc_tile_levels.argtypes = [C.c_int, p, C.c_int, p, p]
         L.orc_total_tiles.argtypes = [C.c_int, p, C.c_int]
         L.orc_total_tiles.restype = C.c_int64
-        L.orc_count_pairs.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p]
+        L.orc_count_pairs.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p]
         L.orc_count_pairs.restype = C.c_int64
-        L.orc_bin.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, C.c_int64, p, p, p]
+        L.orc_bin.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p, C.c_int64, p, p,
+                              p]
         L.orc_project_values.argtypes = [C.c_int, p, p, p, p, C.c_int, C.c_int, p, p, p]
         L.orc_sh_basis.argtypes = [p, p]
         L.orc_sh_basis.restype = None
@@ -158,17 +161,23 @@ def _c64(a):
     return np.ascontiguousarray(a, np.float64)
 
 
-def keyed_project(scene, cams, tile):
+def keyed_project(scene, cams, tile, tight=False, fov: "FovArrays | None" = None):
+    """Keyed FP32 projection.  Returns (vis, depth bits, rect) and, with
+    ``tight``, also the (V*N, 6) tight-support records."""
     n, V = scene.n, len(cams)
     vis = np.zeros(V * n, np.uint8)
     dbits = np.zeros(V * n, np.uint32)
     rect = np.zeros((V * n, 4), np.int32)
+    supp = np.zeros((V * n, ORC_SUPP), np.float32) if tight else None
     cs = cams_struct(cams)
+    fs = fov.struct() if fov is not None else None
     arrs = [_c32(scene.means), _c32(scene.scales), _c32(scene.quats), _c32(scene.opac),
             _c32(scene.sh)]
     lib().orc_keyed_project(n, *[a.ctypes.data for a in arrs], scene.sh_degree, V,
-                            C.addressof(cs), tile, vis.ctypes.data, dbits.ctypes.data,
-                            rect.ctypes.data)
+                            C.addressof(cs), tile, C.addressof(fs) if fs is not None else None,
+                            vis.ctypes.data, dbits.ctypes.data, rect.ctypes.data, _ptr(supp))
+    if tight:
+        return vis, dbits, rect, supp
     return vis, dbits, rect
 
 
@@ -192,32 +201,36 @@ class Bins:
     keys: np.ndarray
     vals: np.ndarray
     ranges: np.ndarray  # (T, 2)
+    supp: np.ndarray | None = None   # (V*N, 6) tight-support records, if used
 
     @property
     def K(self):
         return int(len(self.keys))
 
 
-def bin_pairs(scene, cams, tile, fov: FovArrays | None = None) -> Bins:
-    """Keyed projection, FR filter, pair emission, stable sort, ranges."""
-    vis, dbits, rect = keyed_project(scene, cams, tile)
+def bin_pairs(scene, cams, tile, fov: FovArrays | None = None, tight=False) -> Bins:
+    """Keyed projection, FR filter, optional tight support, pair emission,
+    stable sort, ranges."""
+    kp = keyed_project(scene, cams, tile, tight=tight, fov=fov)
+    vis, dbits, rect = kp[:3]
+    supp = kp[3] if tight else None
     n, V = scene.n, len(cams)
     cs = cams_struct(cams)
     tl = tile_levels(cams, tile, fov) if fov is not None else None
     bm = fov.bound_m if fov is not None else None
     counts = np.zeros(V * n, np.uint32)
     K = lib().orc_count_pairs(n, V, C.addressof(cs), tile, vis.ctypes.data, rect.ctypes.data,
-                              _ptr(tl), _ptr(bm), counts.ctypes.data)
+                              _ptr(tl), _ptr(bm), _ptr(supp), counts.ctypes.data)
     T = lib().orc_total_tiles(V, C.addressof(cs), tile)
     keys = np.zeros(K, np.uint64)
     vals = np.zeros(K, np.uint32)
     ranges = np.zeros((T, 2), np.uint32)
     rc = lib().orc_bin(n, V, C.addressof(cs), tile, vis.ctypes.data, dbits.ctypes.data,
-                       rect.ctypes.data, _ptr(tl), _ptr(bm), K, keys.ctypes.data,
+                       rect.ctypes.data, _ptr(tl), _ptr(bm), _ptr(supp), K, keys.ctypes.data,
                        vals.ctypes.data, ranges.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"orc_bin failed: {rc}")
-    return Bins(vis, dbits, rect, tl, counts, keys, vals, ranges)
+    return Bins(vis, dbits, rect, tl, counts, keys, vals, ranges, supp)
 
 
 def project_values(scene, cams, vis, means=None, scales=None, quats=None, sh=None):

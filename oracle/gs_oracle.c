@@ -68,9 +68,95 @@ static uint32_t f32_bits(float f) {
   return u;
 }
 
+/* ------------------------------------------------------------------------ */
+/* opacity-aware tight support (optional)                                   */
+/*                                                                          */
+/* A pixel p can blend point i only inside the ellipse E: q(p) <= 2 ln(255 o)*/
+/* with q(p) = (p - mu)^T Sigma'^-1 (p - mu).  With the option on, E is     */
+/* enlarged to q <= tau, tau an upper bound of 2 ln(255 o_max) (o_max: the  */
+/* largest opacity any level uses):                                         */
+/*   255 o = m 2^e, m in [1, 2):  ln(255 o) = e ln 2 + ln m                 */
+/*                                           <= e ln2_up + (m - 1)          */
+/* (ln m <= m - 1; ln2_up = the nearest float to ln 2, which lies above it),*/
+/* then a relative and an absolute slack of 2^-10.  A tile of the 3-sigma   */
+/* rectangle is kept only if the rectangle spanned by its pixel centres,    */
+/* [xB+0.5, xB+B-0.5] x [yB+0.5, yB+B-0.5], meets E.  Per tile row this is  */
+/* one interval of columns: the strip cuts E in a convex set whose x-shadow */
+/* [xl, xr] ends at E's leftmost / rightmost point if that point lies in    */
+/* the strip, else where the nearer strip edge dy crosses E,                */
+/*   dx = (b dy +- sqrt(det (c tau - dy^2))) / c,                            */
+/* with Sigma' = [[a, b], [b, c]], det = a c - b^2, E's x-extent sqrt(tau a)*/
+/* reached at dy = b sqrt(tau a) / a, y-extent sqrt(tau c) (the divisions   */
+/* taken as products with the rounded reciprocals 1/a, 1/c).  The image is  */
+/* unchanged (a dropped tile holds no pixel that could blend the point);    */
+/* the tile lists get shorter.  FP32, fixed order, no contraction.          */
+/* ------------------------------------------------------------------------ */
+#define ORC_SUPP 6   /* u, v, a, b, c, tau */
+
+static float tight_tau(float o) {
+  float x = 255.0f * o;
+  if (!(x > 1.0f)) return -1.0f;      /* alpha < 1/255 at every pixel */
+  int e;
+  float m = frexpf(x, &e);            /* x = m 2^e, m in [0.5, 1), exact */
+  m = m * 2.0f;
+  e = e - 1;
+  float t = (float)e * 0.693147182f;
+  t = t + (m - 1.0f);
+  t = t * 2.0f;
+  float sl = t * 0.0009765625f;
+  t = t + sl;
+  t = t + 0.0009765625f;
+  return t;
+}
+
+static float strip_end(float b, float ic, float det, float ct, float yb, float sgn) {
+  float arg = det * (ct - yb * yb);
+  arg = fmaxf(arg, 0.0f);
+  float r = b * yb + sgn * sqrtf(arg);
+  return r * ic;
+}
+
+/* Columns [*xa, *xb] of tile row `by` whose pixel centres can meet the
+ * support sp (u, v, a, b, c, tau); 0 if none. */
+static int row_interval(const float *sp, int by, int tile, int *xa, int *xb) {
+  const float u = sp[0], v = sp[1], a = sp[2], b = sp[3], c = sp[4], tau = sp[5];
+  if (!(tau >= 0.0f)) return 0;
+  float det = a * c - b * b;
+  float dy0 = ((float)(by * tile) + 0.5f) - v;
+  float dy1 = ((float)(by * tile + tile - 1) + 0.5f) - v;
+  float ye = sqrtf(tau * c);
+  if (dy1 < -ye || dy0 > ye) return 0;
+  float xe = sqrtf(tau * a);
+  float ia = 1.0f / a, ic = 1.0f / c;
+  float dys = (b * xe) * ia;
+  float ct = c * tau;
+  float xr, xl;
+  if (dys >= dy0 && dys <= dy1) xr = xe;
+  else xr = strip_end(b, ic, det, ct, dys > dy1 ? dy1 : dy0, 1.0f);
+  float ndys = -dys;
+  if (ndys >= dy0 && ndys <= dy1) xl = -xe;
+  else xl = strip_end(b, ic, det, ct, ndys > dy1 ? dy1 : dy0, -1.0f);
+  float L = u + xl, R = u + xr;
+  float invB = 1.0f / (float)tile;
+  float fa = ceilf(((L + 0.5f) - (float)tile) * invB);
+  float fb = floorf((R - 0.5f) * invB);
+  fa = fminf(fmaxf(fa, -1.0f), 65536.0f);
+  fb = fminf(fmaxf(fb, -1.0f), 65536.0f);
+  *xa = (int)fa;
+  *xb = (int)fb;
+  return *xa <= *xb;
+}
+
+/* 1 if tile (x, y) is in the support (the tile's row interval holds x). */
+static int tile_in_support(const float *sp, int x, int y, int tile) {
+  int xa, xb;
+  if (!row_interval(sp, y, tile, &xa, &xb)) return 0;
+  return x >= xa && x <= xb;
+}
+
 static int keyed_one(const float *mu, const float *s, const float *q,
                      const orc_cam *c, int tile, int tiles_x, int tiles_y,
-                     uint32_t *dbits, int32_t rect[4]) {
+                     uint32_t *dbits, int32_t rect[4], float o_max, float *supp) {
   const float *R = c->R;
   /* camera-space mean: ((R0 x + R1 y) + R2 z) + t */
   float px = R[0] * mu[0];
@@ -186,13 +272,22 @@ static int keyed_one(const float *mu, const float *s, const float *q,
   rect[2] = (int32_t)y0;
   rect[3] = (int32_t)y1;
   *dbits = f32_bits(pz);
+  if (supp) {
+    supp[0] = u;
+    supp[1] = v;
+    supp[2] = a;
+    supp[3] = b;
+    supp[4] = cc;
+    supp[5] = tight_tau(o_max);
+  }
   return 1;
 }
 
 int orc_keyed_project(int n, const float *means, const float *scales,
                       const float *quats, const float *opac, const float *sh,
                       int sh_degree, int V, const orc_cam *cams, int tile,
-                      uint8_t *vis, uint32_t *depth_bits, int32_t *rect) {
+                      const orc_fov *fov, uint8_t *vis, uint32_t *depth_bits,
+                      int32_t *rect, float *supp) {
   int S = (sh_degree + 1) * (sh_degree + 1);
   for (int v = 0; v < V; ++v) {
     int tx, ty;
@@ -208,9 +303,15 @@ int orc_keyed_project(int n, const float *means, const float *scales,
       depth_bits[it] = 0;
       rect[4 * it] = 0; rect[4 * it + 1] = -1; rect[4 * it + 2] = 0; rect[4 * it + 3] = -1;
       if (!fin) { vis[it] = 2; continue; }
+      /* largest opacity any level composites the point with */
+      float o_max = opac[i];
+      if (fov && fov->opacity_lv)
+        for (int l = 0; l < fov->n_levels - 1; ++l)
+          o_max = fmaxf(o_max, (float)fov->opacity_lv[(int64_t)l * n + i]);
       vis[it] = (uint8_t)keyed_one(&means[3 * i], &scales[3 * i], &quats[4 * i],
                                    &cams[v], tile, tx, ty, &depth_bits[it],
-                                   &rect[4 * it]);
+                                   &rect[4 * it], o_max,
+                                   supp ? &supp[ORC_SUPP * it] : NULL);
     }
   }
   return 0;
@@ -301,7 +402,7 @@ static int kept(const uint8_t *tile_level, const uint8_t *bound_m, int64_t gt,
 int64_t orc_count_pairs(int n, int V, const orc_cam *cams, int tile,
                         const uint8_t *vis, const int32_t *rect,
                         const uint8_t *tile_level, const uint8_t *bound_m,
-                        uint32_t *counts) {
+                        const float *supp, uint32_t *counts) {
   int64_t K = 0;
   for (int v = 0; v < V; ++v) {
     int tx, ty;
@@ -314,7 +415,8 @@ int64_t orc_count_pairs(int n, int V, const orc_cam *cams, int tile,
         const int32_t *rc = &rect[4 * it];
         for (int y = rc[2]; y <= rc[3]; ++y)
           for (int x = rc[0]; x <= rc[1]; ++x)
-            cnt += (uint32_t)kept(tile_level, bound_m, tb + (int64_t)y * tx + x, i);
+            cnt += (uint32_t)(kept(tile_level, bound_m, tb + (int64_t)y * tx + x, i) &&
+                              (!supp || tile_in_support(&supp[ORC_SUPP * it], x, y, tile)));
       }
       if (counts) counts[it] = cnt;
       K += cnt;
@@ -338,8 +440,8 @@ static int cmp_pair(const void *pa, const void *pb) {
 
 int orc_bin(int n, int V, const orc_cam *cams, int tile, const uint8_t *vis,
             const uint32_t *depth_bits, const int32_t *rect,
-            const uint8_t *tile_level, const uint8_t *bound_m, int64_t K,
-            uint64_t *keys, uint32_t *vals, uint32_t *ranges) {
+            const uint8_t *tile_level, const uint8_t *bound_m, const float *supp,
+            int64_t K, uint64_t *keys, uint32_t *vals, uint32_t *ranges) {
   pair_t *p = (pair_t *)malloc(sizeof(pair_t) * (size_t)(K > 0 ? K : 1));
   if (!p) return -1;
   int64_t k = 0;
@@ -355,6 +457,7 @@ int orc_bin(int n, int V, const orc_cam *cams, int tile, const uint8_t *vis,
         for (int x = rc[0]; x <= rc[1]; ++x) {
           int64_t gt = tb + (int64_t)y * tx + x;
           if (!kept(tile_level, bound_m, gt, i)) continue;
+          if (supp && !tile_in_support(&supp[ORC_SUPP * it], x, y, tile)) continue;
           if (k >= K) { free(p); return -2; }
           p[k].key = ((uint64_t)gt << 32) | depth_bits[it];
           p[k].val = (uint32_t)it;

@@ -72,11 +72,15 @@ enum {
 /* Keyed projection (FP32, fixed order).  For each view v and point i writes
  * vis[v*N+i] (1 visible, 0 culled, 2 culled because a parameter is not
  * finite), depth_bits (raw bits of the camera z), rect = {x0, x1, y0, y1}
- * inclusive tile bounds (only meaningful when visible).  Returns 0. */
+ * inclusive tile bounds (only meaningful when visible).  supp (nullable,
+ * 6 floats per item: keyed 2D mean, 2D covariance a b c, tau) receives
+ * the opacity-aware tight support of each visible item; fov (nullable) only
+ * supplies the per-level opacities that support must cover.  Returns 0. */
 int orc_keyed_project(int n, const float *means, const float *scales,
                       const float *quats, const float *opac, const float *sh,
                       int sh_degree, int V, const orc_cam *cams, int tile,
-                      uint8_t *vis, uint32_t *depth_bits, int32_t *rect);
+                      const orc_fov *fov, uint8_t *vis, uint32_t *depth_bits,
+                      int32_t *rect, float *supp);
 
 /* Per-tile filter level (FP32 keyed): minimum over the tile's pixels of
  * the lowest level that pixel needs.  Tiles of plain views get 1.
@@ -87,19 +91,21 @@ int orc_tile_levels(int V, const orc_cam *cams, int tile, const orc_fov *fov,
 /* Total tiles of all views. */
 int64_t orc_total_tiles(int V, const orc_cam *cams, int tile);
 
-/* Pair count K.  counts[v*N+i] receives the number of kept tile pairs. */
+/* Pair count K.  counts[v*N+i] receives the number of kept tile pairs: the
+ * tiles of the rectangle that pass the foveation filter and, when supp is
+ * given, meet the tight support. */
 int64_t orc_count_pairs(int n, int V, const orc_cam *cams, int tile,
                         const uint8_t *vis, const int32_t *rect,
                         const uint8_t *tile_level, const uint8_t *bound_m,
-                        uint32_t *counts);
+                        const float *supp, uint32_t *counts);
 
 /* Emit the K pairs in (view, point, tile-row, tile-col) order with key
  * (global tile << 32 | depth bits) and value v*N+i, stable-sort them by key
  * and write per-tile [start, end) ranges (2 uint32 per tile). */
 int orc_bin(int n, int V, const orc_cam *cams, int tile, const uint8_t *vis,
             const uint32_t *depth_bits, const int32_t *rect,
-            const uint8_t *tile_level, const uint8_t *bound_m, int64_t K,
-            uint64_t *keys, uint32_t *vals, uint32_t *ranges);
+            const uint8_t *tile_level, const uint8_t *bound_m, const float *supp,
+            int64_t K, uint64_t *keys, uint32_t *vals, uint32_t *ranges);
 
 /* FP64 value projection of every visible item into out[(v*N+i)*ORC_NVAL]. */
 int orc_project_values(int n, const double *means, const double *scales,

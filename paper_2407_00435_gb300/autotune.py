@@ -31,9 +31,9 @@ DEFAULT_CANDIDATES = [
 ]
 
 
-def workload_key(n, sh_degree, cams, fov) -> str:
+def workload_key(n, sh_degree, cams, fov, tight=False) -> str:
     sizes = ",".join(f"{int(c[16])}x{int(c[17])}" for c in cams)
-    return f"n={n};deg={sh_degree};fov={int(fov is not None)};views={sizes}"
+    return f"n={n};deg={sh_degree};fov={int(fov is not None)};tight={int(tight)};views={sizes}"
 
 
 def _time_frames(r: Renderer, sc, fov, frames, warmup):
@@ -59,9 +59,9 @@ def _time_frames(r: Renderer, sc, fov, frames, warmup):
 
 def autotune(sc: dict, n: int, sh_degree: int, cams, fov: dict | None = None,
              candidates=None, frames: int = 3, warmup: int = 1, cache_path: str | None = None,
-             headroom: float = 1.05, verbose: bool = False) -> dict:
+             headroom: float = 1.05, tight: bool = False, verbose: bool = False) -> dict:
     """Return {"options": best option dict, "ms": its frame time, "trials": [...]}."""
-    key = workload_key(n, sh_degree, cams, fov)
+    key = workload_key(n, sh_degree, cams, fov, tight)
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
@@ -72,7 +72,7 @@ def autotune(sc: dict, n: int, sh_degree: int, cams, fov: dict | None = None,
         t0 = time.perf_counter()
         try:
             r = Renderer(n, sh_degree, cams, tile=opt["tile"], foveated=fov is not None,
-                         radix_bits=opt["radix_bits"], chunk=opt["chunk"])
+                         radix_bits=opt["radix_bits"], chunk=opt["chunk"], tight=tight)
             r.fit(sc, fov, headroom=headroom)
             ms = _time_frames(r, sc, fov, frames, warmup)
             trials.append({**opt, "ms": round(ms, 4)})

@@ -51,20 +51,24 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   p->chunk = c.chunk > 0 ? c.chunk : 0;
   if (c.radix_bits != 0 && (c.radix_bits < 4 || c.radix_bits > 8)) return GS_ERR_INVALID_ARG;
   p->radix_bits = c.radix_bits;
+  if ((uint32_t)c.flags & ~(GS_FLAG_FOVEATED | GS_FLAG_BACKWARD | GS_FLAG_TIGHT))
+    return GS_ERR_INVALID_ARG;
   p->flags = (uint32_t)c.flags;
-  long long tiles = 0, pixels = 0;
+  long long tiles = 0, pixels = 0, rows = 0;
   for (int v = 0; v < V; ++v) {
     const gs_camera &cam = cams[v];
     if (cam.width <= 0 || cam.height <= 0) return GS_ERR_INVALID_ARG;
     long long tx = (cam.width + c.tile - 1) / c.tile, ty = (cam.height + c.tile - 1) / c.tile;
     if (tx > 65535 || ty > 65535) return GS_ERR_INVALID_ARG;
     tiles += tx * ty;
+    rows += ty;
     pixels += (long long)cam.width * cam.height;
     if (cam.width > p->max_w) p->max_w = cam.width;
     if (cam.height > p->max_h) p->max_h = cam.height;
   }
   if (tiles > 0xffffffffll) return GS_ERR_INVALID_ARG;
   p->tiles_total = tiles;
+  p->rows_total = rows;
   p->pixels_total = pixels;
   long long items = n * (long long)V;
   // records live at fixed slots i * V + v, so every (view, point) has one
@@ -90,11 +94,16 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   b[R_HDR] = sizeof(Hdr);
   b[R_VIEWS] = sizeof(ViewDev) * (size_t)V;
   b[R_TILE_LEVEL] = fov ? (size_t)T : 0;
+  b[R_LEVEL_ROWS] = fov ? 4 * (size_t)GS_MAX_LEVELS * (size_t)(rows > 0 ? rows : 1) : 0;
   b[R_REC_MEAN] = b[R_REC_SHAPE] = b[R_REC_COLOR] = 16 * (size_t)M;
   b[R_REC_REST] = fov ? 16 * (size_t)M : 0;
   b[R_REC_DEPTH] = b[R_REC_COUNT] = b[R_REC_GID] = b[R_REC_VIEW] = 4 * (size_t)M;
   b[R_REC_RECT] = 8 * (size_t)M;
   b[R_REC_M] = fov ? (size_t)M : 0;
+  const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
+  b[R_REC_SUPP] = tight ? 16 * (size_t)M : 0;
+  b[R_REC_SUPP2] = tight ? 8 * (size_t)M : 0;
+  b[R_REC_TABLE] = (tight || fov) ? 16 * (size_t)M : 0;
   b[R_DKEY_A] = b[R_DKEY_B] = b[R_DVAL_A] = b[R_DVAL_B] = 4 * (size_t)M;
   b[R_OFFSETS] = 4 * (size_t)M;
   b[R_PKEY_A] = b[R_PKEY_B] = b[R_PVAL_A] = b[R_PVAL_B] = 4 * (size_t)K;

@@ -34,6 +34,8 @@ enum Region : int {
   R_HDR = 0,
   R_VIEWS,
   R_TILE_LEVEL,
+  R_LEVEL_ROWS,  // u32 per (tile row, level m): columns whose tile level <= m
+                 //   (first | last << 16; first > last when none) [foveated]
   R_REC_MEAN,    // float4 (mx_hi, my_hi, mx_lo, my_lo)
   R_REC_SHAPE,   // float4 whitening rows (w1x, w1y, w2x, w2y)
   R_REC_COLOR,   // float4 (r, g, b, log2 opacity)
@@ -44,6 +46,9 @@ enum Region : int {
   R_REC_GID,     // u32 point index (item slot j = i * V + v)
   R_REC_VIEW,    // u32 view index
   R_REC_M,       // u8 quality bound (foveated)
+  R_REC_SUPP,    // float4 tight support (keyed u, v, covariance a, b) [tight]
+  R_REC_SUPP2,   // float2 tight support (covariance c, tau) [tight]
+  R_REC_TABLE,   // uint4 row intervals of rectangles of <= 8 rows [tight or foveated]
   R_DKEY_A, R_DKEY_B, R_DVAL_A, R_DVAL_B,   // depth sort ping-pong (M)
   R_OFFSETS,     // u32 exclusive pair offsets in depth order (M)
   R_PKEY_A, R_PKEY_B, R_PVAL_A, R_PVAL_B,   // pair sort ping-pong (K)
@@ -80,7 +85,7 @@ struct Hdr {
   uint32_t hist[2][4][256];       // digit histograms: [sort][pass][digit]
   unsigned long long queue;       // next work item of the chunked render
   uint32_t n_slots;               // chunk slots requested by the chunk plan
-  uint32_t pad1;
+  uint32_t count_big;             // items queued for the warp-wide pair count
 };
 
 // Per-view constants, computed on the device from the cameras.
@@ -92,7 +97,7 @@ struct ViewDev {
   int32_t fov;           // 1 = foveated
   float gx, gy;          // gaze pixel
   float R[GS_MAX_LEVELS - 1];   // ring radii (px), fy * ring_tan
-  float pad[1];
+  int32_t row_base;      // tile rows of the views before this one
 };
 
 // Lookback flags in the top two bits of a 64-bit slot.
@@ -118,7 +123,7 @@ struct gs_plan {
   int32_t sh_degree, V, tile, chunk;
   uint32_t flags;
   int32_t num_sms;
-  int64_t tiles_total, pixels_total;
+  int64_t tiles_total, pixels_total, rows_total;
   int64_t max_visible, max_pairs;
   int32_t tile_bits;
   int32_t radix_bits;     // requested digit width of the pair sort (0 = balanced)

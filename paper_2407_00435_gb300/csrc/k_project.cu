@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "gs_internal.cuh"
+#include "support.cuh"
 #include "tma.cuh"
 
 namespace gs {
@@ -30,7 +31,7 @@ __global__ void k_views(const gs_camera *cams, int V, int tile, FovArgs fa, int 
                         ViewDev *views, Hdr *hdr, long long tiles_total,
                         long long pixels_total, unsigned long long n_items) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  long long tb = 0, pb = 0;
+  long long tb = 0, pb = 0, rb = 0;
   for (int v = 0; v < V; ++v) {
     const gs_camera c = cams[v];
     ViewDev d;
@@ -51,8 +52,9 @@ __global__ void k_views(const gs_camera *cams, int V, int tile, FovArgs fa, int 
     d.gy = has_fov ? fa.gaze[2 * v + 1] : 0.0f;
     for (int k = 0; k < GS_MAX_LEVELS - 1; ++k)
       d.R[k] = (has_fov && k < fa.n_levels - 1) ? c.fy * fa.ring_tan[k] : 0.0f;
-    d.pad[0] = 0.0f;
+    d.row_base = (int32_t)rb;
     views[v] = d;
+    rb += d.ty;
     tb += (long long)d.tx * d.ty;
     pb += (long long)c.width * c.height;
   }
@@ -134,11 +136,49 @@ __global__ void k_tile_levels(const ViewDev *views, int V, int tile, int L, floa
   }
 }
 
+// Per tile row and level m, the columns whose tile level is <= m (one
+// interval, see level_row).
+__global__ void k_level_rows(const ViewDev *views, int V, const uint8_t *tile_level,
+                             long long rows_total, uint32_t *out) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < rows_total;
+       g += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (views[mid].row_base <= g) lo = mid; else hi = mid - 1;
+    }
+    const ViewDev &vd = views[lo];
+    const uint8_t *tl = tile_level + vd.tile_base + (g - vd.row_base) * vd.tx;
+    int first[GS_MAX_LEVELS], last[GS_MAX_LEVELS];
+#pragma unroll
+    for (int m = 0; m < GS_MAX_LEVELS; ++m) {
+      first[m] = 0xffff;
+      last[m] = 0;
+    }
+    for (int x = 0; x < vd.tx; ++x) {
+      const int lvl = tl[x];
+#pragma unroll
+      for (int m = 0; m < GS_MAX_LEVELS; ++m)
+        if (lvl <= m + 1) {
+          first[m] = min(first[m], x);
+          last[m] = max(last[m], x);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < GS_MAX_LEVELS; ++m)
+      out[g * GS_MAX_LEVELS + m] = (uint32_t)first[m] | ((uint32_t)last[m] << 16);
+  }
+}
+
 cudaError_t launch_tile_levels(const gs_plan *p, void *ws, cudaStream_t s) {
   if (!p->has_fov || p->tiles_total == 0) return cudaSuccess;
   k_tile_levels<<<(unsigned)p->tiles_total, 64, 0, s>>>(
       region<ViewDev>(p, ws, R_VIEWS), p->V, p->tile, p->fov.n_levels, p->fov.band_px,
       region<uint8_t>(p, ws, R_TILE_LEVEL), p->tiles_total);
+  const long long rb = (p->rows_total + 127) / 128;
+  k_level_rows<<<(unsigned)(rb < 4096 ? rb : 4096), 128, 0, s>>>(
+      region<ViewDev>(p, ws, R_VIEWS), p->V, region<uint8_t>(p, ws, R_TILE_LEVEL), p->rows_total,
+      region<uint32_t>(p, ws, R_LEVEL_ROWS));
   return cudaGetLastError();
 }
 
@@ -160,6 +200,15 @@ struct ProjArgs {
   uint32_t *rec_depth, *rec_count, *rec_gid, *rec_view;
   uint2 *rec_rect;
   uint8_t *rec_m;
+  // opacity-aware tight support (null records = 3-sigma rectangle only)
+  float4 *rec_supp;             // (u, v, a, b)
+  float2 *rec_supp2;            // (c, tau)
+  uint4 *rec_table;              // row intervals of small rectangles (tight or foveated)
+  const uint32_t *level_rows;    // columns kept by the foveation filter, per row and level
+  uint32_t *count_q;             // items left to k_count_big
+  unsigned int *count_q_len;
+  const float *opacity_lv;      // (L-1, N) level opacities the support must cover, or null
+  int n_opacity_lv;
 };
 
 struct Keyed {
@@ -168,6 +217,8 @@ struct Keyed {
   int x0, x1, y0, y1;    // inclusive tile rect
   float M[9];            // Rq diag(s)
   float j00, j02, j11, j12;
+  float u, v;            // keyed 2D mean
+  float a, b, cc;        // keyed 2D covariance (with low-pass)
 };
 
 // The keyed FP32 projection.  Every statement is one IEEE operation in a
@@ -283,6 +334,8 @@ __device__ __forceinline__ bool keyed_project(const float mu[3], const float s[3
   k.tx = tx; k.ty = ty;
   k.x0 = (int)x0; k.x1 = (int)x1; k.y0 = (int)y0; k.y1 = (int)y1;
   k.j00 = j00; k.j02 = j02; k.j11 = j11; k.j12 = j12;
+  k.u = u; k.v = v;
+  k.a = a; k.b = b; k.cc = cc;
   return true;
 }
 
@@ -413,7 +466,7 @@ __device__ __forceinline__ void stage_rows(float *dst, int stride, const float *
 
 struct Rec {
   float4 mean, shape, color, rest;
-  uint32_t depth, count;
+  uint32_t depth;
   uint2 rect;
   uint8_t m;
 };
@@ -485,26 +538,124 @@ __device__ __forceinline__ void project_value(const ProjArgs &a, const ProjSmem<
     rest[ch] = acc;
     col[ch] = fmaxf(0.0f, fmaf(shc[ch], Y[0], acc) + kShOffset);
   }
-  // --- pairs kept by the foveation filter ---
-  uint32_t pairs;
-  uint8_t m = 0;
-  if (a.tile_level) {
-    m = a.bound_m[i];
-    pairs = 0;
-    const long long tb = vd.tile_base;
-    for (int y = k.y0; y <= k.y1; ++y)
-      for (int x = k.x0; x <= k.x1; ++x)
-        pairs += a.tile_level[tb + (long long)y * vd.tx + x] <= m ? 1u : 0u;
-  } else {
-    pairs = (uint32_t)((k.x1 - k.x0 + 1) * (k.y1 - k.y0 + 1));
-  }
   out.mean = make_float4(uh, vh, ul, vl);
   out.color = make_float4(col[0], col[1], col[2], log2f(sm.op[tid]));
   out.rest = make_float4(rest[0], rest[1], rest[2], 0.0f);
   out.depth = __float_as_uint(k.pz);
-  out.count = pairs;
   out.rect = make_uint2((uint32_t)k.x0 | ((uint32_t)k.x1 << 16), (uint32_t)k.y0 | ((uint32_t)k.y1 << 16));
-  out.m = m;
+  out.m = a.tile_level ? a.bound_m[i] : 0;
+}
+
+// Tile pairs of every visible item: the rectangle's tiles that pass the
+// foveation filter (tile level <= m: one interval per row, from the level
+// rows) and, with the tight support, lie in their row's interval.  Items
+// whose rectangle has at most kTableRows rows get their row intervals as a
+// table for the emit.  With the tight support, items with more rows are
+// queued for k_count_big (a warp each).  A kernel of its own after the
+// projection, which keeps the projection's register footprint small.
+__global__ void __launch_bounds__(256) k_count_pairs(ProjArgs a) {
+  const long long slots = a.n * a.V;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < slots;
+       j += (long long)gridDim.x * blockDim.x) {
+    if (a.rec_depth[j] == 0xffffffffu) continue;   // invisible: count already 0
+    const uint2 r = a.rec_rect[j];
+    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+    if (!a.rec_supp && !a.tile_level) {
+      a.rec_count[j] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+      continue;
+    }
+    const bool tabled = has_table(x0, x1, y0, y1);
+    if (a.rec_supp && !tabled) {
+      // many rows: counted by a whole warp in k_count_big
+      const unsigned int q = atomicAdd(a.count_q_len, 1u);
+      a.count_q[q] = (uint32_t)j;
+      continue;
+    }
+    const ViewDev &vd = a.views[j % a.V];
+    const int m = a.tile_level ? (int)a.rec_m[j] : 0;
+    SuppPre pre;
+    if (a.rec_supp) {
+      // tau covers the largest opacity any level composites the point with
+      const long long i = j / a.V;
+      float o_max = a.opac[i];
+      for (int l = 0; l < a.n_opacity_lv; ++l)
+        o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
+      const float2 s1 = make_float2(a.rec_supp2[j].x, tight_tau(o_max));
+      a.rec_supp2[j] = s1;
+      pre = supp_prep(a.rec_supp[j], s1);
+    }
+    uint32_t tb[4] = {0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu};   // rows empty
+    uint32_t pairs = 0;
+    for (int y = y0; y <= y1; ++y) {
+      int xa = x0, xb = x1;
+      if (a.rec_supp) {
+        int ia, ib;
+        if (!row_interval(pre, y, a.tile, ia, ib)) continue;
+        xa = max(xa, ia);
+        xb = min(xb, ib);
+      }
+      if (a.tile_level) {
+        int la, lb;
+        level_row(a.level_rows, vd.row_base + y, m, la, lb);
+        xa = max(xa, la);
+        xb = min(xb, lb);
+      }
+      if (xa > xb) continue;
+      pairs += (uint32_t)(xb - xa + 1);
+      if (tabled) {
+        const int rr = y - y0;
+        const uint32_t e = (uint32_t)(xa - x0) | ((uint32_t)(xb - x0) << 8);
+        const int sh = 16 * (rr & 1);
+        const uint32_t cur = rr < 2 ? tb[0] : rr < 4 ? tb[1] : rr < 6 ? tb[2] : tb[3];
+        const uint32_t nv = (cur & ~(0xffffu << sh)) | (e << sh);
+        if (rr < 2) tb[0] = nv; else if (rr < 4) tb[1] = nv; else if (rr < 6) tb[2] = nv; else tb[3] = nv;
+      }
+    }
+    a.rec_count[j] = pairs;
+    if (tabled) a.rec_table[j] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
+  }
+}
+
+// Pair counts of the items k_count_pairs queued (tight support, rectangles
+// of more than kTableRows rows or kTableCols columns): one warp per item,
+// lanes over the rows.
+__global__ void __launch_bounds__(256) k_count_big(ProjArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nq = *a.count_q_len;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  for (uint32_t qi = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); qi < nq; qi += warps) {
+    const long long j = a.count_q[qi];
+    const uint2 r = a.rec_rect[j];
+    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+    const ViewDev &vd = a.views[j % a.V];
+    const int m = a.tile_level ? (int)a.rec_m[j] : 0;
+    const long long i = j / a.V;
+    float o_max = a.opac[i];
+    for (int l = 0; l < a.n_opacity_lv; ++l)
+      o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
+    const float2 s1 = make_float2(a.rec_supp2[j].x, tight_tau(o_max));
+    const SuppPre pre = supp_prep(a.rec_supp[j], s1);
+    uint32_t pairs = 0;
+    for (int y = y0 + lane; y <= y1; y += 32) {
+      int xa, xb;
+      if (!row_interval(pre, y, a.tile, xa, xb)) continue;
+      xa = max(xa, x0);
+      xb = min(xb, x1);
+      if (a.tile_level) {
+        int la, lb;
+        level_row(a.level_rows, vd.row_base + y, m, la, lb);
+        xa = max(xa, la);
+        xb = min(xb, lb);
+      }
+      if (xa > xb) continue;
+      pairs += (uint32_t)(xb - xa + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    if (lane == 0) {
+      a.rec_supp2[j] = s1;
+      a.rec_count[j] = pairs;
+    }
+  }
 }
 
 __device__ __forceinline__ void write_rec(const ProjArgs &a, unsigned long long j, const Rec &r,
@@ -517,7 +668,6 @@ __device__ __forceinline__ void write_rec(const ProjArgs &a, unsigned long long 
     a.rec_m[j] = r.m;
   }
   a.rec_depth[j] = r.depth;
-  a.rec_count[j] = r.count;
   a.rec_rect[j] = r.rect;
   a.rec_gid[j] = gid;
   a.rec_view[j] = v;
@@ -529,7 +679,7 @@ __device__ __forceinline__ void write_rec(const ProjArgs &a, unsigned long long 
 // visible item) and zero pairs; the number of visible items is counted with
 // one atomic per block.
 template <int S>
-__global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
+__global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
   __shared__ ProjSmem<S> sm;
   __shared__ uint32_t s_vis, s_nonfinite;
   const int tid = threadIdx.x;
@@ -613,6 +763,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
       const ViewDev &vd = a.views[v];
       Keyed k;
       if (fin && keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) {
+        if (a.rec_supp) {
+          // keyed mean and covariance; k_count_pairs adds tau
+          a.rec_supp[j] = make_float4(k.u, k.v, k.a, k.b);
+          a.rec_supp2[j] = make_float2(k.cc, 0.0f);
+        }
         Rec r;
         project_value<S>(a, sm, tid, i, mu, cam, vd, k, r);
         write_rec(a, (unsigned long long)j, r, (uint32_t)i, (uint32_t)v);
@@ -661,6 +816,15 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
   a.rec_view = region<uint32_t>(p, ws, R_REC_VIEW);
   a.rec_rect = region<uint2>(p, ws, R_REC_RECT);
   a.rec_m = p->bytes[R_REC_M] ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
+  const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
+  a.rec_supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
+  a.rec_supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
+  a.rec_table = (tight || p->has_fov) ? region<uint4>(p, ws, R_REC_TABLE) : nullptr;
+  a.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
+  a.count_q = region<uint32_t>(p, ws, R_BIGQ);          // free until the emit
+  a.count_q_len = &a.hdr->count_big;
+  a.opacity_lv = p->has_fov ? p->fov.opacity_lv : nullptr;
+  a.n_opacity_lv = a.opacity_lv ? p->fov.n_levels - 1 : 0;
   unsigned grid = (unsigned)((p->n + kProjThreads - 1) / kProjThreads);
   switch (a.S) {
     case 1: k_project<1><<<grid, kProjThreads, 0, s>>>(a); break;
@@ -668,6 +832,10 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
     case 9: k_project<9><<<grid, kProjThreads, 0, s>>>(a); break;
     default: k_project<16><<<grid, kProjThreads, 0, s>>>(a); break;
   }
+  const long long slots = p->n * p->V;
+  const long long cb = (slots + 255) / 256;
+  k_count_pairs<<<(unsigned)(cb < 65535 ? cb : 65535), 256, 0, s>>>(a);
+  if (tight) k_count_big<<<p->num_sms > 0 ? 4 * p->num_sms : 608, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

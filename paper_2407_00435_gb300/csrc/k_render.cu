@@ -744,7 +744,7 @@ cudaError_t launch_render(const gs_plan *p, void *ws, bool fov, const float bg[3
     a.ch_cap = (unsigned long long)p->chunk_cap;
     a.n_slots = &hdr->n_slots;
     a.queue = &hdr->queue;
-    cudaError_t e = cudaMemsetAsync(&hdr->queue, 0, 2 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(&hdr->queue, 0, sizeof(unsigned long long) + sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const long long T = p->tiles_total;
     const unsigned blocks = (unsigned)((T + 255) / 256 < 4096 ? (T + 255) / 256 : 4096);

@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "gs_internal.cuh"
+#include "support.cuh"
 #include "tma.cuh"
 
 namespace gs {
@@ -610,20 +611,20 @@ struct EmitArgs {
   uint32_t *bigq;                    // queue of items with more than kBigItem tiles
   uint32_t *big_count, *big_ticket;
   uint32_t *hist;                    // pair sort histograms [passes][256]
+  const float4 *supp;                // tight support records, or null (whole rectangle)
+  const float2 *supp2;
+  const uint4 *table;                // row intervals of small rectangles (tight or foveated)
+  const uint32_t *level_rows;        // columns kept by the foveation filter, per row and level
+  int tile;
   int passes, digit_bits;
   uint32_t *status;
 };
 
-// Warp-synchronous: each lane takes one item of a 32-item group.  The
-// group's pairs occupy one contiguous output range; when it holds at most
-// kStage pairs they are assembled in shared memory (small items by their own
-// lane, large ones by the whole warp) and written back with coalesced
-// stores, the pair sort's digit histograms being taken during that flush.
-// Wider groups write directly.
-constexpr uint32_t kSmallItem = 8;
-constexpr uint32_t kBigItem = 64;   // larger items go to k_emit_big
-constexpr int kStage = 768;
+constexpr uint32_t kBigItem = 64;   // items with more pairs go to k_emit_big
 constexpr int kEmitThreads = 128;
+
+// Adds the pair sort's digits of tile id t (lanes with `on`) to the block's
+// histograms; a warp whose tiles share a digit adds once.
 
 __device__ __forceinline__ void hist_add_warp(uint32_t (*sh)[256], bool on, uint32_t t,
                                               int passes, int bits, uint32_t dmask, int lane) {
@@ -641,10 +642,18 @@ __device__ __forceinline__ void hist_add_warp(uint32_t (*sh)[256], bool on, uint
   }
 }
 
-__global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
+// Emit of (tile, item) pairs in depth order.  Each item's kept tiles are an
+// arithmetic function of its rank inside the item: rows of the rectangle
+// (TABLE = false: no filter), or the row intervals of the table the pair
+// count wrote (tight support and/or foveation filter).  So the pairs of a
+// warp's 32 items are expanded load-balanced: lane l writes output positions
+// g0 + l, g0 + l + 32, ... of the group, finds the owning item by binary
+// search over the group's offsets (warp shuffles) and maps its rank to a
+// tile.  Writes are coalesced; no lane loops over another lane's item.
+// Items queued for k_emit_big (many tiles, or no row table) are skipped.
+template <bool TABLE>
+__global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
   __shared__ uint32_t sh[4][256];
-  __shared__ uint32_t s_t[kEmitThreads / 32][kStage];
-  __shared__ uint32_t s_v[kEmitThreads / 32][kStage];
   for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0u;
   __syncthreads();
   unsigned long long nn = *a.n_items;
@@ -657,117 +666,89 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
     set_status(a.status, GS_ERR_CAPACITY);
   const long long warps = (long long)gridDim.x * (blockDim.x / 32);
   const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + wl;
-  uint32_t *st = s_t[wl], *sv = s_v[wl];
   for (long long base = wid * 32; base < n; base += warps * 32) {
     const long long k = base + lane;
     const bool valid = k < n;
-    uint32_t j = 0, cnt = 0, off = 0, view = 0;
+    uint32_t j = 0, cnt = 0, off = 0xffffffffu;
     uint2 r = make_uint2(0u, 0u);
     if (valid) {
       j = items[k];
       off = a.offsets[k];
       cnt = a.count[j];
       r = a.rect[j];
-      view = a.view[j];
     }
-    // items with more than kBigItem tiles are queued for k_emit_big, whose
-    // warps take them one at a time (they cluster in depth order and would
-    // otherwise leave a few warps with most of the work)
-    const bool huge = valid && cnt > kBigItem;
+    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+    const bool huge = valid && (cnt > kBigItem || (TABLE && !has_table(x0, x1, y0, y1)));
     const uint32_t hb = __ballot_sync(0xffffffffu, huge);
-    const bool any_huge = hb != 0u;
-    if (any_huge) {
-      // one queue reservation per warp
-      uint32_t base = 0;
-      if (lane == __ffs(hb) - 1) base = atomicAdd(a.big_count, (uint32_t)__popc(hb));
-      base = __shfl_sync(0xffffffffu, base, __ffs(hb) - 1);
-      if (huge) a.bigq[base + __popc(hb & ltmask)] = (uint32_t)k;
+    if (hb) {
+      uint32_t qb = 0;
+      if (lane == __ffs(hb) - 1) qb = atomicAdd(a.big_count, (uint32_t)__popc(hb));
+      qb = __shfl_sync(0xffffffffu, qb, __ffs(hb) - 1);
+      if (huge) a.bigq[qb + __popc(hb & ltmask)] = (uint32_t)k;
     }
-    // the group's output range [g0, g1)
+    uint4 tbl = make_uint4(0u, 0u, 0u, 0u);
+    if (TABLE && valid && !huge && cnt > 0) tbl = a.table[j];
     const uint32_t g0 = __shfl_sync(0xffffffffu, off, 0);
     const uint32_t last = 31 - __clz(__ballot_sync(0xffffffffu, valid));
     const uint32_t g1 = __shfl_sync(0xffffffffu, off + cnt, last);
-    const bool staged = !any_huge && g1 - g0 <= (uint32_t)kStage;
-    // small items: one lane each
-    if (valid && cnt <= kSmallItem && cnt > 0) {
-      const ViewDev &vd = a.views[view];
-      const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-      const uint8_t m = a.tile_level ? a.rec_m[j] : 0;
-      long long o = off;
-      for (int y = y0; y <= y1; ++y)
-        for (int x = x0; x <= x1; ++x) {
-          const long long t = vd.tile_base + (long long)y * vd.tx + x;
-          if (a.tile_level && a.tile_level[t] > m) continue;
-          if (staged) {
-            st[o - g0] = (uint32_t)t;
-            sv[o - g0] = j;
-          } else if (o < a.pair_capacity) {
-            a.pkey[o] = (uint32_t)t;
-            a.pval[o] = j;
-            for (int p = 0; p < a.passes; ++p)
-              atomicAdd(&sh[p][((uint32_t)t >> (a.digit_bits * p)) & dmask], 1u);
+    for (uint32_t p0 = g0; p0 < g1; p0 += 32) {
+      const uint32_t pos = p0 + lane;
+      // owning item: the last lane whose offset is <= pos (offsets ascend;
+      // invalid lanes hold 0xffffffff)
+      int L = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t o = __shfl_sync(0xffffffffu, off, L + step);
+        if (o <= pos) L += step;
+      }
+      const uint32_t ioff = __shfl_sync(0xffffffffu, off, L);
+      const uint32_t icnt = __shfl_sync(0xffffffffu, cnt, L);
+      const bool ihuge = __shfl_sync(0xffffffffu, (int)huge, L) != 0;
+      const uint32_t ij = __shfl_sync(0xffffffffu, j, L);
+      const uint32_t rx = __shfl_sync(0xffffffffu, r.x, L);
+      const uint32_t ry = __shfl_sync(0xffffffffu, r.y, L);
+      uint4 it;
+      it.x = __shfl_sync(0xffffffffu, tbl.x, L);
+      it.y = __shfl_sync(0xffffffffu, tbl.y, L);
+      it.z = __shfl_sync(0xffffffffu, tbl.z, L);
+      it.w = __shfl_sync(0xffffffffu, tbl.w, L);
+      bool wr = pos < g1 && !ihuge && pos - ioff < icnt && (long long)pos < a.pair_capacity;
+      uint32_t t = 0;
+      if (wr) {
+        const uint32_t rank = pos - ioff;
+        const int ix0 = rx & 0xffff, ix1 = rx >> 16, iy0 = ry & 0xffff;
+        int row = 0, col = 0;
+        if (TABLE) {
+          // walk the row table
+          uint32_t rem = rank;
+          bool found = false;
+#pragma unroll
+          for (int q = 0; q < kTableRows; ++q) {
+            int first, lastc;
+            table_row(it, q, first, lastc);
+            const uint32_t len = lastc >= first ? (uint32_t)(lastc - first + 1) : 0u;
+            if (!found && rem < len) {
+              row = q;
+              col = first + (int)rem;
+              found = true;
+            }
+            if (!found) rem -= len;
           }
-          ++o;
-        }
-    }
-    // large items: the whole warp, one item at a time
-    uint32_t big = __ballot_sync(0xffffffffu, valid && cnt > kSmallItem && cnt <= kBigItem);
-    while (big) {
-      const int src = __ffs(big) - 1;
-      big &= big - 1;
-      const uint32_t bj = __shfl_sync(0xffffffffu, j, src);
-      const uint32_t boff = __shfl_sync(0xffffffffu, off, src);
-      const uint32_t rx = __shfl_sync(0xffffffffu, r.x, src);
-      const uint32_t ry = __shfl_sync(0xffffffffu, r.y, src);
-      const uint32_t bview = __shfl_sync(0xffffffffu, view, src);
-      const ViewDev &vd = a.views[bview];
-      const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
-      const int w = x1 - x0 + 1;
-      const int area = w * (y1 - y0 + 1);
-      const uint8_t m = a.tile_level ? a.rec_m[bj] : 0;
-      long long run = boff;
-      for (int l0 = 0; l0 < area; l0 += 32) {
-        const int l = l0 + lane;
-        bool kept = l < area;
-        long long t = 0;
-        if (kept) {
-          t = vd.tile_base + (long long)(y0 + l / w) * vd.tx + (x0 + l % w);
-          if (a.tile_level && a.tile_level[t] > m) kept = false;
-        }
-        // every lane takes part in the ballots (never inside && or ?:)
-        const uint32_t b = __ballot_sync(0xffffffffu, kept);
-        const long long o = run + __popc(b & ltmask);
-        if (staged) {
-          if (kept) {
-            st[o - g0] = (uint32_t)t;
-            sv[o - g0] = bj;
-          }
+          wr = found;
         } else {
-          const bool wr = kept && o < a.pair_capacity;
-          if (wr) {
-            a.pkey[o] = (uint32_t)t;
-            a.pval[o] = bj;
-          }
-          hist_add_warp(sh, wr, (uint32_t)t, a.passes, a.digit_bits, dmask, lane);
+          const uint32_t w = (uint32_t)(ix1 - ix0 + 1);
+          row = (int)(rank / w);
+          col = (int)(rank - (uint32_t)row * w);
         }
-        run += __popc(b);
-      }
-    }
-    // coalesced flush of a staged group
-    if (staged) {
-      __syncwarp();
-      for (uint32_t l0 = 0; l0 < g1 - g0; l0 += 32) {
-        const uint32_t l = l0 + lane;
-        const long long o = (long long)g0 + l;
-        const bool wr = l < g1 - g0 && o < a.pair_capacity;
-        const uint32_t t = wr ? st[l] : 0u;
+        const uint32_t view = a.view[ij];
+        const ViewDev &vd = a.views[view];
+        t = (uint32_t)(vd.tile_base + (long long)(iy0 + row) * vd.tx + (ix0 + col));
         if (wr) {
-          a.pkey[o] = t;
-          a.pval[o] = sv[l];
+          a.pkey[pos] = t;
+          a.pval[pos] = ij;
         }
-        hist_add_warp(sh, wr, t, a.passes, a.digit_bits, dmask, lane);
       }
-      __syncwarp();
+      hist_add_warp(sh, wr, t, a.passes, a.digit_bits, dmask, lane);
     }
   }
   __syncthreads();
@@ -780,6 +761,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
 // Items with more than kBigItem tiles: the warps of the grid stride over the
 // queue (no shared ticket to contend on) and write each item's tiles 32 at a
 // time (ballot prefix for the kept ones).
+template <bool FOV, bool TIGHT>
 __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
   __shared__ uint32_t sh[4][256];
   for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) (&sh[0][0])[q] = 0u;
@@ -797,32 +779,41 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
     const uint2 r = a.rect[j];
     const ViewDev &vd = a.views[a.view[j]];
     const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-    const int w = x1 - x0 + 1;
-    const uint8_t m = a.tile_level ? a.rec_m[j] : 0;
+    const int m = FOV ? (int)a.rec_m[j] : 0;
+    SuppPre pre;
+    if (TIGHT) pre = supp_prep(a.supp[j], a.supp2[j]);
     long long run = off;
-    // row by row, 32 tiles of a row at a time (no division per tile)
-    for (int y = y0, x = 0; y <= y1; x += 32) {
-      if (x >= w) {
-        x = -32;
-        ++y;
-        continue;
+    // row by row (the kept columns of a row form one interval), 32 tiles of
+    // a row at a time
+    for (int y = y0; y <= y1; ++y) {
+      int xa = x0, xb = x1;
+      if (TIGHT) {
+        int ia, ib;
+        if (!row_interval(pre, y, a.tile, ia, ib)) continue;   // warp-uniform
+        xa = max(xa, ia);
+        xb = min(xb, ib);
       }
-      const int xx = x + lane;
-      bool kept = xx < w;
-      long long t = 0;
-      if (kept) {
-        t = vd.tile_base + (long long)y * vd.tx + (x0 + xx);
-        if (a.tile_level && a.tile_level[t] > m) kept = false;
+      if (FOV) {
+        int la, lb;
+        level_row(a.level_rows, vd.row_base + y, m, la, lb);
+        xa = max(xa, la);
+        xb = min(xb, lb);
       }
-      const uint32_t b = __ballot_sync(0xffffffffu, kept);
-      const long long o = run + __popc(b & ltmask);
-      const bool wr = kept && o < a.pair_capacity;
-      if (wr) {
-        a.pkey[o] = (uint32_t)t;
-        a.pval[o] = j;
+      for (int xs = xa; xs <= xb; xs += 32) {
+        const int x = xs + lane;
+        const bool kept = x <= xb;
+        long long t = 0;
+        if (kept) t = vd.tile_base + (long long)y * vd.tx + x;
+        const uint32_t b = __ballot_sync(0xffffffffu, kept);
+        const long long o = run + __popc(b & ltmask);
+        const bool wr = kept && o < a.pair_capacity;
+        if (wr) {
+          a.pkey[o] = (uint32_t)t;
+          a.pval[o] = j;
+        }
+        hist_add_warp(sh, wr, (uint32_t)t, a.passes, a.digit_bits, dmask, lane);
+        run += __popc(b);
       }
-      hist_add_warp(sh, wr, (uint32_t)t, a.passes, a.digit_bits, dmask, lane);
-      run += __popc(b);
     }
   }
   __syncthreads();
@@ -838,7 +829,8 @@ constexpr int kRangeUnroll = 8;
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t *key_a, const uint32_t *key_b,
                                                 const uint32_t *sel,
                                                 const unsigned long long *n_pairs,
-                                                long long capacity, uint2 *ranges) {
+                                                long long capacity, long long tiles,
+                                                uint2 *ranges, uint32_t *status) {
   unsigned long long nn = *n_pairs;
   const long long n = (long long)nn > capacity ? capacity : (long long)nn;
   const uint32_t *key = *sel ? key_b : key_a;
@@ -857,6 +849,10 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *key_a, const uin
     for (int u = 0; u < kRangeUnroll; ++u) {
       const long long p = base + u * blockDim.x + threadIdx.x;
       if (p >= n) continue;
+      if ((long long)k[u] >= tiles) {   // never written by a consistent emit
+        set_status(status, GS_ERR_CUDA);
+        continue;
+      }
       if (p == 0 || kp[u] != k[u]) ranges[k[u]].x = (uint32_t)p;
       if (p == n - 1 || kn[u] != k[u]) ranges[k[u]].y = (uint32_t)(p + 1);
     }
@@ -933,6 +929,12 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.views = region<ViewDev>(p, ws, R_VIEWS);
   ea.tile_level = p->has_fov ? region<uint8_t>(p, ws, R_TILE_LEVEL) : nullptr;
   ea.rec_m = p->has_fov ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
+  const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
+  ea.supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
+  ea.supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
+  ea.table = (tight || p->has_fov) ? region<uint4>(p, ws, R_REC_TABLE) : nullptr;
+  ea.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
+  ea.tile = p->tile;
   ea.n_pairs = &hdr->n_pairs;
   ea.pair_capacity = p->max_pairs;
   ea.pkey = region<uint32_t>(p, ws, R_PKEY_A);
@@ -946,8 +948,20 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.big_ticket = &hdr->big_ticket;
   e = cudaMemsetAsync(&hdr->big_count, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  k_emit<<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
-  k_emit_big<<<g_stream_blocks, 256, 0, s>>>(ea);
+  const bool fov = ea.tile_level != nullptr;
+  if (fov && tight) {
+    k_emit_expand<true><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
+    k_emit_big<true, true><<<g_stream_blocks, 256, 0, s>>>(ea);
+  } else if (fov) {
+    k_emit_expand<true><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
+    k_emit_big<true, false><<<g_stream_blocks, 256, 0, s>>>(ea);
+  } else if (tight) {
+    k_emit_expand<true><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
+    k_emit_big<false, true><<<g_stream_blocks, 256, 0, s>>>(ea);
+  } else {
+    k_emit_expand<false><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
+    k_emit_big<false, false><<<g_stream_blocks, 256, 0, s>>>(ea);
+  }
   // 4. stable sort of the pairs by tile
   SortArgs t = {};
   t.first_keys = ea.pkey;
@@ -973,7 +987,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   e = cudaMemsetAsync(ranges, 0, p->bytes[R_RANGES], s);
   if (e != cudaSuccess) return e;
   k_ranges<<<g_stream_blocks, 256, 0, s>>>(t.keys[0], t.keys[1], &hdr->sel_pair, &hdr->n_pairs,
-                                         p->max_pairs, ranges);
+                                         p->max_pairs, p->tiles_total, ranges, &hdr->status);
   return cudaGetLastError();
 }
 

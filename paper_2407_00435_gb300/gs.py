@@ -22,6 +22,7 @@ from . import build as _build
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_UNSUPPORTED = range(6)
 GS_FLAG_FOVEATED = 1
 GS_FLAG_BACKWARD = 2
+GS_FLAG_TIGHT = 4
 GS_MAX_LEVELS = 8
 (GS_REGION_ITEM_GID, GS_REGION_ITEM_VIEW, GS_REGION_ITEM_DEPTH, GS_REGION_ITEM_COUNT) = (1, 2, 3, 4)
 GS_REGION_RANGES, GS_REGION_TILE_LEVEL = 7, 8
@@ -212,13 +213,14 @@ class Renderer:
 
     def __init__(self, n, sh_degree, cams, tile=16, foveated=False, backward=False,
                  max_pairs=0, max_levels=0, chunk=0, radix_bits=0, chunk_slots=0,
-                 device="cuda"):
+                 tight=False, device="cuda"):
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cams_np = np.asarray(cams, np.float32).reshape(-1, 20)
         self.V = len(self.cams_np)
         self.device = device
         self.cfg = gs_config(tile, chunk, (GS_FLAG_FOVEATED if foveated else 0)
-                             | (GS_FLAG_BACKWARD if backward else 0), max_levels,
+                             | (GS_FLAG_BACKWARD if backward else 0)
+                             | (GS_FLAG_TIGHT if tight else 0), max_levels,
                              radix_bits, chunk_slots, max_pairs)
         self.plan = C.create_string_buffer(int(_lib.gs_plan_size()))
         self._cams_h = cams_host(self.cams_np)
@@ -307,7 +309,10 @@ class Renderer:
         tile_bits = max(1, int(self.T_tiles - 1).bit_length())
         want = self.cfg.radix_bits or 8
         passes = min(4, (tile_bits + want - 1) // want)
-        project = 1 + (1 if fov else 0) + (1 if self.n > 0 else 0)
+        # views, levels, project, pair count (+ warp-wide count with the tight support)
+        project = 1 + (1 if fov else 0) + (2 if self.n > 0 else 0)
+        if self.n > 0 and self.cfg.flags & GS_FLAG_TIGHT:
+            project += 1
         # depth sort (hist, scan, 4 passes of upsweep + scan + downsweep),
         # offsets (upsweep, scan, downsweep), emit + large-item emit, pair
         # sort (scan + 3 kernels per pass), ranges
