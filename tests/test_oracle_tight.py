@@ -154,3 +154,26 @@ def test_tight_support_without_any_blendable_pixel(orc):
     sc.opac[:] = 0.5 / 255.0
     b = orc.bin_pairs(sc, _views(rng, [(64, 64)]), 16, tight=True)
     assert (b.vis == 1).sum() > 100 and b.K == 0
+
+
+@pytest.mark.parametrize("band", [0.0, 6.0, 40.0])
+def test_tile_levels_at_most_m_are_one_interval_per_row(orc, band):
+    # the foveation filter keeps a pair iff tile level <= m; per tile row those
+    # tiles form one run of columns (levels first fall, then rise along a row)
+    rng = np.random.default_rng(35)
+    for trial in range(6):
+        W, H = int(rng.integers(40, 300)), int(rng.integers(40, 300))
+        cams = synth.orbit_cameras(rng, 1, 3.0, [(W, H)])
+        L = int(rng.integers(2, 6))
+        rings = np.sort(rng.uniform(3, 40, L - 1))
+        gaze = np.array([[rng.uniform(-0.2, 1.2) * W, rng.uniform(-0.2, 1.2) * H]], np.float32)
+        f = synth.Foveation(L, np.ones(10, np.uint8), synth.ring_tangents(list(rings)), band, gaze)
+        for tile in (16, 8):
+            tl = orc.tile_levels(cams, tile, orc.FovArrays.from_synth(f))
+            tx, ty = (W + tile - 1) // tile, (H + tile - 1) // tile
+            lv = tl.reshape(ty, tx)
+            for m in range(1, L + 1):
+                for row in lv:
+                    cols = np.nonzero(row <= m)[0]
+                    if len(cols):
+                        assert cols[-1] - cols[0] + 1 == len(cols), (trial, tile, m, row)
