@@ -85,7 +85,7 @@ struct Hdr {
   uint32_t hist[2][4][256];       // digit histograms: [sort][pass][digit]
   unsigned long long queue;       // next work item of the chunked render
   uint32_t n_slots;               // chunk slots requested by the chunk plan
-  uint32_t count_big;             // items queued for the warp-wide pair count
+  uint32_t pad1;
 };
 
 // Per-view constants, computed on the device from the cameras.
@@ -106,9 +106,10 @@ constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 20;   // bounded waits (about a second), then GS_ERR_TIMEOUT
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortPart = kSortThreads * kSortItems;   // 4096 keys per partition
+constexpr int kSortThreads = 256;                     // upsweep / histogram blocks
+constexpr int kDownThreads = 512;                     // downsweep blocks
+constexpr int kDownItems = 8;                         // keys per downsweep thread
+constexpr int kSortPart = kDownThreads * kDownItems;  // 4096 keys per partition
 constexpr int kSortBlocksPerSm = 8;   // most sort blocks resident per SM (sizes the block table)
 constexpr int kSortMaxBlocks = 1024;  // grid cap of the sort's downsweep
 constexpr int kSortSub = 4;           // upsweep sub-ranges per downsweep block

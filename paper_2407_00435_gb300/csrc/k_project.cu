@@ -205,8 +205,6 @@ struct ProjArgs {
   float2 *rec_supp2;            // (c, tau)
   uint4 *rec_table;              // row intervals of small rectangles (tight or foveated)
   const uint32_t *level_rows;    // columns kept by the foveation filter, per row and level
-  uint32_t *count_q;             // items left to k_count_big
-  unsigned int *count_q_len;
   const float *opacity_lv;      // (L-1, N) level opacities the support must cover, or null
   int n_opacity_lv;
 };
@@ -550,111 +548,180 @@ __device__ __forceinline__ void project_value(const ProjArgs &a, const ProjSmem<
 // foveation filter (tile level <= m: one interval per row, from the level
 // rows) and, with the tight support, lie in their row's interval.  Items
 // whose rectangle has at most kTableRows rows get their row intervals as a
-// table for the emit.  With the tight support, items with more rows are
-// queued for k_count_big (a warp each).  A kernel of its own after the
-// projection, which keeps the projection's register footprint small.
-__global__ void __launch_bounds__(256) k_count_pairs(ProjArgs a) {
+// table for the emit; their rows are evaluated warp-cooperatively: the rows
+// of a warp's 32 items are spread over the lanes (owner found by binary
+// search over the row prefix sums, its constants fetched by shuffles) and
+// the per-row results meet in shared memory.  With the tight support, items
+// with more rows are taken by the whole warp, one at a time, lanes over rows.
+constexpr int kCountThreads = 256;
+
+__global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
+  __shared__ uint16_t s_row[kCountThreads / 32][32][kTableRows];   // xa | xb << 8 (relative)
   const long long slots = a.n * a.V;
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < slots;
-       j += (long long)gridDim.x * blockDim.x) {
-    if (a.rec_depth[j] == 0xffffffffu) continue;   // invisible: count already 0
-    const uint2 r = a.rec_rect[j];
-    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-    if (!a.rec_supp && !a.tile_level) {
-      a.rec_count[j] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-      continue;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const long long warps = (long long)gridDim.x * (kCountThreads / 32);
+  const long long wid = (long long)blockIdx.x * (kCountThreads / 32) + wl;
+  const bool tight = a.rec_supp != nullptr, fov = a.tile_level != nullptr;
+  for (long long base = wid * 32; base < slots; base += warps * 32) {
+    const long long j = base + lane;
+    bool vis = false;
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    if (j < slots && a.rec_depth[j] != 0xffffffffu) {
+      vis = true;
+      const uint2 r = a.rec_rect[j];
+      x0 = r.x & 0xffff; x1 = r.x >> 16; y0 = r.y & 0xffff; y1 = r.y >> 16;
     }
-    const bool tabled = has_table(x0, x1, y0, y1);
-    if (a.rec_supp && !tabled) {
-      // many rows: counted by a whole warp in k_count_big
-      const unsigned int q = atomicAdd(a.count_q_len, 1u);
-      a.count_q[q] = (uint32_t)j;
-      continue;
+    // rows this lane's item contributes to the cooperative pass
+    int rows = 0;
+    if (vis) {
+      if (!tight && !fov) {
+        a.rec_count[j] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+      } else if (!has_table(x0, x1, y0, y1)) {
+        if (tight) {
+          // many rows: counted by the whole warp below
+        } else {
+          // foveation filter only: one interval lookup per row
+          const ViewDev &vd = a.views[j % a.V];
+          const int m = (int)a.rec_m[j];
+          uint32_t pairs = 0;
+          for (int y = y0; y <= y1; ++y) {
+            int la, lb;
+            level_row(a.level_rows, vd.row_base + y, m, la, lb);
+            const int xa = max(x0, la), xb = min(x1, lb);
+            if (xa <= xb) pairs += (uint32_t)(xb - xa + 1);
+          }
+          a.rec_count[j] = pairs;
+        }
+      } else {
+        rows = y1 - y0 + 1;
+      }
     }
-    const ViewDev &vd = a.views[j % a.V];
-    const int m = a.tile_level ? (int)a.rec_m[j] : 0;
-    SuppPre pre;
-    if (a.rec_supp) {
-      // tau covers the largest opacity any level composites the point with
-      const long long i = j / a.V;
+    // per-item constants of the row test
+    SuppPre pre = {};
+    int m = 0, rbase = 0;
+    if (rows) {
+      if (tight) {
+        const long long i = j / a.V;
+        float o_max = a.opac[i];
+        for (int l = 0; l < a.n_opacity_lv; ++l)
+          o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
+        const float2 s1 = make_float2(a.rec_supp2[j].x, tight_tau(o_max));
+        a.rec_supp2[j] = s1;
+        pre = supp_prep(a.rec_supp[j], s1);
+      }
+      if (fov) {
+        m = (int)a.rec_m[j];
+        rbase = a.views[j % a.V].row_base;
+      }
+    }
+    // inclusive prefix of the rows over the warp
+    int incl = rows;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - rows;
+    for (int q0 = 0; q0 < total; q0 += 32) {
+      const int q = q0 + lane;
+      // owner: the first lane whose inclusive prefix exceeds q
+      int L = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, incl, L + step - 1);
+        if (e <= q) L += step;
+      }
+      const int oexcl = __shfl_sync(0xffffffffu, excl, L);
+      const int ox0 = __shfl_sync(0xffffffffu, x0, L), ox1 = __shfl_sync(0xffffffffu, x1, L);
+      const int oy0 = __shfl_sync(0xffffffffu, y0, L);
+      SuppPre p;
+      p.u = __shfl_sync(0xffffffffu, pre.u, L);
+      p.v = __shfl_sync(0xffffffffu, pre.v, L);
+      p.b = __shfl_sync(0xffffffffu, pre.b, L);
+      p.ic = __shfl_sync(0xffffffffu, pre.ic, L);
+      p.det = __shfl_sync(0xffffffffu, pre.det, L);
+      p.ct = __shfl_sync(0xffffffffu, pre.ct, L);
+      p.xe = __shfl_sync(0xffffffffu, pre.xe, L);
+      p.ye = __shfl_sync(0xffffffffu, pre.ye, L);
+      p.dys = __shfl_sync(0xffffffffu, pre.dys, L);
+      p.any = __shfl_sync(0xffffffffu, (int)pre.any, L) != 0;
+      const int om = __shfl_sync(0xffffffffu, m, L), orb = __shfl_sync(0xffffffffu, rbase, L);
+      if (q < total) {
+        const int r = q - oexcl, y = oy0 + r;
+        int xa = ox0, xb = ox1;
+        bool any = true;
+        if (tight) {
+          int ia, ib;
+          any = row_interval(p, y, a.tile, ia, ib);
+          xa = max(xa, ia);
+          xb = min(xb, ib);
+        }
+        if (fov) {
+          int la, lb;
+          level_row(a.level_rows, orb + y, om, la, lb);
+          xa = max(xa, la);
+          xb = min(xb, lb);
+        }
+        s_row[wl][L][r] = (any && xa <= xb) ? (uint16_t)((xa - ox0) | ((xb - ox0) << 8))
+                                            : (uint16_t)0x00ffu;   // empty: first 255 > last 0
+      }
+    }
+    __syncwarp();
+    // tight support, rectangles without a table: the whole warp takes each
+    // such item in turn, lanes over its rows
+    uint32_t pending = __ballot_sync(0xffffffffu, vis && tight && !has_table(x0, x1, y0, y1));
+    while (pending) {
+      const int src = __ffs(pending) - 1;
+      pending &= pending - 1;
+      const long long jb = base + src;
+      const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+      const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
+      const long long i = jb / a.V;
       float o_max = a.opac[i];
       for (int l = 0; l < a.n_opacity_lv; ++l)
         o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
-      const float2 s1 = make_float2(a.rec_supp2[j].x, tight_tau(o_max));
-      a.rec_supp2[j] = s1;
-      pre = supp_prep(a.rec_supp[j], s1);
-    }
-    uint32_t tb[4] = {0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu};   // rows empty
-    uint32_t pairs = 0;
-    for (int y = y0; y <= y1; ++y) {
-      int xa = x0, xb = x1;
-      if (a.rec_supp) {
-        int ia, ib;
-        if (!row_interval(pre, y, a.tile, ia, ib)) continue;
-        xa = max(xa, ia);
-        xb = min(xb, ib);
+      const float2 s1 = make_float2(a.rec_supp2[jb].x, tight_tau(o_max));
+      const SuppPre pb = supp_prep(a.rec_supp[jb], s1);
+      const int bm = fov ? (int)a.rec_m[jb] : 0;
+      const int brb = fov ? a.views[jb % a.V].row_base : 0;
+      uint32_t bpairs = 0;
+      for (int y = by0 + lane; y <= by1; y += 32) {
+        int xa, xb;
+        if (!row_interval(pb, y, a.tile, xa, xb)) continue;
+        xa = max(xa, bx0);
+        xb = min(xb, bx1);
+        if (fov) {
+          int la, lb;
+          level_row(a.level_rows, brb + y, bm, la, lb);
+          xa = max(xa, la);
+          xb = min(xb, lb);
+        }
+        if (xa <= xb) bpairs += (uint32_t)(xb - xa + 1);
       }
-      if (a.tile_level) {
-        int la, lb;
-        level_row(a.level_rows, vd.row_base + y, m, la, lb);
-        xa = max(xa, la);
-        xb = min(xb, lb);
-      }
-      if (xa > xb) continue;
-      pairs += (uint32_t)(xb - xa + 1);
-      if (tabled) {
-        const int rr = y - y0;
-        const uint32_t e = (uint32_t)(xa - x0) | ((uint32_t)(xb - x0) << 8);
-        const int sh = 16 * (rr & 1);
-        const uint32_t cur = rr < 2 ? tb[0] : rr < 4 ? tb[1] : rr < 6 ? tb[2] : tb[3];
-        const uint32_t nv = (cur & ~(0xffffu << sh)) | (e << sh);
-        if (rr < 2) tb[0] = nv; else if (rr < 4) tb[1] = nv; else if (rr < 6) tb[2] = nv; else tb[3] = nv;
+      for (int o = 16; o > 0; o >>= 1) bpairs += __shfl_xor_sync(0xffffffffu, bpairs, o);
+      if (lane == 0) {
+        a.rec_supp2[jb] = s1;
+        a.rec_count[jb] = bpairs;
       }
     }
-    a.rec_count[j] = pairs;
-    if (tabled) a.rec_table[j] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
-  }
-}
-
-// Pair counts of the items k_count_pairs queued (tight support, rectangles
-// of more than kTableRows rows or kTableCols columns): one warp per item,
-// lanes over the rows.
-__global__ void __launch_bounds__(256) k_count_big(ProjArgs a) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t nq = *a.count_q_len;
-  const uint32_t warps = gridDim.x * (blockDim.x / 32);
-  for (uint32_t qi = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); qi < nq; qi += warps) {
-    const long long j = a.count_q[qi];
-    const uint2 r = a.rec_rect[j];
-    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-    const ViewDev &vd = a.views[j % a.V];
-    const int m = a.tile_level ? (int)a.rec_m[j] : 0;
-    const long long i = j / a.V;
-    float o_max = a.opac[i];
-    for (int l = 0; l < a.n_opacity_lv; ++l)
-      o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
-    const float2 s1 = make_float2(a.rec_supp2[j].x, tight_tau(o_max));
-    const SuppPre pre = supp_prep(a.rec_supp[j], s1);
-    uint32_t pairs = 0;
-    for (int y = y0 + lane; y <= y1; y += 32) {
-      int xa, xb;
-      if (!row_interval(pre, y, a.tile, xa, xb)) continue;
-      xa = max(xa, x0);
-      xb = min(xb, x1);
-      if (a.tile_level) {
-        int la, lb;
-        level_row(a.level_rows, vd.row_base + y, m, la, lb);
-        xa = max(xa, la);
-        xb = min(xb, lb);
+    if (rows) {
+      uint32_t tb[4] = {0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu};
+      uint32_t pairs = 0;
+      for (int r = 0; r < rows; ++r) {
+        const uint32_t e = s_row[wl][lane][r];
+        const int first = (int)(e & 0xffu), last = (int)(e >> 8);
+        if (first <= last) pairs += (uint32_t)(last - first + 1);
+        const int sh = 16 * (r & 1);
+        if (r < 2) tb[0] = (tb[0] & ~(0xffffu << sh)) | (e << sh);
+        else if (r < 4) tb[1] = (tb[1] & ~(0xffffu << sh)) | (e << sh);
+        else if (r < 6) tb[2] = (tb[2] & ~(0xffffu << sh)) | (e << sh);
+        else tb[3] = (tb[3] & ~(0xffffu << sh)) | (e << sh);
       }
-      if (xa > xb) continue;
-      pairs += (uint32_t)(xb - xa + 1);
-    }
-    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-    if (lane == 0) {
-      a.rec_supp2[j] = s1;
       a.rec_count[j] = pairs;
+      a.rec_table[j] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
     }
+    __syncwarp();
   }
 }
 
@@ -821,8 +888,6 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
   a.rec_supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
   a.rec_table = (tight || p->has_fov) ? region<uint4>(p, ws, R_REC_TABLE) : nullptr;
   a.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
-  a.count_q = region<uint32_t>(p, ws, R_BIGQ);          // free until the emit
-  a.count_q_len = &a.hdr->count_big;
   a.opacity_lv = p->has_fov ? p->fov.opacity_lv : nullptr;
   a.n_opacity_lv = a.opacity_lv ? p->fov.n_levels - 1 : 0;
   unsigned grid = (unsigned)((p->n + kProjThreads - 1) / kProjThreads);
@@ -833,9 +898,8 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
     default: k_project<16><<<grid, kProjThreads, 0, s>>>(a); break;
   }
   const long long slots = p->n * p->V;
-  const long long cb = (slots + 255) / 256;
-  k_count_pairs<<<(unsigned)(cb < 65535 ? cb : 65535), 256, 0, s>>>(a);
-  if (tight) k_count_big<<<p->num_sms > 0 ? 4 * p->num_sms : 608, 256, 0, s>>>(a);
+  const long long cb = (slots + kCountThreads - 1) / kCountThreads;
+  k_count_pairs<<<(unsigned)(cb < 65535 ? cb : 65535), kCountThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -211,10 +211,12 @@ __global__ void __launch_bounds__(kSortThreads) k_upsweep(SortArgs a, int pass) 
 }
 
 // ---- scan: bsum[s][d] <- global start of digit d + its count in
-// sub-ranges < s.  One block per 32 digits; warp w owns a run of rows,
-// read kScanChunk rows at a time (independent loads).
+// sub-ranges < s.  One block per 32 digits; warp w owns a run of rows.  Up
+// to kScanRegRows rows per warp stay in registers between the two phases
+// (one read of the table); longer runs are read twice, kScanChunk at a time.
 constexpr int kScanThreads = 1024;
 constexpr int kScanChunk = 16;
+constexpr int kScanRegRows = 48;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pass) {
   __shared__ uint32_t s_p[kScanThreads / 32][32];
@@ -226,13 +228,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pa
   const int rows = (R + NW - 1) / NW;
   const int r0 = warp * rows;
   const int r1 = r0 + rows < R ? r0 + rows : R;
+  const bool in_regs = rows <= kScanRegRows;
+  uint32_t v[kScanRegRows];
   uint32_t sum = 0;
-  for (int c = r0; c < r1; c += kScanChunk) {
-    uint32_t v[kScanChunk];
+  if (in_regs) {
 #pragma unroll
-    for (int i = 0; i < kScanChunk; ++i) v[i] = c + i < r1 ? a.bsum[(long long)(c + i) * 256 + d] : 0u;
+    for (int i = 0; i < kScanRegRows; ++i)
+      v[i] = r0 + i < r1 ? a.bsum[(long long)(r0 + i) * 256 + d] : 0u;
 #pragma unroll
-    for (int i = 0; i < kScanChunk; ++i) sum += v[i];
+    for (int i = 0; i < kScanRegRows; ++i) sum += v[i];
+  } else {
+    for (int c = r0; c < r1; c += kScanChunk) {
+      uint32_t w[kScanChunk];
+#pragma unroll
+      for (int i = 0; i < kScanChunk; ++i) w[i] = c + i < r1 ? a.bsum[(long long)(c + i) * 256 + d] : 0u;
+#pragma unroll
+      for (int i = 0; i < kScanChunk; ++i) sum += w[i];
+    }
   }
   s_p[warp][lane] = sum;
   __syncthreads();
@@ -246,14 +258,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pa
   }
   __syncthreads();
   uint32_t run = s_p[warp][lane];
-  for (int c = r0; c < r1; c += kScanChunk) {
-    uint32_t v[kScanChunk];
+  if (in_regs) {
 #pragma unroll
-    for (int i = 0; i < kScanChunk; ++i) v[i] = c + i < r1 ? a.bsum[(long long)(c + i) * 256 + d] : 0u;
-#pragma unroll
-    for (int i = 0; i < kScanChunk; ++i) {
-      if (c + i < r1) a.bsum[(long long)(c + i) * 256 + d] = run;
+    for (int i = 0; i < kScanRegRows; ++i) {
+      if (r0 + i < r1) a.bsum[(long long)(r0 + i) * 256 + d] = run;
       run += v[i];
+    }
+  } else {
+    for (int c = r0; c < r1; c += kScanChunk) {
+      uint32_t w[kScanChunk];
+#pragma unroll
+      for (int i = 0; i < kScanChunk; ++i) w[i] = c + i < r1 ? a.bsum[(long long)(c + i) * 256 + d] : 0u;
+#pragma unroll
+      for (int i = 0; i < kScanChunk; ++i) {
+        if (c + i < r1) a.bsum[(long long)(c + i) * 256 + d] = run;
+        run += w[i];
+      }
     }
   }
 }
@@ -270,15 +290,16 @@ struct DownSmem {
   uint32_t in_v[2][kSortPart];
   uint32_t key[kSortPart];            // staging in digit order
   uint32_t val[kSortPart];
-  uint32_t wh[kSortThreads / 32][256];
+  uint16_t wh[kDownThreads / 32][256];   // per-warp digit counts, then offsets
   uint32_t base[256], carry[256], dstart[256];
-  uint32_t wsum[kSortThreads / 32];
+  uint32_t wsum[8];                   // the 256 digit threads' warp sums
   uint64_t bar[2];
 };
 
-__global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int pass) {
+__global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int pass) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   DownSmem &sm = *reinterpret_cast<DownSmem *>(dyn_smem);
+  constexpr int NW = kDownThreads / 32;
   if (a.skip[pass]) return;
   const uint32_t n = sort_n(a);
   const int before = passes_before(a, pass);
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int p
   long long p0, p1;
   block_parts(n, a.blocks, blockIdx.x, p0, p1);
   if (p0 >= p1) return;
-  sm.carry[tid] = a.bsum[(long long)blockIdx.x * kSortSub * 256 + tid];   // 256 threads = digits
+  if (tid < 256) sm.carry[tid] = a.bsum[(long long)blockIdx.x * kSortSub * 256 + tid];
   const bool aligned = ((uintptr_t)kin & 15u) == 0 && (iota || ((uintptr_t)vin & 15u) == 0);
   const long long full = (long long)n / kSortPart;   // partitions [0, full) hold 4096 keys
   constexpr uint32_t kBytes = kSortPart * sizeof(uint32_t);
@@ -323,10 +344,11 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int p
     // the other half was last read before the barrier ending the previous
     // partition: refill it with the next partition
     if (part + 1 < p1 && aligned && part + 1 < full) issue(part + 1, h ^ 1);
-    for (int q = tid; q < (kSortThreads / 32) * 256; q += kSortThreads) (&sm.wh[0][0])[q] = 0u;
-    const long long wbase = part * kSortPart + warp * (32 * kSortItems);
-    const int lbase = warp * (32 * kSortItems);
-    uint32_t key[kSortItems], rank[kSortItems];
+    for (int q = tid; q < NW * 256 / 2; q += kDownThreads)
+      reinterpret_cast<uint32_t *>(&sm.wh[0][0])[q] = 0u;
+    const long long wbase = part * kSortPart + warp * (32 * kDownItems);
+    const int lbase = warp * (32 * kDownItems);
+    uint32_t key[kDownItems], rank[kDownItems];
     if (bulk) {
       const uint32_t u = h ? used1 : used0;
       const bool landed = mbar_wait_bounded(&sm.bar[h], u & 1u);
@@ -339,10 +361,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int p
         return;
       }
 #pragma unroll
-      for (int k = 0; k < kSortItems; ++k) key[k] = sm.in_k[h][lbase + k * 32 + lane];
+      for (int k = 0; k < kDownItems; ++k) key[k] = sm.in_k[h][lbase + k * 32 + lane];
     } else {
 #pragma unroll
-      for (int k = 0; k < kSortItems; ++k) {
+      for (int k = 0; k < kDownItems; ++k) {
         const long long idx = wbase + k * 32 + lane;
         key[k] = idx < (long long)n ? kin[idx] : 0u;
       }
@@ -351,7 +373,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int p
     // warp-level stable ranking (original order = (k, lane)); the lanes
     // holding the same digit are found with one ballot per digit bit
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
+    for (int k = 0; k < kDownItems; ++k) {
       long long idx = wbase + k * 32 + lane;
       bool valid = idx < (long long)n;
       uint32_t d = (key[k] >> shift) & dmask;
@@ -364,48 +386,50 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int p
           peers &= ((d >> bit) & 1u) ? bb : ~bb;
         }
       }
-      uint32_t before_w = valid ? sm.wh[warp][d] : 0u;
+      uint32_t before_w = valid ? (uint32_t)sm.wh[warp][d] : 0u;
       rank[k] = before_w + __popc(peers & ltmask);
       __syncwarp();
-      if (valid && (__ffs(peers) - 1) == lane) sm.wh[warp][d] = before_w + __popc(peers);
+      if (valid && (__ffs(peers) - 1) == lane) sm.wh[warp][d] = (uint16_t)(before_w + __popc(peers));
       __syncwarp();
     }
     __syncthreads();
-    // per digit: warp offsets inside the partition, the running base, and
-    // the digit's start inside the partition (block exclusive scan)
-    {
+    // per digit (threads 0..255): warp offsets inside the partition, the
+    // running base, and the digit's start inside the partition
+    uint32_t tot = 0, incl = 0;
+    if (tid < 256) {
       const int d = tid;
-      uint32_t tot = 0;
 #pragma unroll
-      for (int w = 0; w < kSortThreads / 32; ++w) {
-        uint32_t c = sm.wh[w][d];
-        sm.wh[w][d] = tot;
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = sm.wh[w][d];
+        sm.wh[w][d] = (uint16_t)tot;
         tot += c;
       }
       sm.base[d] = sm.carry[d];
       sm.carry[d] += tot;
-      uint32_t incl = tot;
+      incl = tot;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
       }
       if (lane == 31) sm.wsum[warp] = incl;
-      __syncthreads();
+    }
+    __syncthreads();
+    if (tid < 256) {
       uint32_t wofs = 0;
 #pragma unroll
-      for (int w = 0; w < kSortThreads / 32; ++w) wofs += w < warp ? sm.wsum[w] : 0u;
-      sm.dstart[d] = wofs + incl - tot;
+      for (int w = 0; w < 8; ++w) wofs += w < warp ? sm.wsum[w] : 0u;
+      sm.dstart[tid] = wofs + incl - tot;
     }
     __syncthreads();
     // stage the partition in digit order, then write runs of equal digits
     // to consecutive global addresses
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
+    for (int k = 0; k < kDownItems; ++k) {
       const long long idx = wbase + k * 32 + lane;
       if (idx < (long long)n) {
         uint32_t d = (key[k] >> shift) & dmask;
-        uint32_t lp = sm.dstart[d] + sm.wh[warp][d] + rank[k];
+        uint32_t lp = sm.dstart[d] + (uint32_t)sm.wh[warp][d] + rank[k];
         sm.key[lp] = key[k];
         sm.val[lp] = iota ? (uint32_t)idx : (bulk ? sm.in_v[h][lbase + k * 32 + lane] : vin[idx]);
       }
@@ -414,8 +438,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_downsweep(SortArgs a, int p
     const long long pbase = part * kSortPart;
     const uint32_t pcount = (uint32_t)min((long long)kSortPart, (long long)n - pbase);
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-      const uint32_t lp = (uint32_t)(k * kSortThreads + tid);
+    for (int k = 0; k < kDownItems; ++k) {
+      const uint32_t lp = (uint32_t)(k * kDownThreads + tid);
       if (lp < pcount) {
         const uint32_t kk = sm.key[lp];
         const uint32_t d = (kk >> shift) & dmask;
@@ -448,7 +472,7 @@ static void init_grids() {
   }
   if (g_sort_blocks) return;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_downsweep, kSortThreads, sizeof(DownSmem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_downsweep, kDownThreads, sizeof(DownSmem));
   if (sms < 1) sms = 1;
   if (per > kSortBlocksPerSm) per = kSortBlocksPerSm;
   g_sort_blocks = sms * (per > 0 ? per : 1);
@@ -464,7 +488,7 @@ static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = 
   for (int p = 0; p < a.passes; ++p) {
     k_upsweep<<<kSortSub * a.blocks, kSortThreads, 0, s>>>(a, p);
     k_scan_blocks<<<scan_blocks, kScanThreads, 0, s>>>(a, p);
-    k_downsweep<<<a.blocks, kSortThreads, sizeof(DownSmem), s>>>(a, p);
+    k_downsweep<<<a.blocks, kDownThreads, sizeof(DownSmem), s>>>(a, p);
   }
   return cudaGetLastError();
 }

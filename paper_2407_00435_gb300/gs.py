@@ -309,10 +309,8 @@ class Renderer:
         tile_bits = max(1, int(self.T_tiles - 1).bit_length())
         want = self.cfg.radix_bits or 8
         passes = min(4, (tile_bits + want - 1) // want)
-        # views, levels, project, pair count (+ warp-wide count with the tight support)
-        project = 1 + (1 if fov else 0) + (2 if self.n > 0 else 0)
-        if self.n > 0 and self.cfg.flags & GS_FLAG_TIGHT:
-            project += 1
+        # views, levels (+ level rows), project, pair count
+        project = 1 + (2 if fov else 0) + (2 if self.n > 0 else 0)
         # depth sort (hist, scan, 4 passes of upsweep + scan + downsweep),
         # offsets (upsweep, scan, downsweep), emit + large-item emit, pair
         # sort (scan + 3 kernels per pass), ranges
