@@ -313,7 +313,7 @@ def gpu_arm(args):
         torch.cuda.empty_cache()
         steps_x = max(3, min(args.steps, 10))
         for name, fn in (("foveated_stereo", extra_foveated), ("fwd_bwd", extra_fwd_bwd),
-                         ("batched_64_views", extra_batched)):
+                         ("prune_round", extra_prune), ("batched_64_views", extra_batched)):
             if args.only and name not in args.only:
                 continue
             try:
@@ -452,6 +452,64 @@ def extra_fwd_bwd(torch, gs, synth, flush, steps):
     return {"workload": wl.name, "views": V, "fwd_bwd_ms_batched": round(ms_b, 3),
             "fwd_bwd_ms_per_view_plans": round(ms_v, 3), "speedup": round(ms_v / ms_b, 3),
             "bwd_ms_per_view": round(ms_bwd / V, 4), "autograd_step_ms": round(ms_ag, 3)}
+
+
+def extra_prune(torch, gs, synth, flush, steps):
+    """One round of efficiency-aware pruning (Sec. 3.2-3.4) on the 1080p/1M
+    workload: statistics renders of 4 orbit poses + the bench pose, CE
+    maximum over them, mask of the lowest 10%, stable compaction; then the
+    frame rate and pair count of the pruned scene."""
+    import numpy as np
+    wl = synth.workload(1)
+    sc = gs.scene_to_device(wl.scene)
+    rng = np.random.default_rng(2024)
+    poses = np.concatenate([wl.cams, synth.orbit_cameras(rng, 4, 4.0, [(1920, 1080)] * 4)])
+    rs = [gs.Renderer(wl.scene.n, 3, poses[v:v + 1], tight=True) for v in range(len(poses))]
+    for r in rs:
+        r.fit(sc, headroom=1.05)
+    outs = [r.alloc_outputs(stats=True) for r in rs]
+    ce = torch.zeros(wl.scene.n, device="cuda")
+
+    def prune_round():
+        ce.zero_()
+        for r, o in zip(rs, outs):
+            r.project(sc)
+            r.bin_sort()
+            r.render(o)
+            gs.gs_ce_update(wl.scene.n, o["stats"], ce)
+        keep = rs[0].prune_mask(ce, 0.10)
+        return rs[0].compact(sc, keep)
+
+    pruned = prune_round()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    pruned = prune_round()
+    t1.record()
+    torch.cuda.synchronize()
+    round_ms = t0.elapsed_time(t1)
+    n_kept = int(pruned["means"].shape[0])
+    res = {"workload": wl.name, "poses": len(poses), "fraction": 0.10,
+           "points_before": wl.scene.n, "points_after": n_kept,
+           "round_ms_incl_stats_renders": round(round_ms, 3)}
+    for name, scene, n in (("before", sc, wl.scene.n), ("after", pruned, n_kept)):
+        r = gs.Renderer(n, 3, wl.cams, tight=True)
+        c = r.fit({k: v.contiguous() for k, v in scene.items()}, headroom=1.05)
+        out = r.alloc_outputs()
+
+        def frame():
+            r.project({k: v.contiguous() for k, v in scene.items()})
+            r.bin_sort()
+            r.render(out)
+
+        ms = _ms(torch, frame, steps, 2, flush)
+        res[f"fps_{name}"] = round(1000.0 / ms, 2)
+        res[f"pairs_{name}"] = int(c["n_pairs"])
+        del r, out
+    del rs, outs, sc, pruned
+    torch.cuda.empty_cache()
+    return res
 
 
 def extra_batched(torch, gs, synth, flush, steps):

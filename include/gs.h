@@ -287,6 +287,44 @@ gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_t *vals_in,
 int64_t gs_plan_tiles(const gs_plan *plan);
 int64_t gs_plan_pixels(const gs_plan *plan);
 
+/* ---- efficiency-aware pruning and scale decay (Sec. 3.2-3.4) ---------- */
+
+/* Computational efficiency of each point in one pose (Sec. 3.2, Eq. 2):
+ * CE_i = Val_i / Comp_i with Val_i = pixels dominated by the point and
+ * Comp_i = tiles whose list holds it (tiles_touched), both from the stats
+ * buffer (4,N) of a gs_render / gs_render_fov call on that pose.  Keeps the
+ * maximum over poses: ce_max[i] = max(ce_max[i], CE_i); points no tile
+ * holds leave ce_max[i] unchanged.  ce_max: device (N,) float, zeroed by the
+ * caller before the first pose.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_ce_update(int64_t n, const uint32_t *stats, float *ce_max, cudaStream_t stream);
+
+/* Intersection-aware pruning (Sec. 3.2; R = 10% per round in Sec. 3.4):
+ * keep[i] = 0 for the floor(fraction * n) points with the lowest ce_max
+ * (ties: lower index first), 1 for the others.  ce_max (device, n
+ * non-negative floats) is sorted with its indices in the plan's depth-sort
+ * buffers, so n must not exceed the plan's item slots (N x V); the last
+ * gs_bin_sort's depth order is overwritten (rendering needs a new
+ * gs_project / gs_bin_sort).  fraction in [0, 1].  keep: device (n,) bytes. */
+gs_status gs_prune_mask(gs_plan *plan, void *ws, int64_t n, const float *ce_max, double fraction,
+                        uint8_t *keep, cudaStream_t stream);
+
+/* Stable compaction of a scene by keep (device (n,) bytes): the kept points'
+ * parameters are copied, in order, from `in` to `out` (device arrays with
+ * room for n points, not overlapping `in`); *n_out (device uint64) receives
+ * the number kept.  Uses the plan's workspace as scratch (any plan). */
+gs_status gs_compact_points(gs_plan *plan, void *ws, int64_t n, int32_t sh_degree,
+                            const uint8_t *keep, const gs_scene *in, gs_scene *out,
+                            uint64_t *n_out, cudaStream_t stream);
+
+/* Weighted scale (Sec. 3.3, Eq. 3-4): WS = (1/N) sum_i S_i G_i with S_i the
+ * largest of point i's three (activated) scales and G_i = (U_i > T)(U_i - T),
+ * U_i = tiles where the point was blended (tiles_used, stats row 1).  Writes
+ * WS to *ws_out (device double) and, if d_scales is given, adds
+ * gamma dWS/ds (gamma G_i / N on the first largest axis) to it, the scale
+ * decay term of the loss L = L_quality + gamma WS (Eq. 5). */
+gs_status gs_weighted_scale(int64_t n, const float *scales, const uint32_t *stats, float T,
+                            float gamma, double *ws_out, float *d_scales, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

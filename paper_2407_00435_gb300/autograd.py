@@ -79,3 +79,29 @@ def render(scene: dict, renderer: Renderer, fov: dict | None = None, bg=(0.0, 0.
 
 def l1_loss(rgb: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
     return (rgb - target).abs().mean()
+
+
+class _WeightedScaleFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, scales, stats, T: float, gamma: float):
+        from .gs import gs_weighted_scale
+        s = scales.detach().contiguous()
+        n = s.shape[0]
+        ws = torch.zeros(1, dtype=torch.float64, device=s.device)
+        grad = torch.zeros_like(s)
+        gs_weighted_scale(n, s, stats, T, gamma, ws, grad)
+        ctx.save_for_backward(grad)
+        return (gamma * ws).to(scales.dtype).reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g, None, None, None
+
+
+def scale_decay(scales: torch.Tensor, stats: torch.Tensor, T: float, gamma: float) -> torch.Tensor:
+    """gamma * WS (Sec. 3.3, Eq. 3-5): the scale-decay term of the training
+    loss L = L_quality + gamma WS, from the (N, 3) activated scales and the
+    (4, N) statistics of the current render (U = tiles_used, treated as a
+    constant of the iterate)."""
+    return _WeightedScaleFn.apply(scales, stats, float(T), float(gamma))

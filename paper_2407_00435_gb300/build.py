@@ -28,6 +28,7 @@ UNITS = {
     "k_sort.cu": [],
     "k_render.cu": [],
     "k_backward.cu": [],
+    "k_prune.cu": [],
 }
 
 

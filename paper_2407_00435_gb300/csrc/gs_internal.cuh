@@ -86,6 +86,8 @@ struct Hdr {
   unsigned long long queue;       // next work item of the chunked render
   uint32_t n_slots;               // chunk slots requested by the chunk plan
   uint32_t pad1;
+  unsigned long long aux_n;       // key count of a sort outside the frame (pruning)
+  unsigned long long aux_out;     // result count of such a pass (compaction)
 };
 
 // Per-view constants, computed on the device from the cameras.
@@ -158,6 +160,10 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s);
 cudaError_t launch_render(const gs_plan *p, void *ws, bool fov, const float bg[3],
                           float *rgb, float *T, int32_t *last, uint32_t *stats,
                           cudaStream_t s);
+// Stable sort of n uint32 keys with their indices in the plan's depth-sort
+// buffers (n <= max_visible); the sorted indices end in R_DVAL_A.
+cudaError_t launch_sort_indices(const gs_plan *p, void *ws, const uint32_t *keys, long long n,
+                                cudaStream_t s);
 cudaError_t launch_backward(const gs_plan *p, void *ws, const float *dL, const float *T,
                             const int32_t *last, const float bg[3], float *d_means,
                             float *d_scales, float *d_quats, float *d_opac, float *d_sh,

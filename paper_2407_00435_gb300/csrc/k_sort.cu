@@ -1015,6 +1015,37 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---- sort of caller keys with their indices (pruning by CE) --------------
+__global__ void k_set_aux_n(Hdr *h, unsigned long long n) { h->aux_n = n; }
+
+cudaError_t launch_sort_indices(const gs_plan *p, void *ws, const uint32_t *keys, long long n,
+                                cudaStream_t s) {
+  Hdr *hdr = region<Hdr>(p, ws, R_HDR);
+  init_grids();
+  cudaError_t e = cudaMemsetAsync(&hdr->hist[0][0][0], 0, sizeof(hdr->hist[0]), s);
+  if (e != cudaSuccess) return e;
+  k_set_aux_n<<<1, 1, 0, s>>>(hdr, (unsigned long long)n);
+  SortArgs d = {};
+  d.first_keys = keys;
+  d.first_vals = nullptr;                 // values = key index
+  d.keys[0] = region<uint32_t>(p, ws, R_DKEY_A);
+  d.keys[1] = region<uint32_t>(p, ws, R_DKEY_B);
+  d.vals[0] = region<uint32_t>(p, ws, R_DVAL_A);
+  d.vals[1] = region<uint32_t>(p, ws, R_DVAL_B);
+  d.count = &hdr->aux_n;
+  d.capacity = p->max_visible;
+  d.sel = &hdr->sel_depth;
+  d.hist = &hdr->hist[0][0][0];
+  d.skip = &hdr->skip[0];
+  d.bsum = region<uint32_t>(p, ws, R_BSUM);
+  d.blocks = g_sort_blocks < p->sort_blocks ? g_sort_blocks : p->sort_blocks;
+  d.passes = 4;
+  d.digit_bits = 8;
+  d.no_skip = 1;                          // four passes: the result ends in buffer 0
+  d.status = &hdr->status;
+  return run_sort(d, s);
+}
+
 // --------------------------------------------------------------------------
 // Allocation-free variant of the pair sort (no counterpart in the paper).
 //

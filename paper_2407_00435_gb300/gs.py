@@ -105,6 +105,14 @@ def _load():
     lib.gs_plan_tiles.restype = C.c_int64
     lib.gs_plan_pixels.argtypes = [p]
     lib.gs_plan_pixels.restype = C.c_int64
+    lib.gs_ce_update.argtypes = [C.c_int64, p, p, p]
+    lib.gs_ce_update.restype = s
+    lib.gs_prune_mask.argtypes = [p, p, C.c_int64, p, C.c_double, p, p]
+    lib.gs_prune_mask.restype = s
+    lib.gs_compact_points.argtypes = [p, p, C.c_int64, s, p, p, p, p, p]
+    lib.gs_compact_points.restype = s
+    lib.gs_weighted_scale.argtypes = [C.c_int64, p, p, C.c_float, C.c_float, p, p, p]
+    lib.gs_weighted_scale.restype = s
     return lib
 
 
@@ -195,6 +203,27 @@ def gs_render_backward(plan_buf, ws, dL, T, last, bg, d_means, d_scales, d_quats
            "gs_render_backward")
 
 
+def gs_ce_update(n, stats, ce_max, stream=None):
+    _check(_lib.gs_ce_update(n, _ptr(stats), _ptr(ce_max), _stream(stream)), "gs_ce_update")
+
+
+def gs_prune_mask(plan_buf, ws, n, ce_max, fraction, keep, stream=None):
+    _check(_lib.gs_prune_mask(plan_buf, _ptr(ws), n, _ptr(ce_max), float(fraction), _ptr(keep),
+                              _stream(stream)), "gs_prune_mask")
+
+
+def gs_compact_points(plan_buf, ws, n, sh_degree, keep, scene_in, scene_out, n_out, stream=None):
+    _check(_lib.gs_compact_points(plan_buf, _ptr(ws), n, sh_degree, _ptr(keep), C.byref(scene_in),
+                                  C.byref(scene_out), _ptr(n_out), _stream(stream)),
+           "gs_compact_points")
+
+
+def gs_weighted_scale(n, scales, stats, T, gamma, ws_out, d_scales=None, stream=None):
+    _check(_lib.gs_weighted_scale(n, _ptr(scales), _ptr(stats), float(T), float(gamma),
+                                  _ptr(ws_out), _ptr(d_scales), _stream(stream)),
+           "gs_weighted_scale")
+
+
 def gs_get_error(plan_buf, ws, stream=None):
     c = gs_counters()
     code = _lib.gs_get_error(plan_buf, _ptr(ws), _stream(stream), C.byref(c))
@@ -261,6 +290,28 @@ class Renderer:
 
     def bin_sort(self, stream=None):
         gs_bin_sort(self.plan, self.ws, stream)
+
+    # -- efficiency-aware pruning (Sec. 3.2-3.4) -----------------------------
+    def _scene(self, sc: dict, n=None):
+        return gs_scene(self.n if n is None else n, self.sh_degree, 0, sc["means"].data_ptr(),
+                        sc["scales"].data_ptr(), sc["quats"].data_ptr(), sc["opac"].data_ptr(),
+                        sc["sh"].data_ptr())
+
+    def prune_mask(self, ce_max, fraction, stream=None):
+        """uint8 keep mask: 0 for the floor(fraction * N) lowest-CE points.
+        Overwrites the plan's depth order (project again before rendering)."""
+        keep = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        gs_prune_mask(self.plan, self.ws, self.n, ce_max, fraction, keep, stream)
+        return keep
+
+    def compact(self, sc: dict, keep, stream=None) -> dict:
+        """The scene's kept points, in order (device tensors)."""
+        out = {k: torch.empty_like(v) for k, v in sc.items()}
+        n_out = torch.zeros(1, dtype=torch.int64, device=self.device)
+        gs_compact_points(self.plan, self.ws, self.n, self.sh_degree, keep, self._scene(sc),
+                          self._scene(out), n_out, stream)
+        k = int(n_out.item())
+        return {kk: v[:k] for kk, v in out.items()}
 
     def _replan(self, max_pairs):
         self.cfg.max_pairs = int(max_pairs)
