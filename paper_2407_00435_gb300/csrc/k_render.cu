@@ -132,6 +132,52 @@ struct Pix {
   int lvl[PX];        // foveation level
 };
 
+// Plain views: composites the warp's ordered list of batch slots into the
+// thread's PX pixels.  The per-pixel decisions are written as data flow (the
+// compiler predicates them instead of branching), every lane takes the
+// warp's trip count, and the warp leaves once none of its pixels is live,
+// checked every 4 entries.  Decisions and arithmetic are those of the
+// generic loop in walk().
+template <int PX>
+__device__ __forceinline__ void composite_plain(const uint16_t *list, int nlist,
+                                                const float4 *ra, const float4 *rb,
+                                                const float4 *rc, int base, const Pix<PX> &pp,
+                                                Acc (&A)[PX], uint32_t (&walk_end)[PX]) {
+  // pixel centres packed twice: the paired FMA operands of eval_s2
+  const unsigned long long px2 = f2_pack(pp.px, pp.px);
+  unsigned long long py2[PX];
+#pragma unroll
+  for (int k = 0; k < PX; ++k) py2[k] = f2_pack(pp.py[k], pp.py[k]);
+  for (int li = 0; li < nlist; ++li) {
+    const int q = list[li];
+    const float4 sa = ra[q], sb = rb[q], c = rc[q];
+    const int pos = base + q;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+      float t1, t2;
+      const float sq = eval_s2(px2, py2[k], sa, sb, t1, t2);
+      const float al = alpha_of(__fsub_rn(c.w, sq));
+      const float Tn = A[k].T * (1.0f - al);
+      const bool hit = !A[k].done && sq <= sb.z;
+      if (hit && !(Tn < kTMin)) {
+        const float w = al * A[k].T;
+        A[k].r = fmaf(w, c.x, A[k].r);
+        A[k].g = fmaf(w, c.y, A[k].g);
+        A[k].b = fmaf(w, c.z, A[k].b);
+        A[k].T = Tn;
+        A[k].last = pos;
+      }
+      if (hit && Tn < kTMin) {
+        A[k].done = true;
+        walk_end[k] = pos + 1;
+      }
+      live = live || !A[k].done;
+    }
+    if ((li & 3) == 3 && !__any_sync(0xffffffffu, live)) break;
+  }
+}
+
 // Composites the sorted points [begin, end) of a tile front to back into
 // every accumulator that is not done.  List positions (`last`) are reported
 // relative to `origin`, the first pair of the tile.  Starts and ends with a
@@ -245,8 +291,16 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
       const uint32_t k = b + NB + tid + u * NT;
       prefetch<FOV>(a, vals, k, k < end, pre[u]);
     }
-    if (!all_done_here()) {
+    if (!FOV && !STATS) {
+      if (__any_sync(0xffffffffu, !all_done_here()))
+        composite_plain<PX>(sm.list[warp], sm.woff[warp][SPT * NWS], sm.a, sm.b, sm.c,
+                            (int)(b - origin), pp, A, walk_end);
+    } else if (!all_done_here()) {
       const int nlist = sm.woff[warp][SPT * NWS];
+      const unsigned long long px2 = f2_pack(pp.px, pp.px);
+      unsigned long long py2[PX];
+#pragma unroll
+      for (int k = 0; k < PX; ++k) py2[k] = f2_pack(pp.py[k], pp.py[k]);
       for (int li = 0; li < nlist; ++li) {
         const uint32_t q = sm.list[warp][li];
         const float4 sb = sm.b[q];
@@ -255,7 +309,7 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
           float t1, t2;
-          const float sq = eval_s(pp.px, pp.py[k], sa, sb, t1, t2);
+          const float sq = eval_s2(px2, py2[k], sa, sb, t1, t2);
           // accumulator A: the pixel's own level
           if (!A[k].done && (!FOV || m >= pp.lvl[k])) {
             const bool own = MV && pp.lvl[k] >= 2;

@@ -211,22 +211,25 @@ __global__ void __launch_bounds__(kSortThreads) k_upsweep(SortArgs a, int pass) 
 }
 
 // ---- scan: bsum[s][d] <- global start of digit d + its count in
-// sub-ranges < s.  One block per 32 digits; warp w owns a run of rows.  Up
-// to kScanRegRows rows per warp stay in registers between the two phases
-// (one read of the table); longer runs are read twice, kScanChunk at a time.
+// sub-ranges < s.  One block per 8 digits (one 32-byte sector of a table
+// row); thread (slice, digit) owns a run of rows of its digit, so each load
+// instruction of a warp reads whole sectors of 4 rows.  Up to kScanRegRows
+// rows per thread stay in registers between the two phases (one read of the
+// table); longer runs are read twice, kScanChunk at a time.
 constexpr int kScanThreads = 1024;
+constexpr int kScanDigits = 8;
+constexpr int kScanSlices = kScanThreads / kScanDigits;
 constexpr int kScanChunk = 16;
-constexpr int kScanRegRows = 48;
+constexpr int kScanRegRows = 32;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pass) {
-  __shared__ uint32_t s_p[kScanThreads / 32][32];
+  __shared__ uint32_t s_p[kScanDigits][kScanSlices + 1];
   if (a.skip[pass]) return;
-  constexpr int NW = kScanThreads / 32;
   const int R = kSortSub * a.blocks;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int d = blockIdx.x * 32 + lane;
-  const int rows = (R + NW - 1) / NW;
-  const int r0 = warp * rows;
+  const int dl = threadIdx.x & (kScanDigits - 1), sl = threadIdx.x / kScanDigits;
+  const int d = blockIdx.x * kScanDigits + dl;
+  const int rows = (R + kScanSlices - 1) / kScanSlices;
+  const int r0 = sl * rows < R ? sl * rows : R;
   const int r1 = r0 + rows < R ? r0 + rows : R;
   const bool in_regs = rows <= kScanRegRows;
   uint32_t v[kScanRegRows];
@@ -246,18 +249,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pa
       for (int i = 0; i < kScanChunk; ++i) sum += w[i];
     }
   }
-  s_p[warp][lane] = sum;
+  s_p[dl][sl] = sum;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t run = a.hist[pass * 256 + d];
-    for (int w = 0; w < NW; ++w) {
-      const uint32_t c = s_p[w][lane];
-      s_p[w][lane] = run;
-      run += c;
+  // warp w < 8: exclusive scan of digit w's slice sums (4 slices per lane)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  static_assert(kScanSlices == 4 * 32, "4 slices per lane");
+  if (warp < kScanDigits) {
+    uint32_t x[4], loc = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[i] = s_p[warp][4 * lane + i];
+      loc += x[i];
+    }
+    uint32_t incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t run = a.hist[pass * 256 + blockIdx.x * kScanDigits + warp] + incl - loc;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      s_p[warp][4 * lane + i] = run;
+      run += x[i];
     }
   }
   __syncthreads();
-  uint32_t run = s_p[warp][lane];
+  uint32_t run = s_p[dl][sl];
   if (in_regs) {
 #pragma unroll
     for (int i = 0; i < kScanRegRows; ++i) {
@@ -484,7 +502,8 @@ static void init_grids() {
 static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = false) {
   if (!hist_done) k_hist<<<a.blocks, 256, 0, s>>>(a);
   k_hist_scan<<<1, 256, 0, s>>>(a);
-  const unsigned scan_blocks = (1u << a.digit_bits) > 32 ? (1u << a.digit_bits) / 32 : 1u;
+  const unsigned scan_blocks =
+      (1u << a.digit_bits) > kScanDigits ? (1u << a.digit_bits) / kScanDigits : 1u;
   for (int p = 0; p < a.passes; ++p) {
     k_upsweep<<<kSortSub * a.blocks, kSortThreads, 0, s>>>(a, p);
     k_scan_blocks<<<scan_blocks, kScanThreads, 0, s>>>(a, p);

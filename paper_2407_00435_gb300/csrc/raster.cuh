@@ -129,24 +129,53 @@ __device__ __forceinline__ uint32_t warp_mask_exact(float mx, float my, float4 s
   return mask;
 }
 
+// A pair of FP32 values in one 64-bit register pair, and the paired FP32
+// fused multiply-add of sm_100-family GPUs on it: two correctly rounded
+// fmaf results for one issued instruction.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Evaluation record of one point in a tile: whitened offsets t = W p + c
-// (p the tile-local pixel centre), so t = W (p - mu) with c = -W mu.
-//   a = (w1x, w1y, c1, w2x), b = (w2y, c2, F - floor, warp mask bits)
+// (p the tile-local pixel centre), so t = W (p - mu) with c = -W mu.  The
+// two rows of W are interleaved so that (t1, t2) is one paired FMA chain:
+//   a = (w1x, w2x, w1y, w2y), b = (c1, c2, F - floor, warp mask bits)
 __device__ __forceinline__ void make_eval(float mx, float my, float4 sh, float F, uint32_t mask,
                                           float4 &a, float4 &b) {
   const float c1 = -__fmaf_rn(sh.x, mx, __fmul_rn(sh.y, my));
   const float c2 = -__fmaf_rn(sh.z, mx, __fmul_rn(sh.w, my));
-  a = make_float4(sh.x, sh.y, c1, sh.z);
-  b = make_float4(sh.w, c2, __fsub_rn(F, kLog2AlphaMin), __uint_as_float(mask));
+  a = make_float4(sh.x, sh.z, sh.y, sh.w);
+  b = make_float4(c1, c2, __fsub_rn(F, kLog2AlphaMin), __uint_as_float(mask));
 }
 
-// |t|^2 at pixel (px, py); the point can blend iff s <= F - floor, and then
-// alpha = min(0.99, 2^(F - s)).
+// |t|^2 at the pixel whose centre coordinates are packed twice in px2 =
+// (px, px) and py2 = (py, py):
+//   t1 = fma(w1x, px, fma(w1y, py, c1)),  t2 = fma(w2x, px, fma(w2y, py, c2)),
+//   s = fma(t1, t1, t2 * t2).
+// The point can blend iff s <= F - floor, and then alpha = min(0.99, 2^(F - s)).
+__device__ __forceinline__ float eval_s2(unsigned long long px2, unsigned long long py2,
+                                         float4 a, float4 b, float &t1, float &t2) {
+  const unsigned long long in = f2_fma(f2_pack(a.z, a.w), py2, f2_pack(b.x, b.y));
+  f2_unpack(f2_fma(f2_pack(a.x, a.y), px2, in), t1, t2);
+  return __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
+}
+
 __device__ __forceinline__ float eval_s(float px, float py, float4 a, float4 b, float &t1,
                                         float &t2) {
-  t1 = __fmaf_rn(a.x, px, __fmaf_rn(a.y, py, a.z));
-  t2 = __fmaf_rn(a.w, px, __fmaf_rn(b.x, py, b.y));
-  return __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
+  return eval_s2(f2_pack(px, px), f2_pack(py, py), a, b, t1, t2);
 }
 
 }  // namespace gs
