@@ -101,6 +101,32 @@ def test_ragged_multiview_uneven_sizes(gs, orc):
     compare_images(out["rgb"].cpu().numpy(), img)
 
 
+@pytest.mark.parametrize("layout", ["wide", "ties"])
+def test_depth_order_wide_range_and_ties(gs, orc, layout):
+    """The depth sort ranks keys relative to the range of visible depths:
+    a range wide enough that no digit is constant (depths 0.6 to 400), and a
+    narrow one with many equal keys (two depth planes), whose ties must stay
+    in point order.  Points behind the camera make invisible slots."""
+    rng = np.random.default_rng(4242)
+    n = 3000
+    sc = synth.uniform_scene(rng, n, degree=1, log_scale=(-3.0, 0.5), dc_mode="coef")
+    if layout == "wide":
+        z = np.exp(rng.uniform(np.log(0.6), np.log(400.0), n)) - 4.0
+    else:
+        z = np.where(rng.random(n) < 0.5, 0.0, 0.5)
+    z[rng.random(n) < 0.1] = -6.0          # behind the camera at z = -4
+    sc.means[:, 2] = z.astype(np.float32)
+    sc.means[:, :2] *= (0.5 * (z + 4.0)).clip(0.2, None)[:, None].astype(np.float32)
+    cams = synth.camera_lookat((0, 0, -4), (0, 0, 0), 96, 80)[None]
+    wl = synth.Workload("depth_" + layout, sc, cams, 16)
+    r, out, _, _ = run_gpu(gs, wl)
+    ob, img, _ = oracle_image(orc, wl)
+    gb = gpu_bins(gs, r)
+    assert 0 < gb["M"] < n
+    check_bins_exact(gb, ob, n)
+    compare_images(out["rgb"].cpu().numpy(), img)
+
+
 def test_tile8(gs, orc):
     wl = synth.workload(0, n=4000)
     wl.tile = 8
