@@ -52,7 +52,7 @@ class _Fov(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("bound_m", C.c_void_p),
                 ("ring_tan", C.c_void_p), ("band_px", C.c_float),
                 ("gaze", C.c_void_p), ("view_fov", C.c_void_p),
-                ("opacity_lv", C.c_void_p), ("dc_lv", C.c_void_p)]
+                ("opacity_lv", C.c_void_p), ("dc_lv", C.c_void_p), ("disjoint", C.c_int32)]
 
 
 _lib = None
@@ -125,6 +125,7 @@ class FovArrays:
     view_fov: np.ndarray | None = None
     opacity_lv: np.ndarray | None = None
     dc_lv: np.ndarray | None = None
+    disjoint: bool = False   # a separate model per level (bound_m = model level)
 
     @staticmethod
     def from_synth(f, opacity_lv=None, dc_lv=None):
@@ -138,7 +139,8 @@ class FovArrays:
             np.ascontiguousarray(f.gaze, np.float32),
             None if f.view_fov is None else np.ascontiguousarray(f.view_fov, np.uint8),
             None if op is None else np.ascontiguousarray(op, np.float64),
-            None if dc is None else np.ascontiguousarray(dc, np.float64))
+            None if dc is None else np.ascontiguousarray(dc, np.float64),
+            bool(getattr(f, "disjoint", False)))
 
     def struct(self):
         s = _Fov()
@@ -150,6 +152,7 @@ class FovArrays:
         s.view_fov = _ptr(self.view_fov)
         s.opacity_lv = _ptr(self.opacity_lv)
         s.dc_lv = _ptr(self.dc_lv)
+        s.disjoint = 1 if self.disjoint else 0
         return s
 
 

@@ -395,7 +395,9 @@ static int kept(const uint8_t *tile_level, const uint8_t *bound_m, int64_t gt,
                 int i) {
   if (!tile_level || !bound_m) return 1;
   /* Sec. 4.2 filtering: the point takes part in a tile of level t only if
-   * t <= m (its quality bound). */
+   * t <= m (its quality bound).  With a separate model per level the same
+   * rule is conservative: a pixel of level l uses the model of level l (and
+   * l - 1 inside a band), never below the tile's level t. */
   return tile_level[gt] <= bound_m[i];
 }
 
@@ -756,9 +758,17 @@ static double rel_margin(double a, double thr) {
  * twice the largest colour, which the tests use as the bound. */
 #define AMB_REL 1e-3
 
+/* Whether point i takes part at level lvl (see orc_fov.disjoint).  Without
+ * foveation every point takes part. */
+static int takes_part(const orc_fov *fov, int i, int lvl) {
+  if (!fov || !fov->bound_m) return 1;
+  if (fov->disjoint) return fov->bound_m[i] == lvl;
+  return lvl <= 1 || fov->bound_m[i] >= lvl;
+}
+
 /* Composite one accumulator of one pixel over list positions [s, e).
- * `px`, `py` are the pixel centre.  Only points with m >= lvl take part
- * (lvl = 1 with no foveation: all points). */
+ * `px`, `py` are the pixel centre.  Only the points that take part at level
+ * lvl are composited (takes_part). */
 static void composite(int n, const double *vp, const double *opac,
                       const uint32_t *vals, int64_t s, int64_t e,
                       const orc_fov *fov, int lvl, double px, double py,
@@ -773,7 +783,7 @@ static void composite(int n, const double *vp, const double *opac,
   for (int64_t k = s; k < e; ++k) {
     uint32_t id = vals[k];
     int i = (int)(id % (uint32_t)n);
-    if (fov && fov->bound_m && lvl > 1 && fov->bound_m[i] < lvl) continue;
+    if (!takes_part(fov, i, lvl)) continue;
     const double *pv = &vp[(int64_t)id * ORC_NVAL];
     double dx = px - pv[ORC_U], dy = py - pv[ORC_V];
     double power = -0.5 * (pv[ORC_CA] * dx * dx + pv[ORC_CC] * dy * dy) - pv[ORC_CB] * dx * dy;
@@ -908,7 +918,7 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
               for (int64_t k = s; k <= s + A.last; ++k) {
                 uint32_t id = vals[k];
                 int i = (int)(id % (uint32_t)n);
-                if (fov && fov->bound_m && fp.level > 1 && fov->bound_m[i] < fp.level) continue;
+                if (!takes_part(fov, i, fp.level)) continue;
                 const double *pv = &vp[(int64_t)id * ORC_NVAL];
                 double dx = px - pv[ORC_U], dy = py - pv[ORC_V];
                 double power = -0.5 * (pv[ORC_CA] * dx * dx + pv[ORC_CC] * dy * dy) - pv[ORC_CB] * dx * dy;
@@ -1019,7 +1029,7 @@ static void backward_acc(int n, const double *vp, const double *opac,
   for (int64_t k = s; k < e; ++k) {
     uint32_t id = vals[k];
     int i = (int)(id % (uint32_t)n);
-    if (fov && fov->bound_m && lvl > 1 && fov->bound_m[i] < lvl) continue;
+    if (!takes_part(fov, i, lvl)) continue;
     const double *pv = &vp[(int64_t)id * ORC_NVAL];
     double dx = px - pv[ORC_U], dy = py - pv[ORC_V];
     double power = -0.5 * (pv[ORC_CA] * dx * dx + pv[ORC_CC] * dy * dy) - pv[ORC_CB] * dx * dy;

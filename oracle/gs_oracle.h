@@ -58,6 +58,10 @@ typedef struct {
   const uint8_t *view_fov;   /* (V,) 1 = foveated, 0 = plain; NULL = all foveated */
   const double *opacity_lv;  /* (L-1,N) opacity of levels 2..L, or NULL */
   const double *dc_lv;       /* (L-1,N,3) SH DC of levels 2..L, or NULL */
+  int32_t disjoint;          /* 0: nested subsets, level l uses the points with m >= l
+                                (Sec. 4.2); 1: a separate model per level (Sec. 4.1),
+                                bound_m = the level of the model a point belongs to and
+                                level l uses exactly the points with m == l */
 } orc_fov;
 
 /* Per-item (view, point) FP64 value record produced by orc_project_values. */

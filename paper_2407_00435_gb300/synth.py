@@ -61,6 +61,7 @@ class Foveation:
     view_fov: np.ndarray | None = None   # (V,) uint8, 1 = foveated view, 0 = plain
     opacity_lv: np.ndarray | None = None  # (L-1, N) float32, levels 2..L
     dc_lv: np.ndarray | None = None       # (L-1, N, 3) float32, levels 2..L
+    disjoint: bool = False        # bound_m is each point's model level (one model per level)
 
 
 @dataclass
@@ -247,6 +248,51 @@ def multiversion_params(rng, scene: Scene, n_levels):
                  1e-3, 0.999).astype(np.float32)
     dc = (scene.sh[None, :, 0, :] + rng.normal(0, 0.1, (n_levels - 1, n, 3))).astype(np.float32)
     return op, dc
+
+
+def multi_model_scene(rng, scene: Scene, bound_m, n_levels):
+    """Separate per-level models for the multi-model foveated render
+    (Sec. 4.1, main pipeline; the paper's multi-model baseline prunes each
+    level's model from the level-1 model on its own).  Level 1 is `scene`;
+    level l >= 2 is a copy of the points of the nested level-l subset
+    (bound_m >= l) with parameters of its own: opacity and SH DC perturbed as
+    in multiversion_params, scales by a log-normal factor.  Returns the
+    concatenated scene and the uint8 model level of every point."""
+    parts = [(np.arange(scene.n), 1)]
+    for lvl in range(2, n_levels + 1):
+        parts.append((np.nonzero(np.asarray(bound_m) >= lvl)[0], lvl))
+    means, scales, quats, opac, sh, level = [], [], [], [], [], []
+    for idx, lvl in parts:
+        k = len(idx)
+        means.append(scene.means[idx])
+        quats.append(scene.quats[idx])
+        if lvl == 1:
+            scales.append(scene.scales[idx])
+            opac.append(scene.opac[idx])
+            sh.append(scene.sh[idx])
+        else:
+            scales.append((scene.scales[idx] * np.exp(rng.normal(0.0, 0.1, (k, 1)))).astype(np.float32))
+            opac.append(np.clip(scene.opac[idx] * rng.uniform(0.7, 1.0, k), 1e-3, 0.999).astype(np.float32))
+            shl = scene.sh[idx].copy()
+            shl[:, 0, :] += rng.normal(0, 0.1, (k, 3)).astype(np.float32)
+            sh.append(shl)
+        level.append(np.full(k, lvl, np.uint8))
+    sc = Scene(np.concatenate(means), np.concatenate(scales), np.concatenate(quats),
+               np.concatenate(opac), np.concatenate(sh), scene.sh_degree)
+    return sc, np.concatenate(level)
+
+
+def multi_model_workload(n=None, views=None) -> Workload:
+    """The foveated stereo workload with a separate model per level: the
+    level-l model is its own copy of the nested level-l subset (N, N/2, N/4,
+    N/8 points, 1.875 N in all), same rings, band and gaze."""
+    wl = workload(2, n=n, views=views)
+    rng = np.random.default_rng(config_seed(2) + 100)
+    sc, lv = multi_model_scene(rng, wl.scene, wl.fov.bound_m, wl.fov.n_levels)
+    f = wl.fov
+    fov = Foveation(f.n_levels, lv, f.ring_tan, f.band_px, f.gaze, f.view_fov, disjoint=True)
+    name = wl.name.replace("fov_stereo", "mmfr_stereo")
+    return Workload(name, sc, wl.cams, wl.tile, fov)
 
 
 # --------------------------------------------------------------------------
