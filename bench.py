@@ -312,7 +312,8 @@ def gpu_arm(args):
         del rr, outr, sc
         torch.cuda.empty_cache()
         steps_x = max(3, min(args.steps, 10))
-        for name, fn in (("foveated_stereo", extra_foveated), ("fwd_bwd", extra_fwd_bwd),
+        for name, fn in (("foveated_stereo", extra_foveated), ("multi_model_fr", extra_mmfr),
+                         ("fwd_bwd", extra_fwd_bwd),
                          ("prune_round", extra_prune), ("batched_64_views", extra_batched)):
             if args.only and name not in args.only:
                 continue
@@ -390,6 +391,48 @@ def extra_foveated(torch, gs, synth, flush, steps):
             "pairs_foveated": int(cf["n_pairs"]), "pairs_plain": int(cp["n_pairs"]),
             "blends_per_s_foveated": round(int(cntf["n_blends"]) * 1000 / ms_f, 1),
             "frame": "2 eyes"}
+
+
+def extra_mmfr(torch, gs, synth, flush, steps):
+    """The foveated stereo frame with a separate model per level (the
+    multi-model pipeline of Sec. 4.1; level-l model = its own copy of the
+    nested level-l subset, 1.875 x 3M points) against the nested-subset
+    representation of the same levels."""
+    wl = synth.multi_model_workload()
+    sc = gs.scene_to_device(wl.scene)
+    f = gs.fov_to_device(wl.fov)
+    r = gs.Renderer(wl.scene.n, 3, wl.cams, multi_model=True, tight=True)
+    c = r.fit(sc, f)
+    out = r.alloc_outputs(fov=True)
+
+    def step():
+        r.project(sc, f)
+        r.bin_sort()
+        r.render(out, fov=True)
+
+    ms = _ms(torch, step, steps, 2, flush)
+    res = {"workload": wl.name, "points": wl.scene.n, "fps_multi_model": round(1000 / ms, 2),
+           "pairs_multi_model": int(c["n_pairs"])}
+    del r, out, sc, f
+    torch.cuda.empty_cache()
+    wn = synth.workload(2)
+    sc = gs.scene_to_device(wn.scene)
+    f = gs.fov_to_device(wn.fov)
+    r = gs.Renderer(wn.scene.n, 3, wn.cams, foveated=True, tight=True)
+    c = r.fit(sc, f)
+    out = r.alloc_outputs(fov=True)
+
+    def step_n():
+        r.project(sc, f)
+        r.bin_sort()
+        r.render(out, fov=True)
+
+    ms_n = _ms(torch, step_n, steps, 2, flush)
+    res.update({"fps_nested": round(1000 / ms_n, 2), "pairs_nested": int(c["n_pairs"]),
+                "nested_speedup": round(ms / ms_n, 3), "frame": "2 eyes"})
+    del r, out, sc, f
+    torch.cuda.empty_cache()
+    return res
 
 
 def extra_fwd_bwd(torch, gs, synth, flush, steps):

@@ -133,6 +133,15 @@ typedef struct gs_config {
                                 bound of 2 ln(255 o) on the Mahalanobis distance, o the
                                 largest opacity of any level).  Same image, shorter tile
                                 lists.  Rectangles of more than 256 tiles keep all tiles. */
+#define GS_FLAG_MULTI_MODEL 8u  /* foveated render with a separate model per quality level
+                                (Sec. 4.1, main pipeline): the scene is the concatenation of
+                                the levels' models and gs_fov.bound_m holds the level of the
+                                model each point belongs to.  A pixel of level l composites
+                                only the points of model l (and, inside a blend band, those
+                                of model l - 1 into its second accumulator).  Requires
+                                GS_FLAG_FOVEATED, a gs_fov in every gs_project and
+                                gs_render_fov; per-level parameters (opacity_lv, dc_lv) are
+                                rejected (every model carries its own). */
 
 /* Counters read back by gs_get_error. */
 typedef struct gs_counters {

@@ -51,7 +51,10 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   p->chunk = c.chunk > 0 ? c.chunk : 0;
   if (c.radix_bits != 0 && (c.radix_bits < 4 || c.radix_bits > 8)) return GS_ERR_INVALID_ARG;
   p->radix_bits = c.radix_bits;
-  if ((uint32_t)c.flags & ~(GS_FLAG_FOVEATED | GS_FLAG_BACKWARD | GS_FLAG_TIGHT))
+  if (((uint32_t)c.flags & GS_FLAG_MULTI_MODEL) && !((uint32_t)c.flags & GS_FLAG_FOVEATED))
+    return GS_ERR_INVALID_ARG;
+  if ((uint32_t)c.flags &
+      ~(GS_FLAG_FOVEATED | GS_FLAG_BACKWARD | GS_FLAG_TIGHT | GS_FLAG_MULTI_MODEL))
     return GS_ERR_INVALID_ARG;
   p->flags = (uint32_t)c.flags;
   long long tiles = 0, pixels = 0, rows = 0;
@@ -186,10 +189,13 @@ gs_status gs_project(gs_plan *p, void *ws, size_t ws_bytes, const gs_scene *scen
         p->bytes[R_GRAD_LV] < 4 * sizeof(float) * (size_t)(L - 1) * (size_t)p->max_visible)
       return GS_ERR_INVALID_ARG;
     if ((fov->opacity_lv || fov->dc_lv) && L > kMvMaxLevels) return GS_ERR_UNSUPPORTED;
+    if ((p->flags & GS_FLAG_MULTI_MODEL) && (fov->opacity_lv || fov->dc_lv))
+      return GS_ERR_INVALID_ARG;
     p->fov = *fov;
     p->has_fov = 1;
     p->fov_mv = (fov->opacity_lv || fov->dc_lv) && L > 1;
   } else {
+    if (p->flags & GS_FLAG_MULTI_MODEL) return GS_ERR_INVALID_ARG;   // levels select the models
     memset(&p->fov, 0, sizeof(p->fov));
     p->has_fov = 0;
     p->fov_mv = 0;
@@ -214,6 +220,7 @@ gs_status gs_bin_sort(gs_plan *p, void *ws, cudaStream_t stream) {
 gs_status gs_render(gs_plan *p, void *ws, const float bg[3], float *rgb, float *T_final,
                     int32_t *last, uint32_t *stats, cudaStream_t stream) {
   if (!plan_ok(p) || !ws || !bg || !rgb || !T_final || !last || !p->cams) return GS_ERR_INVALID_ARG;
+  if (p->flags & GS_FLAG_MULTI_MODEL) return GS_ERR_INVALID_ARG;   // gs_render_fov selects the models
   p->last_fov = 0;
   return cuda_status(launch_render(p, ws, false, bg, rgb, T_final, last, stats, stream));
 }

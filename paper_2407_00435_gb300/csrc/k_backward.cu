@@ -43,6 +43,7 @@ struct BwdArgs {
   const float *opac;          // base opacities (N)
   int L;
   float band;
+  int mmfr;                   // a separate model per level (GS_FLAG_MULTI_MODEL)
   const float *opacity_lv, *dc_lv;
   float bg0, bg1, bg2;
   const float *dL;            // (P,3)
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
         BAcc &S = acc == 0 ? A : Bq;
         const int L_here = acc == 0 ? lvl : lvl - 1;
         if (pos > S.last) continue;
-        if (FOV && m < L_here) continue;
+        if (FOV && !takes_part(m, L_here, a.mmfr)) continue;
         const bool own = MV && L_here >= 2;
         const float4 c = own ? s_lv[q][L_here - 2] : s_col[q];
         const float r2 = own ? __fsub_rn(c.w, kLog2AlphaMin) : eb.z;
@@ -579,6 +580,7 @@ cudaError_t launch_backward(const gs_plan *p, void *ws, const float *dL, const f
   a.opac = p->scene.opacities;
   a.L = L;
   a.band = fov ? p->fov.band_px : 0.f;
+  a.mmfr = fov && (p->flags & GS_FLAG_MULTI_MODEL) ? 1 : 0;
   a.opacity_lv = mv ? p->fov.opacity_lv : nullptr;
   a.dc_lv = mv ? p->fov.dc_lv : nullptr;
   a.bg0 = bg[0]; a.bg1 = bg[1]; a.bg2 = bg[2];

@@ -35,6 +35,7 @@ struct RenderArgs {
   const uint8_t *rec_m;
   int L;
   float band;
+  int mmfr;                      // a separate model per level (GS_FLAG_MULTI_MODEL)
   const float *opacity_lv, *dc_lv;
   float bg0, bg1, bg2;
   float *rgb;
@@ -119,6 +120,9 @@ struct RSmem {
   uint16_t list[NW][NB];
   uint16_t wcnt[NW][SPT * NWS];
   uint16_t woff[NW][SPT * NWS + 1];
+  // per warp: the lowest level its pixels need | the highest own level << 8
+  // (a point whose m no pixel of the warp can use is left out of its list)
+  uint16_t wlv[FOV ? NW : 1];
   unsigned long long item;   // work-queue item broadcast
   int flag;                  // last chunk of a tile to arrive
   int abort;                 // an earlier chunk of the tile stopped every pixel
@@ -252,6 +256,14 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
         }
       }
       wm[u] = warp_mask_exact<B, PX>(mx, my, pre[u].shape, Fmax);
+      if (FOV) {
+#pragma unroll
+        for (int w = 0; w < G::kWarps; ++w) {
+          const int lo = sm.wlv[w] & 0xff, hi = sm.wlv[w] >> 8;
+          const int m = pre[u].m;
+          if (a.mmfr ? (m < lo || m > hi) : m < lo) wm[u] &= ~(1u << w);
+        }
+      }
       float4 ea, eb;
       make_eval(mx, my, pre[u].shape, pre[u].color.w, wm[u], ea, eb);
       sm.a[q] = ea;
@@ -315,7 +327,7 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
           float t1, t2;
           const float sq = eval_s2(px2, py2[k], sa, sb, t1, t2);
           // accumulator A: the pixel's own level
-          if (!A[k].done && (!FOV || m >= pp.lvl[k])) {
+          if (!A[k].done && (!FOV || takes_part(m, pp.lvl[k], a.mmfr))) {
             const bool own = MV && pp.lvl[k] >= 2;
             const float F = own ? sm.lv[q][pp.lvl[k] - 2].w : sm.c[q].w;
             const float r2 = own ? __fsub_rn(F, kLog2AlphaMin) : sb.z;
@@ -342,7 +354,7 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
             }
           }
           // accumulator B: the better level inside a blend band
-          if (FOV && !Bq[k].done && m >= pp.lvl[k] - 1) {
+          if (FOV && !Bq[k].done && takes_part(m, pp.lvl[k] - 1, a.mmfr)) {
             const bool own = MV && pp.lvl[k] >= 3;
             const float F = own ? sm.lv[q][pp.lvl[k] - 3].w : sm.c[q].w;
             const float r2 = own ? __fsub_rn(F, kLog2AlphaMin) : sb.z;
@@ -463,6 +475,21 @@ __device__ __forceinline__ void render_item(const RenderArgs &a,
       Bq[k] = Acc{0.f, 0.f, 0.f, 1.f, -1, !(inside && in_band)};
       dom_w[k] = -1.0f;
       dom_gid[k] = 0;
+    }
+    if (FOV) {
+      // the levels this warp's pixels use: own level, and one below in a band
+      int lo = 255, hi = 0;
+#pragma unroll
+      for (int k = 0; k < PX; ++k)
+        if ((inb >> k) & 1u) {
+          lo = min(lo, pp.lvl[k] - (int)((inb >> (PX + k)) & 1u));
+          hi = max(hi, pp.lvl[k]);
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if (lane == 0) sm.wlv[warp] = (uint16_t)(lo | (hi << 8));
     }
     if (CHUNK && tid == 0) {
       sm.abort = 0;
@@ -777,6 +804,7 @@ cudaError_t launch_render(const gs_plan *p, void *ws, bool fov, const float bg[3
   a.rec_m = p->bytes[R_REC_M] ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
   a.L = fov ? p->fov.n_levels : 1;
   a.band = fov ? p->fov.band_px : 0.0f;
+  a.mmfr = fov && (p->flags & GS_FLAG_MULTI_MODEL) ? 1 : 0;
   a.opacity_lv = fov ? p->fov.opacity_lv : nullptr;
   a.dc_lv = fov ? p->fov.dc_lv : nullptr;
   a.bg0 = bg[0];

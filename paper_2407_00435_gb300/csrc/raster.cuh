@@ -30,6 +30,14 @@ __device__ __forceinline__ int find_view(const ViewDev *views, int V, long long 
   return lo;
 }
 
+// Whether a point of quality bound (or model level) m takes part at level
+// l: nested subsets (Sec. 4.2) use the points with m >= l; with a separate
+// model per level (Sec. 4.1, main pipeline) level l uses the points of
+// model l only.
+__device__ __forceinline__ bool takes_part(int m, int l, bool disjoint) {
+  return disjoint ? m == l : m >= l;
+}
+
 // Foveation level of a pixel, band membership and the blend weight of the
 // pixel's own level (same FP32 expressions as the tile filter).
 __device__ __forceinline__ void pixel_level(const ViewDev &vd, int L, float band, int x, int y,

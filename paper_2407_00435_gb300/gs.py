@@ -23,6 +23,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_
 GS_FLAG_FOVEATED = 1
 GS_FLAG_BACKWARD = 2
 GS_FLAG_TIGHT = 4
+GS_FLAG_MULTI_MODEL = 8
 GS_MAX_LEVELS = 8
 (GS_REGION_ITEM_GID, GS_REGION_ITEM_VIEW, GS_REGION_ITEM_DEPTH, GS_REGION_ITEM_COUNT) = (1, 2, 3, 4)
 GS_REGION_RANGES, GS_REGION_TILE_LEVEL = 7, 8
@@ -242,14 +243,16 @@ class Renderer:
 
     def __init__(self, n, sh_degree, cams, tile=16, foveated=False, backward=False,
                  max_pairs=0, max_levels=0, chunk=0, radix_bits=0, chunk_slots=0,
-                 tight=False, device="cuda"):
+                 tight=False, multi_model=False, device="cuda"):
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cams_np = np.asarray(cams, np.float32).reshape(-1, 20)
         self.V = len(self.cams_np)
         self.device = device
         self.cfg = gs_config(tile, chunk, (GS_FLAG_FOVEATED if foveated else 0)
                              | (GS_FLAG_BACKWARD if backward else 0)
-                             | (GS_FLAG_TIGHT if tight else 0), max_levels,
+                             | (GS_FLAG_TIGHT if tight else 0)
+                             | (GS_FLAG_MULTI_MODEL | GS_FLAG_FOVEATED if multi_model else 0),
+                             max_levels,
                              radix_bits, chunk_slots, max_pairs)
         self.plan = C.create_string_buffer(int(_lib.gs_plan_size()))
         self._cams_h = cams_host(self.cams_np)

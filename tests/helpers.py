@@ -23,7 +23,7 @@ def ambiguous_bound(img, sel):
 
 
 def run_gpu(gs, wl, fov=None, stats=False, tile=None, bg=(0, 0, 0), mv=None, max_pairs=0,
-            backward=False, chunk=0, chunk_slots=0, tight=False):
+            backward=False, chunk=0, chunk_slots=0, tight=False, multi_model=False):
     import torch
     sc = gs.scene_to_device(wl.scene)
     f = None
@@ -32,7 +32,7 @@ def run_gpu(gs, wl, fov=None, stats=False, tile=None, bg=(0, 0, 0), mv=None, max
                              dc_lv=None if mv is None else mv[1])
     r = gs.Renderer(wl.scene.n, wl.scene.sh_degree, wl.cams, tile=tile or wl.tile,
                     foveated=fov is not None, backward=backward, max_pairs=max_pairs,
-                    chunk=chunk, chunk_slots=chunk_slots, tight=tight)
+                    chunk=chunk, chunk_slots=chunk_slots, tight=tight, multi_model=multi_model)
     if max_pairs:
         r.project(sc, f)
         r.bin_sort()

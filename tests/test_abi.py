@@ -42,6 +42,11 @@ def test_plan_init_validates_on_host(lib):
                 gs.gs_config(16, 32, 0, 0, 0, 0, 0),     # chunk below 64 points
                 gs.gs_config(16, 256, 0, 0, 0, -1, 0)):  # negative chunk slots
         assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(cfg)) == gs.GS_ERR_INVALID_ARG
+    # a separate model per level is a foveated plan
+    mm = gs.gs_config(16, 0, gs.GS_FLAG_MULTI_MODEL, 0, 0, 0, 0)
+    assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(mm)) == gs.GS_ERR_INVALID_ARG
+    mm = gs.gs_config(16, 0, gs.GS_FLAG_MULTI_MODEL | gs.GS_FLAG_FOVEATED, 0, 0, 0, 0)
+    assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(mm)) == gs.GS_OK
     lib.gs_workspace_size.argtypes = [C.c_void_p]
     lib.gs_workspace_size.restype = C.c_size_t
     # chunking reserves its slots; a plan without it does not
