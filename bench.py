@@ -123,6 +123,27 @@ RENDER_SOURCES = ("paper_2407_00435_gb300/csrc/k_render.cu", "paper_2407_00435_g
 RENDER_PROFILE = "profiles/render_plain_1080p_n1M.md"
 
 
+def peak_probe(torch, gs, iters=20000, reps=5):
+    """Measured FP32 FMA and ex2 lane-op rates (T ops/s): best of `reps`
+    event-timed launches of the library's probe kernel."""
+    sink = torch.zeros(1, device="cuda")
+    out = []
+    for kind in (0, 1):
+        gs.gs_peak_probe(kind, 100, sink)
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = gs.gs_peak_probe(kind, iters, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out.append(round(ops / (best * 1e-3) / 1e12, 3))
+    return out
+
+
 def render_sources_sha1():
     import hashlib
     h = hashlib.sha1()
@@ -262,12 +283,17 @@ def gpu_arm(args):
     peak_tops = N_SM * FP32_LANES * mhz * 1e6 / 1e12
     achieved_tops = (OPS_PER_EVAL * n_evals + OPS_PER_BLEND * n_blends) / (render_ms * 1e-3) / 1e12
     traffic, _ = captured_traffic()
+    probe = peak_probe(torch, gs)
     roofline = {"bound": "alu", "kernel": "k_render", "achieved": round(achieved_tops, 3),
                 "peak": round(peak_tops, 3), "unit": "TFLOP/s (FP32 lane-ops)",
                 "frac": round(achieved_tops / peak_tops, 4), "traffic": traffic,
                 "traffic_source": RENDER_PROFILE if traffic else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src} sm_max_mhz)",
-                "render_ms": round(render_ms, 4)}
+                "render_ms": round(render_ms, 4),
+                "probe": {"fma_tops": probe[0], "ex2_tops": probe[1],
+                          "frac_of_fma_probe": round(achieved_tops / probe[0], 4) if probe[0] else None,
+                          "note": "measured issue rates of independent FP32 FMA / ex2 chains on "
+                                  "every SM (gs_peak_probe), at the clock of the run"}}
 
     # ---- end to end through the public API with host buffers ----------------
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(wl.scene, k2))).pin_memory()

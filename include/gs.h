@@ -334,6 +334,20 @@ gs_status gs_compact_points(gs_plan *plan, void *ws, int64_t n, int32_t sh_degre
 gs_status gs_weighted_scale(int64_t n, const float *scales, const uint32_t *stats, float T,
                             float gamma, double *ws_out, float *d_scales, cudaStream_t stream);
 
+/* ---- measurement -------------------------------------------------------- */
+
+/* Issue-rate probe of the two units the render is bound by (the roofline
+ * denominators; no counterpart in the paper): kind 0 runs chains of
+ * independent FP32 fused multiply-adds, kind 1 chains of ex2.approx on the
+ * special-function unit, on every resident thread of every SM, `iters`
+ * steps of 8 chains per thread.  *ops (host) receives the lane operations
+ * launched (one FMA or one ex2 = one), so the caller divides it by the
+ * call's event-timed duration.  d_sink: device float receiving a checksum
+ * (keeps the work alive).  Errors: GS_ERR_INVALID_ARG (kind, iters < 1,
+ * NULL pointers), GS_ERR_CUDA. */
+gs_status gs_peak_probe(int32_t kind, int32_t iters, float *d_sink, int64_t *ops,
+                        cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@ UNITS = {
     "k_render.cu": [],
     "k_backward.cu": [],
     "k_prune.cu": [],
+    "k_peak.cu": [],
 }
 
 

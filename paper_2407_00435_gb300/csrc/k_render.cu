@@ -270,7 +270,12 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
       sm.b[q] = eb;
       sm.c[q] = pre[u].color;
       if (STATS) sm.gid[q] = pre[u].gid;
-      if (FOV) sm.m[q] = pre[u].m;
+      // levels the point takes part in, as a bit mask (bit l - 1: level l):
+      // levels 1..m for nested subsets, level m alone with a model per level
+      if (FOV) {
+        const int m = pre[u].m;
+        sm.m[q] = m < 1 ? 0 : (a.mmfr ? (1 << (m - 1)) : (1 << m) - 1);
+      }
     }
     // ordered compaction of the slots per target warp: ballot prefixes
     // inside each staging warp, then prefix sums over (u, staging warp)
@@ -316,18 +321,25 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
       unsigned long long py2[PX];
 #pragma unroll
       for (int k = 0; k < PX; ++k) py2[k] = f2_pack(pp.py[k], pp.py[k]);
+      // level bits of the two accumulators (own level; one below in a band)
+      uint32_t bitA[PX], bitB[PX];
+#pragma unroll
+      for (int k = 0; k < PX; ++k) {
+        bitA[k] = 1u << (pp.lvl[k] - 1);
+        bitB[k] = pp.lvl[k] >= 2 ? 1u << (pp.lvl[k] - 2) : 0u;
+      }
 #pragma unroll 4
       for (int li = 0; li < nlist; ++li) {
         const uint32_t q = sm.list[warp][li];
         const float4 sb = sm.b[q];
         const float4 sa = sm.a[q];
-        const int m = FOV ? sm.m[q] : 0;
+        const uint32_t pm = FOV ? (uint32_t)sm.m[q] : 0u;
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
           float t1, t2;
           const float sq = eval_s2(px2, py2[k], sa, sb, t1, t2);
           // accumulator A: the pixel's own level
-          if (!A[k].done && (!FOV || takes_part(m, pp.lvl[k], a.mmfr))) {
+          if (!A[k].done && (!FOV || (pm & bitA[k]))) {
             const bool own = MV && pp.lvl[k] >= 2;
             const float F = own ? sm.lv[q][pp.lvl[k] - 2].w : sm.c[q].w;
             const float r2 = own ? __fsub_rn(F, kLog2AlphaMin) : sb.z;
@@ -354,7 +366,7 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
             }
           }
           // accumulator B: the better level inside a blend band
-          if (FOV && !Bq[k].done && takes_part(m, pp.lvl[k] - 1, a.mmfr)) {
+          if (FOV && !Bq[k].done && (pm & bitB[k])) {
             const bool own = MV && pp.lvl[k] >= 3;
             const float F = own ? sm.lv[q][pp.lvl[k] - 3].w : sm.c[q].w;
             const float r2 = own ? __fsub_rn(F, kLog2AlphaMin) : sb.z;

@@ -114,6 +114,8 @@ def _load():
     lib.gs_compact_points.restype = s
     lib.gs_weighted_scale.argtypes = [C.c_int64, p, p, C.c_float, C.c_float, p, p, p]
     lib.gs_weighted_scale.restype = s
+    lib.gs_peak_probe.argtypes = [s, s, p, p, p]
+    lib.gs_peak_probe.restype = s
     return lib
 
 
@@ -223,6 +225,15 @@ def gs_weighted_scale(n, scales, stats, T, gamma, ws_out, d_scales=None, stream=
     _check(_lib.gs_weighted_scale(n, _ptr(scales), _ptr(stats), float(T), float(gamma),
                                   _ptr(ws_out), _ptr(d_scales), _stream(stream)),
            "gs_weighted_scale")
+
+
+def gs_peak_probe(kind, iters, sink, stream=None) -> int:
+    """Launches the FMA (kind 0) or ex2 (kind 1) issue-rate probe; returns
+    the lane operations launched (time the call with CUDA events)."""
+    ops = C.c_int64(0)
+    _check(_lib.gs_peak_probe(int(kind), int(iters), _ptr(sink), C.byref(ops), _stream(stream)),
+           "gs_peak_probe")
+    return int(ops.value)
 
 
 def gs_get_error(plan_buf, ws, stream=None):
