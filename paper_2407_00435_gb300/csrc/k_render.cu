@@ -2,11 +2,13 @@
 // foveated views (Sec. 4.1 "Main Pipeline", Sec. 4.2 subsetting and
 // multi-versioning), plus the per-point cost statistics of Sec. 3.2.
 //
-// One block per 16x16 (or 8x8) tile, one pixel per thread.  The tile's
-// sorted list is consumed in batches of one point per thread: each thread
-// gathers one record into shared memory (2D mean made tile-local from its
-// compensated hi/lo form), then every pixel walks the batch front to back.
-// A block leaves as soon as every pixel has stopped (block-wide vote).
+// One block per 16x16 (or 8x8) tile, two pixels per thread 4 rows apart
+// (one for foveated renders with per-level parameters or statistics).  The
+// tile's sorted list is consumed in batches: each thread gathers records into
+// shared memory (2D mean made tile-local from its compensated hi/lo form),
+// ordered per-warp lists of the points that can reach each warp are built,
+// then every warp walks its list front to back.  A block leaves as soon as
+// every pixel has stopped (block-wide vote).
 //
 // Per pixel and point: t = W (p - mu) with W the whitened inverse square
 // root of the 2D covariance scaled by sqrt(log2(e)/2), so that
@@ -185,6 +187,55 @@ __device__ __forceinline__ void composite_plain(const uint16_t *list, int nlist,
   }
 }
 
+// Foveated views, warps with no pixel in a blend band: accumulator A only,
+// composited as in composite_plain; a point takes part where its level bit
+// mask holds the pixel's level.
+template <int PX>
+__device__ __forceinline__ void composite_fov_a(const uint16_t *list, int nlist,
+                                                const float4 *ra, const float4 *rb,
+                                                const float4 *rc, const int *rm, int base,
+                                                const Pix<PX> &pp, Acc (&A)[PX],
+                                                uint32_t (&walk_end)[PX]) {
+  const unsigned long long px2 = f2_pack(pp.px, pp.px);
+  unsigned long long py2[PX];
+  uint32_t bit[PX];
+#pragma unroll
+  for (int k = 0; k < PX; ++k) {
+    py2[k] = f2_pack(pp.py[k], pp.py[k]);
+    bit[k] = 1u << (pp.lvl[k] - 1);
+  }
+#pragma unroll 8
+  for (int li = 0; li < nlist; ++li) {
+    const int q = list[li];
+    const float4 sa = ra[q], sb = rb[q], c = rc[q];
+    const uint32_t pm = (uint32_t)rm[q];
+    const int pos = base + q;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+      float t1, t2;
+      const float sq = eval_s2(px2, py2[k], sa, sb, t1, t2);
+      const float al = alpha_of(__fsub_rn(c.w, sq));
+      const float Tn = A[k].T * (1.0f - al);
+      const bool hit = !A[k].done && (pm & bit[k]) != 0u && sq <= sb.z;
+      if (hit && !(Tn < kTMin)) {
+        const float w = al * A[k].T;
+        A[k].r = fmaf(w, c.x, A[k].r);
+        A[k].g = fmaf(w, c.y, A[k].g);
+        A[k].b = fmaf(w, c.z, A[k].b);
+        A[k].T = Tn;
+        A[k].last = pos;
+      }
+      if (hit && Tn < kTMin) {
+        A[k].done = true;
+        walk_end[k] = pos + 1;
+      }
+      live = live || !A[k].done;
+    }
+    if ((li & 3) == 3 && !__any_sync(0xffffffffu, live)) break;
+  }
+}
+
 // Composites the sorted points [begin, end) of a tile front to back into
 // every accumulator that is not done.  List positions (`last`) are reported
 // relative to `origin`, the first pair of the tile.  Starts and ends with a
@@ -314,6 +365,17 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
     if (!FOV && !STATS) {
       if (__any_sync(0xffffffffu, !all_done_here()))
         composite_plain<PX>(sm.list[warp], sm.woff[warp][SPT * NWS], sm.a, sm.b, sm.c,
+                            (int)(b - origin), pp, A, walk_end);
+    } else if (FOV && !MV && !STATS &&
+               __all_sync(0xffffffffu, [&] {
+                 bool nb = true;
+#pragma unroll
+                 for (int k = 0; k < PX; ++k) nb = nb && Bq[k].done;
+                 return nb;
+               }())) {
+      // no pixel of the warp needs the second accumulator
+      if (__any_sync(0xffffffffu, !all_done_here()))
+        composite_fov_a<PX>(sm.list[warp], sm.woff[warp][SPT * NWS], sm.a, sm.b, sm.c, sm.m,
                             (int)(b - origin), pp, A, walk_end);
     } else if (__any_sync(0xffffffffu, !all_done_here())) {
       const int nlist = sm.woff[warp][SPT * NWS];
@@ -751,8 +813,9 @@ __global__ void k_tiles_touched(const uint32_t *count, const uint32_t *gid,
 template <int B, bool FOV, bool MV, bool STATS>
 static void launch_t(const RenderArgs &a, long long tiles, bool chunked, int num_sms,
                      cudaStream_t s) {
-  // plain views: two pixels per thread; foveated: one (two accumulators)
-  constexpr int PX = FOV ? 1 : 2;
+  // two pixels per thread, except foveated renders with per-level parameters
+  // or statistics, whose state does not fit the registers of two pixels
+  constexpr int PX = (FOV && (MV || STATS)) ? 1 : 2;
   constexpr int NT = B * B / PX;
   if (STATS || !chunked) {
     k_render<B, FOV, MV, STATS, PX, false><<<(unsigned)tiles, NT, 0, s>>>(a);
