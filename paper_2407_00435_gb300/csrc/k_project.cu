@@ -564,12 +564,24 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
   const bool tight = a.rec_supp != nullptr, fov = a.tile_level != nullptr;
   for (long long base = wid * 32; base < slots; base += warps * 32) {
     const long long j = base + lane;
+    // every record the item may need, loaded at once (invisible slots hold
+    // stale values that are never used): one round trip instead of a chain
+    const bool in = j < slots;
+    const uint32_t dkey = in ? a.rec_depth[j] : 0xffffffffu;
+    const uint2 rr = in ? a.rec_rect[j] : make_uint2(0u, 0u);
+    float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float spc = 0.f, op0 = 0.f;
+    if (tight && in) {
+      sp = a.rec_supp[j];
+      spc = a.rec_supp2[j].x;
+      op0 = a.opac[j / a.V];
+    }
+    const int mrec = (fov && in) ? (int)a.rec_m[j] : 0;
     bool vis = false;
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
-    if (j < slots && a.rec_depth[j] != 0xffffffffu) {
+    if (dkey != 0xffffffffu) {
       vis = true;
-      const uint2 r = a.rec_rect[j];
-      x0 = r.x & 0xffff; x1 = r.x >> 16; y0 = r.y & 0xffff; y1 = r.y >> 16;
+      x0 = rr.x & 0xffff; x1 = rr.x >> 16; y0 = rr.y & 0xffff; y1 = rr.y >> 16;
     }
     // rows this lane's item contributes to the cooperative pass
     int rows = 0;
@@ -582,7 +594,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
         } else {
           // foveation filter only: one interval lookup per row
           const ViewDev &vd = a.views[j % a.V];
-          const int m = (int)a.rec_m[j];
+          const int m = mrec;
           uint32_t pairs = 0;
           for (int y = y0; y <= y1; ++y) {
             int la, lb;
@@ -602,15 +614,15 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
     if (rows) {
       if (tight) {
         const long long i = j / a.V;
-        float o_max = a.opac[i];
+        float o_max = op0;
         for (int l = 0; l < a.n_opacity_lv; ++l)
           o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
-        const float2 s1 = make_float2(a.rec_supp2[j].x, tight_tau(o_max));
+        const float2 s1 = make_float2(spc, tight_tau(o_max));
         a.rec_supp2[j] = s1;
-        pre = supp_prep(a.rec_supp[j], s1);
+        pre = supp_prep(sp, s1);
       }
       if (fov) {
-        m = (int)a.rec_m[j];
+        m = mrec;
         rbase = a.views[j % a.V].row_base;
       }
     }
@@ -678,12 +690,15 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
       const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
       const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
       const long long i = jb / a.V;
-      float o_max = a.opac[i];
+      float o_max = __shfl_sync(0xffffffffu, op0, src);
       for (int l = 0; l < a.n_opacity_lv; ++l)
         o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
-      const float2 s1 = make_float2(a.rec_supp2[jb].x, tight_tau(o_max));
-      const SuppPre pb = supp_prep(a.rec_supp[jb], s1);
-      const int bm = fov ? (int)a.rec_m[jb] : 0;
+      const float2 s1 = make_float2(__shfl_sync(0xffffffffu, spc, src), tight_tau(o_max));
+      const float4 bsp = make_float4(
+          __shfl_sync(0xffffffffu, sp.x, src), __shfl_sync(0xffffffffu, sp.y, src),
+          __shfl_sync(0xffffffffu, sp.z, src), __shfl_sync(0xffffffffu, sp.w, src));
+      const SuppPre pb = supp_prep(bsp, s1);
+      const int bm = __shfl_sync(0xffffffffu, mrec, src);
       const int brb = fov ? a.views[jb % a.V].row_base : 0;
       uint32_t bpairs = 0;
       for (int y = by0 + lane; y <= by1; y += 32) {

@@ -49,6 +49,7 @@ struct SortArgs {
   int digit_bits;                    // bits per pass (<= 8)
   int no_skip;                       // run every pass (fixed buffer parity)
   uint32_t *status;
+  int sub;                           // upsweep sub-ranges per block, 1..kSortSub (0: kSortSub)
 };
 
 __device__ __forceinline__ uint32_t sort_n(const SortArgs &a) {
@@ -65,8 +66,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // Partition ranges: downsweep block b of G owns partitions [b q, (b + 1) q),
 // q = ceil(parts / G).  The upsweep splits each block's key range into
-// kSortSub equal pieces (it only counts, so any split is fine); row s of
-// the block table belongs to piece s % kSortSub of block s / kSortSub.
+// `sub` equal pieces (it only counts, so any split is fine); row s of the
+// block table belongs to piece s % sub of block s / sub.
 __device__ __forceinline__ void block_parts(uint32_t n, int G, int b, long long &p0, long long &p1) {
   const long long nparts = ((long long)n + kSortPart - 1) / kSortPart;
   const long long q = (nparts + G - 1) / G;
@@ -74,16 +75,16 @@ __device__ __forceinline__ void block_parts(uint32_t n, int G, int b, long long 
   p1 = p0 + q < nparts ? p0 + q : nparts;
 }
 
-__device__ __forceinline__ void sub_keys(uint32_t n, int G, long long s, long long &k0,
+__device__ __forceinline__ void sub_keys(uint32_t n, int G, int sub, long long s, long long &k0,
                                          long long &k1) {
   long long p0, p1;
-  block_parts(n, G, (int)(s / kSortSub), p0, p1);
+  block_parts(n, G, (int)(s / sub), p0, p1);
   const long long b0 = p0 * kSortPart;
   const long long b1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
   const long long len = b1 > b0 ? b1 - b0 : 0;
-  const long long j = s % kSortSub;
-  k0 = b0 + len * j / kSortSub;
-  k1 = b0 + len * (j + 1) / kSortSub;
+  const long long j = s % sub;
+  k0 = b0 + len * j / sub;
+  k1 = b0 + len * (j + 1) / sub;
 }
 
 // Input buffers of pass `pass`: the first executed pass reads the caller's
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(256) k_hist_scan(SortArgs a) {
   if (t == 0) *a.sel = (uint32_t)(executed & 1);
 }
 
-// ---- upsweep: digit counts of each sub-range (kSortSub x G blocks) ------------
+// ---- upsweep: digit counts of each sub-range (sub x G blocks) ----------------
 constexpr int kUpUnroll = 8;
 
 __global__ void __launch_bounds__(kSortThreads) k_upsweep(SortArgs a, int pass) {
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kSortThreads) k_upsweep(SortArgs a, int pass) 
   for (int q = tid; q < (kSortThreads / 32) * 256; q += kSortThreads) (&s_h[0][0])[q] = 0u;
   __syncthreads();
   long long k0, k1;
-  sub_keys(n, a.blocks, blockIdx.x, k0, k1);
+  sub_keys(n, a.blocks, a.sub, blockIdx.x, k0, k1);
   constexpr int kStep = kSortThreads * kUpUnroll;
   for (long long base = k0; base < k1; base += kStep) {
     uint32_t key[kUpUnroll];
@@ -225,7 +226,7 @@ constexpr int kScanRegRows = 32;
 __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pass) {
   __shared__ uint32_t s_p[kScanDigits][kScanSlices + 1];
   if (a.skip[pass]) return;
-  const int R = kSortSub * a.blocks;
+  const int R = a.sub * a.blocks;
   const int dl = threadIdx.x & (kScanDigits - 1), sl = threadIdx.x / kScanDigits;
   const int d = blockIdx.x * kScanDigits + dl;
   const int rows = (R + kScanSlices - 1) / kScanSlices;
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
   long long p0, p1;
   block_parts(n, a.blocks, blockIdx.x, p0, p1);
   if (p0 >= p1) return;
-  if (tid < 256) sm.carry[tid] = a.bsum[(long long)blockIdx.x * kSortSub * 256 + tid];
+  if (tid < 256) sm.carry[tid] = a.bsum[(long long)blockIdx.x * a.sub * 256 + tid];
   const bool aligned = ((uintptr_t)kin & 15u) == 0 && (iota || ((uintptr_t)vin & 15u) == 0);
   const long long full = (long long)n / kSortPart;   // partitions [0, full) hold 4096 keys
   constexpr uint32_t kBytes = kSortPart * sizeof(uint32_t);
@@ -499,13 +500,15 @@ static void init_grids() {
 
 // Runs every pass of one sort.  a.blocks must be set (at most the rows of
 // a.bsum).
-static cudaError_t run_sort(const SortArgs &a, cudaStream_t s, bool hist_done = false) {
+static cudaError_t run_sort(const SortArgs &a0, cudaStream_t s, bool hist_done = false) {
+  SortArgs a = a0;
+  if (a.sub < 1 || a.sub > kSortSub) a.sub = kSortSub;
   if (!hist_done) k_hist<<<a.blocks, 256, 0, s>>>(a);
   k_hist_scan<<<1, 256, 0, s>>>(a);
   const unsigned scan_blocks =
       (1u << a.digit_bits) > kScanDigits ? (1u << a.digit_bits) / kScanDigits : 1u;
   for (int p = 0; p < a.passes; ++p) {
-    k_upsweep<<<kSortSub * a.blocks, kSortThreads, 0, s>>>(a, p);
+    k_upsweep<<<a.sub * a.blocks, kSortThreads, 0, s>>>(a, p);
     k_scan_blocks<<<scan_blocks, kScanThreads, 0, s>>>(a, p);
     k_downsweep<<<a.blocks, kDownThreads, sizeof(DownSmem), s>>>(a, p);
   }
@@ -935,6 +938,13 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   d.passes = 4;
   d.digit_bits = 8;
   d.status = &hdr->status;
+  {
+    // sub-ranges per block so that an upsweep block counts about one
+    // partition of keys (few partitions per block for small scenes)
+    const long long nparts = (p->n * p->V + kSortPart - 1) / kSortPart;
+    const long long q = (nparts + G - 1) / G;
+    d.sub = (int)(q < 1 ? 1 : (q > kSortSub ? kSortSub : q));
+  }
   e = run_sort(d, s);
   if (e != cudaSuccess) return e;
   // 2. pair offsets in depth order
