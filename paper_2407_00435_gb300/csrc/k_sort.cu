@@ -734,22 +734,29 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
     }
     uint4 tbl = make_uint4(0u, 0u, 0u, 0u);
     if (TABLE && valid && !huge && cnt > 0) tbl = a.table[j];
-    const uint32_t g0 = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t last = 31 - __clz(__ballot_sync(0xffffffffu, valid));
-    const uint32_t g1 = __shfl_sync(0xffffffffu, off + cnt, last);
-    for (uint32_t p0 = g0; p0 < g1; p0 += 32) {
-      const uint32_t pos = p0 + lane;
-      // owning item: the last lane whose offset is <= pos (offsets ascend;
-      // invalid lanes hold 0xffffffff)
+    // the pairs this kernel writes: the warp's items without the queued ones,
+    // numbered by a warp scan (queued items take no iterations here)
+    const uint32_t ce = (valid && !huge) ? cnt : 0u;
+    uint32_t lincl = ce;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, lincl, o);
+      if (lane >= o) lincl += v;
+    }
+    const uint32_t lexcl = lincl - ce;
+    const uint32_t total = __shfl_sync(0xffffffffu, lincl, 31);
+    for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+      const uint32_t lp = p0 + lane;
+      // owning item: the last lane whose local start is <= lp (starts
+      // ascend; a lane after it with no pairs starts beyond lp)
       int L = 0;
 #pragma unroll
       for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t o = __shfl_sync(0xffffffffu, off, L + step);
-        if (o <= pos) L += step;
+        const uint32_t o = __shfl_sync(0xffffffffu, lexcl, L + step);
+        if (o <= lp) L += step;
       }
+      const uint32_t lstart = __shfl_sync(0xffffffffu, lexcl, L);
       const uint32_t ioff = __shfl_sync(0xffffffffu, off, L);
-      const uint32_t icnt = __shfl_sync(0xffffffffu, cnt, L);
-      const bool ihuge = __shfl_sync(0xffffffffu, (int)huge, L) != 0;
       const uint32_t ij = __shfl_sync(0xffffffffu, j, L);
       const uint32_t rx = __shfl_sync(0xffffffffu, r.x, L);
       const uint32_t ry = __shfl_sync(0xffffffffu, r.y, L);
@@ -758,10 +765,11 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
       it.y = __shfl_sync(0xffffffffu, tbl.y, L);
       it.z = __shfl_sync(0xffffffffu, tbl.z, L);
       it.w = __shfl_sync(0xffffffffu, tbl.w, L);
-      bool wr = pos < g1 && !ihuge && pos - ioff < icnt && (long long)pos < a.pair_capacity;
+      const uint32_t rank = lp - lstart;
+      const uint32_t pos = ioff + rank;
+      bool wr = lp < total && (long long)pos < a.pair_capacity;
       uint32_t t = 0;
       if (wr) {
-        const uint32_t rank = pos - ioff;
         const int ix0 = rx & 0xffff, ix1 = rx >> 16, iy0 = ry & 0xffff;
         int row = 0, col = 0;
         if (TABLE) {
