@@ -28,7 +28,7 @@ METRIC = "FPS & Gpix/s @1080p, 1M Gaussians: batched/foveated vs plain; bwd ms/v
 L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--only", nargs="*", default=None, help="extras to run")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # --------------------------------------------------------------------------
@@ -121,6 +121,21 @@ OPS_PER_BLEND = 8
 
 RENDER_SOURCES = ("paper_2407_00435_gb300/csrc/k_render.cu", "paper_2407_00435_gb300/csrc/raster.cuh")
 RENDER_PROFILE = "profiles/render_plain_1080p_n1M.md"
+
+
+def max_over_ranks(torch, dist, x, world, device):
+    """The largest of the ranks' values of x (a job's step time is its
+    slowest rank's); x itself with one rank."""
+    if world <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ms_max, world):
+    """Whole-job frames/s of `world` replicas whose slowest takes ms_max per frame."""
+    return 1000.0 / ms_max * world
 
 
 def peak_probe(torch, gs, iters=20000, reps=5):
@@ -266,13 +281,8 @@ def gpu_arm(args):
         dist.barrier()
     code, cnt2 = r.counters()
     assert code == gs.GS_OK, cnt2
-    ms = total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    fps_rank = 1000.0 / ms
-    value = fps_rank * world
+    ms = max_over_ranks(torch, dist, total_ms / args.steps, world, "cuda")
+    value = job_rate(ms, world)
     render_ms = sum(k_ms) / len(k_ms)
     clocks = clk.summary()
     stages = {nm: round(sum(e[q].elapsed_time(e[q + 1]) for e in stage_ev) / len(stage_ev), 4)
@@ -316,7 +326,7 @@ def gpu_arm(args):
     eb = torch.cuda.Event(enable_timing=True)
     pipe.run(frames, ea, eb)
     torch.cuda.synchronize()
-    e2e_ms = ea.elapsed_time(eb) / k_e2e
+    e2e_ms = max_over_ranks(torch, dist, ea.elapsed_time(eb) / k_e2e, world, "cuda")
     code, cnt3 = r.counters()
     assert code == gs.GS_OK, cnt3
     gpu_launches = args.steps * r.launches_per_frame()
@@ -369,7 +379,7 @@ def gpu_arm(args):
         "evals_per_s": round(n_evals * value, 1),
         "stages_ms": stages,
         "roofline": roofline,
-        "e2e": {"value": round(1000.0 / e2e_ms * world, 2), "unit": "frames/s",
+        "e2e": {"value": round(job_rate(e2e_ms, world), 2), "unit": "frames/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "pipelined": "scene upload of frame i+1 and image read-back of frame i-1 "
                              "overlap frame i (copy, compute, read-back streams)"},
