@@ -812,9 +812,13 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
   }
 }
 
-// Items with more than kBigItem tiles: the warps of the grid stride over the
-// queue (no shared ticket to contend on) and write each item's tiles 32 at a
-// time (ballot prefix for the kept ones).
+// Items with more than kBigItem tiles (or no row table): the warps of the
+// grid stride over the queue (no shared ticket to contend on), one item per
+// warp.  The item's rows are taken 32 at a time, one row per lane (its kept
+// interval: rectangle, tight support, foveation filter); a warp scan of the
+// row lengths numbers the batch's pairs, which the lanes then write 32 at a
+// time, each finding its row by binary search over the row starts.  Pairs
+// come out row by row, columns ascending, as the item's rank order.
 template <bool FOV, bool TIGHT>
 __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
   __shared__ uint32_t sh[4][256];
@@ -823,7 +827,6 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
   const uint32_t nbig = *a.big_count;
   const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
   const int lane = threadIdx.x & 31;
-  const uint32_t ltmask = (1u << lane) - 1u;
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
   const uint32_t warps = gridDim.x * (blockDim.x / 32);
   for (uint32_t qi = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); qi < nbig; qi += warps) {
@@ -837,37 +840,55 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
     SuppPre pre;
     if (TIGHT) pre = supp_prep(a.supp[j], a.supp2[j]);
     long long run = off;
-    // row by row (the kept columns of a row form one interval), 32 tiles of
-    // a row at a time
-    for (int y = y0; y <= y1; ++y) {
+    for (int yb = y0; yb <= y1; yb += 32) {
+      // this lane's row: its kept columns [xa, xb] (one interval)
+      const int y = yb + lane;
       int xa = x0, xb = x1;
-      if (TIGHT) {
+      bool any = y <= y1;
+      if (TIGHT && any) {
         int ia, ib;
-        if (!row_interval(pre, y, a.tile, ia, ib)) continue;   // warp-uniform
+        any = row_interval(pre, y, a.tile, ia, ib);
         xa = max(xa, ia);
         xb = min(xb, ib);
       }
-      if (FOV) {
+      if (FOV && any) {
         int la, lb;
         level_row(a.level_rows, vd.row_base + y, m, la, lb);
         xa = max(xa, la);
         xb = min(xb, lb);
       }
-      for (int xs = xa; xs <= xb; xs += 32) {
-        const int x = xs + lane;
-        const bool kept = x <= xb;
-        long long t = 0;
-        if (kept) t = vd.tile_base + (long long)y * vd.tx + x;
-        const uint32_t b = __ballot_sync(0xffffffffu, kept);
-        const long long o = run + __popc(b & ltmask);
-        const bool wr = kept && o < a.pair_capacity;
+      const uint32_t len = (any && xa <= xb) ? (uint32_t)(xb - xa + 1) : 0u;
+      uint32_t incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const uint32_t excl = incl - len;
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+        const uint32_t lp = p0 + lane;
+        // owning row: the last lane whose start is <= lp (a later lane with
+        // an empty row starts beyond lp)
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t o = __shfl_sync(0xffffffffu, excl, L + step);
+          if (o <= lp) L += step;
+        }
+        const uint32_t rs = __shfl_sync(0xffffffffu, excl, L);
+        const int rxa = __shfl_sync(0xffffffffu, xa, L);
+        const long long o = run + lp;
+        const bool wr = lp < total && o < a.pair_capacity;
+        uint32_t t = 0;
         if (wr) {
-          a.pkey[o] = (uint32_t)t;
+          t = (uint32_t)(vd.tile_base + (long long)(yb + L) * vd.tx + (rxa + (int)(lp - rs)));
+          a.pkey[o] = t;
           a.pval[o] = j;
         }
-        hist_add_warp(sh, wr, (uint32_t)t, a.passes, a.digit_bits, dmask, lane);
-        run += __popc(b);
+        hist_add_warp(sh, wr, t, a.passes, a.digit_bits, dmask, lane);
       }
+      run += total;
     }
   }
   __syncthreads();
