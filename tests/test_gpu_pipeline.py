@@ -51,3 +51,30 @@ def test_pipeline_frames_equal_direct_renders(gs, depth):
     assert code == gs.GS_OK, c
     for i in range(n):
         np.testing.assert_array_equal(rgb[i].numpy(), ref[i % 2])
+
+
+def test_pipeline_foveated_frames(gs):
+    """The same with a foveated plan (two accumulators, band blending)."""
+    import torch
+    from paper_2407_00435_gb300.pipeline import HostFramePipeline
+    rng = np.random.default_rng(809)
+    sc = synth.blob_scene(rng, 30000, n_blobs=10, degree=1)
+    cams = synth.camera_lookat((0, 0, -4), (0, 0, 0), 256, 192)[None]
+    m = synth.nested_levels(rng, sc.n, 3)
+    f = synth.Foveation(3, m, synth.ring_tangents([6.0, 12.0]), 8.0, synth.random_gaze(rng, cams))
+    fd = gs.fov_to_device(f)
+    r = gs.Renderer(sc.n, 1, cams, foveated=True)
+    r.fit(gs.scene_to_device(sc), fd, headroom=1.5)
+    out = r.alloc_outputs(fov=True)
+    r.project(gs.scene_to_device(sc), fd)
+    r.bin_sort()
+    r.render(out, fov=True)
+    ref = out["rgb"].cpu().numpy()
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).pin_memory()
+            for k in ("means", "scales", "quats", "opac", "sh")}
+    rgb = [torch.zeros(r.P, 3).pin_memory() for _ in range(3)]
+    pipe = HostFramePipeline(r, fov=fd)
+    pipe.run([(host, rgb[i]) for i in range(3)])
+    torch.cuda.synchronize()
+    for i in range(3):
+        np.testing.assert_array_equal(rgb[i].numpy(), ref)
