@@ -26,6 +26,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FPS & Gpix/s @1080p, 1M Gaussians: batched/foveated vs plain; bwd ms/view"
 L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+# the headline workload, the same for both arms
+HEADLINE_CONFIG = {"workload": "plain_1920x1080_n1M_sh3", "points": 1_000_000, "sh_degree": 3,
+                   "resolution": "1920x1080", "tile": 16, "views_per_step": 1,
+                   "support": "tight: tiles of the 3-sigma rectangle that the alpha >= 1/255 "
+                              "ellipse reaches (same image)"}
 
 
 def parse(argv=None):
@@ -239,6 +244,7 @@ def gpu_arm(args):
 
     # ---- headline: plain forward, 1080p, 1M points, SH3 ---------------------
     wl = synth.workload(1)
+    assert wl.name == HEADLINE_CONFIG["workload"] and wl.scene.n == HEADLINE_CONFIG["points"]
     sc = gs.scene_to_device(wl.scene)
     r = gs.Renderer(wl.scene.n, wl.scene.sh_degree, wl.cams, tight=True)
     c = r.fit(sc)
@@ -367,10 +373,7 @@ def gpu_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded blob-mixture scene; the paper's datasets are not available)",
-        "config": {"workload": wl.name, "points": wl.scene.n, "sh_degree": 3,
-                   "resolution": "1920x1080", "tile": 16, "views_per_step": 1,
-                   "support": "tight: tiles of the 3-sigma rectangle that the alpha >= 1/255 "
-                              "ellipse reaches (same image)",
+        "config": {**HEADLINE_CONFIG,
                    "pairs_K": int(c["n_pairs"]), "visible": int(c["n_visible"]),
                    "l2": "flushed between steps (256 MB write) and scene 236 MB > L2",
                    "parallelism": f"replicas x{world}"},
@@ -660,7 +663,7 @@ def cpu_oracle_fps(budget_s=20.0):
     oracle.build()
     wl = synth.workload(1)
     t0 = time.perf_counter()
-    b = oracle.bin_pairs(wl.scene, wl.cams, 16)
+    b = oracle.bin_pairs(wl.scene, wl.cams, 16, tight=True)
     t_bin = time.perf_counter() - t0
     vp = oracle.project_values(wl.scene, wl.cams, b.vis)
     t_proj = time.perf_counter() - t0 - t_bin
@@ -698,7 +701,7 @@ def reference_arm(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000.0 / v, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "plain_1920x1080_n1M_sh3"},
+            "config": {**HEADLINE_CONFIG, "parallelism": f"replicas x{world}"},
             "cpu_baseline": {**vals[-1], "value": round(v, 5)},
             "e2e": {"value": round(v, 5), "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
