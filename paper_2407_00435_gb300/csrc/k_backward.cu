@@ -257,6 +257,231 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
   }
 }
 
+// Plain views: the forward's layout (two pixels per thread, rows 4 apart),
+// per-warp ordered lists of the batch points that can reach the warp's
+// pixels and lie at or before the last position any of them blended, and a
+// reduce-scatter of the nine per-point sums over the warp (16 shuffles; the
+// two lanes holding a total, the even one adds it to shared memory).
+template <int B>
+struct BwdSmem {
+  static constexpr int PX = 2;
+  static constexpr int NT = B * B / PX;                   // threads
+  static constexpr int NB = 2 * NT < 256 ? 2 * NT : 256;  // points per batch
+  static constexpr int SPT = NB / NT;                     // staged per thread
+  static constexpr int NWS = NT / 32;                     // staging warps
+  static constexpr int NW = WarpGeom<B, PX>::kWarps;      // pixel warps
+  float2 mean[NB];
+  float4 shape[NB];
+  float4 col[NB];
+  float4 ea[NB], eb[NB];
+  float op[NB];
+  uint32_t j[NB];
+  float g[NB][9];   // per batch slot: dmu(2) dQ(3) do(1) dc(3)
+  uint16_t list[NW][NB];
+  uint16_t wcnt[NW][SPT * NWS];
+  uint16_t woff[NW][SPT * NWS + 1];
+  int wlast[NW];    // last blended position of the warp's pixels (-1: none)
+  int maxlast;
+};
+
+template <int B>
+__global__ void __launch_bounds__(B * B / 2) k_render_bwd_plain(BwdArgs a) {
+  using Sm = BwdSmem<B>;
+  using G = WarpGeom<B, 2>;
+  constexpr int NT = Sm::NT, NB = Sm::NB, SPT = Sm::SPT, NWS = Sm::NWS, NW = Sm::NW;
+  __shared__ Sm sm;
+  const long long t = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t ltmask = (1u << lane) - 1u;
+  const ViewDev vd = a.views[find_view(a.views, a.V, t)];
+  const int local = (int)(t - vd.tile_base);
+  const int tx0 = (local % vd.tx) * B, ty0 = (local / vd.tx) * B;
+  const int lx = (warp % G::kWx) * 8 + (lane & 7);
+  const int ly0 = (warp / G::kWx) * G::kRows + (lane >> 3);
+  const float px = (float)lx + 0.5f;
+  float py[2];
+  BAcc A[2];
+  int mylast = -1;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int x = tx0 + lx, y = ty0 + ly0 + 4 * k;
+    py[k] = (float)(ly0 + 4 * k) + 0.5f;
+    A[k] = BAcc{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1};
+    if (x < vd.W && y < vd.H) {
+      const long long pix = vd.pix_base + (long long)y * vd.W + x;
+      A[k].T = a.T[pix];
+      A[k].last = a.last[pix];
+      A[k].gr = a.dL[3 * pix];
+      A[k].gg = a.dL[3 * pix + 1];
+      A[k].gb = a.dL[3 * pix + 2];
+      A[k].Sr = A[k].T * a.bg0;
+      A[k].Sg = A[k].T * a.bg1;
+      A[k].Sb = A[k].T * a.bg2;
+      mylast = max(mylast, A[k].last);
+    }
+  }
+  int wl = mylast;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+  if (tid == 0) sm.maxlast = -1;
+  for (int k = tid; k < NB * 9; k += NT) (&sm.g[0][0])[k] = 0.0f;
+  __syncthreads();
+  if (lane == 0) {
+    sm.wlast[warp] = wl;
+    atomicMax(&sm.maxlast, wl);
+  }
+  __syncthreads();
+  const int maxlast = sm.maxlast;
+  if (maxlast < 0) return;
+  const uint2 rg = a.ranges[t];
+  const uint32_t *vals = *a.sel ? a.pval_b : a.pval_a;
+  const uint32_t end = rg.x + (uint32_t)maxlast + 1;
+  const float inv = 1.0f / (kWhiten * kWhiten);
+
+  for (uint32_t hi = end; hi > rg.x;) {
+    const uint32_t lo = hi - rg.x > (uint32_t)NB ? hi - NB : rg.x;
+    const uint32_t cnt = hi - lo;
+    const int base = (int)(lo - rg.x);
+    // stage the batch: records, evaluation constants and the warps each
+    // point can reach at or before their last blended position
+    uint32_t wm[SPT];
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int q = tid + u * NT;
+      wm[u] = 0u;
+      if ((uint32_t)q < cnt) {
+        const uint32_t j = vals[lo + q];
+        const float4 mean = a.rec_mean[j];
+        const float mx = (mean.x - (float)tx0) + mean.z, my = (mean.y - (float)ty0) + mean.w;
+        const float4 shp = a.rec_shape[j];
+        const float4 col = a.rec_color[j];
+        sm.mean[q] = make_float2(mx, my);
+        sm.shape[q] = shp;
+        sm.col[q] = col;
+        sm.j[q] = j;
+        sm.op[q] = a.opac[a.rec_gid[j]];
+        uint32_t msk = warp_mask_exact<B, 2>(mx, my, shp, col.w);
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+          if (base + q > sm.wlast[w]) msk &= ~(1u << w);
+        float4 ea, eb;
+        make_eval(mx, my, shp, col.w, msk, ea, eb);
+        sm.ea[q] = ea;
+        sm.eb[q] = eb;
+        wm[u] = msk;
+      }
+    }
+    // ordered per-warp lists (ballot prefixes, then prefix sums over the
+    // (slot group, staging warp) pairs)
+    uint32_t pfx[SPT][NW];
+#pragma unroll
+    for (int u = 0; u < SPT; ++u)
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (wm[u] >> w) & 1u);
+        pfx[u][w] = __popc(bal & ltmask);
+        if (lane == 0) sm.wcnt[w][u * NWS + warp] = (uint16_t)__popc(bal);
+      }
+    __syncthreads();
+    if (tid < NW) {
+      uint32_t run = 0;
+      for (int e = 0; e < SPT * NWS; ++e) {
+        sm.woff[tid][e] = (uint16_t)run;
+        run += sm.wcnt[tid][e];
+      }
+      sm.woff[tid][SPT * NWS] = (uint16_t)run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SPT; ++u)
+#pragma unroll
+      for (int w = 0; w < NW; ++w)
+        if ((wm[u] >> w) & 1u)
+          sm.list[w][sm.woff[w][u * NWS + warp] + pfx[u][w]] = (uint16_t)(tid + u * NT);
+    __syncthreads();
+    // back to front over this warp's list
+    const int nlist = sm.woff[warp][SPT * NWS];
+    for (int li = nlist - 1; li >= 0; --li) {
+      const int q = sm.list[warp][li];
+      const int pos = base + q;
+      const float4 ea = sm.ea[q], eb = sm.eb[q], c = sm.col[q], shp = sm.shape[q];
+      const float2 mu = sm.mean[q];
+      const float o = sm.op[q];
+      float v[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[k] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        BAcc &S = A[k];
+        if (pos > S.last) continue;
+        float t1, t2;
+        const float sq = eval_s(px, py[k], ea, eb, t1, t2);
+        if (!(sq <= eb.z)) continue;
+        const float al = alpha_of(__fsub_rn(c.w, sq));
+        const float om = 1.0f - al;
+        const float Tb = S.T / om;
+        const float w = al * Tb;
+        v[6] += w * S.gr;
+        v[7] += w * S.gg;
+        v[8] += w * S.gb;
+        const float dal = S.gr * (Tb * c.x - S.Sr / om) + S.gg * (Tb * c.y - S.Sg / om) +
+                          S.gb * (Tb * c.z - S.Sb / om);
+        S.Sr = fmaf(w, c.x, S.Sr);
+        S.Sg = fmaf(w, c.y, S.Sg);
+        S.Sb = fmaf(w, c.z, S.Sb);
+        S.T = Tb;
+        if (al < kAlphaMax) {
+          const float dpow = dal * al;
+          const float dx = px - mu.x, dy = py[k] - mu.y;
+          v[5] += dpow / o;
+          // Q d = (w1 t1 + w2 t2) / kWhiten^2, d = pixel - mean
+          v[0] += dpow * (shp.x * t1 + shp.z * t2) * inv;
+          v[1] += dpow * (shp.y * t1 + shp.w * t2) * inv;
+          v[2] += -0.5f * dpow * dx * dx;
+          v[3] += -dpow * dx * dy;
+          v[4] += -0.5f * dpow * dy * dy;
+        }
+      }
+      bool nz = false;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) nz = nz || v[k] != 0.0f;
+      if (__any_sync(0xffffffffu, nz)) {
+        // reduce-scatter: each halving step keeps half of the values and
+        // adds the partner's copy of them; lanes 2i, 2i + 1 end with total i
+        float r[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) r[k] = k < 9 ? v[k] : 0.0f;
+#pragma unroll
+        for (int off = 16, h = 8; off >= 2; off >>= 1, h >>= 1) {
+          const bool up = (lane & off) != 0;
+#pragma unroll
+          for (int i = 0; i < h; ++i) {
+            const float send = up ? r[i] : r[i + h];
+            const float keep = up ? r[i + h] : r[i];
+            r[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+        r[0] += __shfl_xor_sync(0xffffffffu, r[0], 1);
+        const int idx = lane >> 1;
+        if ((lane & 1) == 0 && idx < 9 && r[0] != 0.0f) atomicAdd(&sm.g[q][idx], r[0]);
+      }
+    }
+    __syncthreads();
+    // flush this batch's per-point sums (one add per value per tile)
+    for (int q = tid; q < (int)cnt; q += NT) {
+      float *g = a.grad_item + (long long)sm.j[q] * kGradItem;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float v = sm.g[q][k];
+        if (v != 0.f) atomicAdd(&g[k], v);
+        sm.g[q][k] = 0.f;
+      }
+    }
+    __syncthreads();
+    hi = lo;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // pass 2: chain to 3D parameters
 // ---------------------------------------------------------------------------
@@ -533,7 +758,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(PBwdArgs a) {
 
 template <int B>
 static void launch_rb(const BwdArgs &a, bool fov, bool mv, long long tiles, cudaStream_t s) {
-  if (!fov) k_render_bwd<B, false, false><<<(unsigned)tiles, B * B, 0, s>>>(a);
+  if (!fov) k_render_bwd_plain<B><<<(unsigned)tiles, B * B / 2, 0, s>>>(a);
   else if (!mv) k_render_bwd<B, true, false><<<(unsigned)tiles, B * B, 0, s>>>(a);
   else k_render_bwd<B, true, true><<<(unsigned)tiles, B * B, 0, s>>>(a);
 }
