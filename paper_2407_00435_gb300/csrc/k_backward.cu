@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd_plain(BwdArgs a) {
         sm.shape[q] = shp;
         sm.col[q] = col;
         sm.j[q] = j;
-        sm.op[q] = a.opac[a.rec_gid[j]];
+        sm.op[q] = 1.0f / a.opac[a.rec_gid[j]];   // reciprocal opacity
         uint32_t msk = warp_mask_exact<B, 2>(mx, my, shp, col.w);
 #pragma unroll
         for (int w = 0; w < NW; ++w)
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd_plain(BwdArgs a) {
       const int pos = base + q;
       const float4 ea = sm.ea[q], eb = sm.eb[q], c = sm.col[q], shp = sm.shape[q];
       const float2 mu = sm.mean[q];
-      const float o = sm.op[q];
+      const float io = sm.op[q];
       float v[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) v[k] = 0.0f;
@@ -418,14 +418,14 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd_plain(BwdArgs a) {
         const float sq = eval_s(px, py[k], ea, eb, t1, t2);
         if (!(sq <= eb.z)) continue;
         const float al = alpha_of(__fsub_rn(c.w, sq));
-        const float om = 1.0f - al;
-        const float Tb = S.T / om;
+        const float rom = 1.0f / (1.0f - al);
+        const float Tb = S.T * rom;
         const float w = al * Tb;
         v[6] += w * S.gr;
         v[7] += w * S.gg;
         v[8] += w * S.gb;
-        const float dal = S.gr * (Tb * c.x - S.Sr / om) + S.gg * (Tb * c.y - S.Sg / om) +
-                          S.gb * (Tb * c.z - S.Sb / om);
+        const float dal = S.gr * (Tb * c.x - S.Sr * rom) + S.gg * (Tb * c.y - S.Sg * rom) +
+                          S.gb * (Tb * c.z - S.Sb * rom);
         S.Sr = fmaf(w, c.x, S.Sr);
         S.Sg = fmaf(w, c.y, S.Sg);
         S.Sb = fmaf(w, c.z, S.Sb);
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd_plain(BwdArgs a) {
         if (al < kAlphaMax) {
           const float dpow = dal * al;
           const float dx = px - mu.x, dy = py[k] - mu.y;
-          v[5] += dpow / o;
+          v[5] += dpow * io;
           // Q d = (w1 t1 + w2 t2) / kWhiten^2, d = pixel - mean
           v[0] += dpow * (shp.x * t1 + shp.z * t2) * inv;
           v[1] += dpow * (shp.y * t1 + shp.w * t2) * inv;
