@@ -60,10 +60,25 @@ struct BAcc {
   int last;
 };
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sums of nine per-lane values over the warp by reduce-scatter: each
+// halving step keeps half of the values and adds the partner's copy of them
+// (16 shuffles in all); lanes 2i and 2i + 1 end with the total of value i,
+// which is returned (value index lane >> 1; lanes >= 18 return 0).
+__device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int lane) {
+  float r[16];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int k = 0; k < 16; ++k) r[k] = k < 9 ? v[k] : 0.0f;
+#pragma unroll
+  for (int off = 16, h = 8; off >= 2; off >>= 1, h >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? r[i] : r[i + h];
+      const float keep = up ? r[i + h] : r[i];
+      r[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return r[0] + __shfl_xor_sync(0xffffffffu, r[0], 1);
 }
 
 template <int B, bool FOV, bool MV>
@@ -193,12 +208,12 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
         const float r2 = own ? __fsub_rn(c.w, kLog2AlphaMin) : eb.z;
         if (!(sq <= r2)) continue;
         const float al = alpha_of(__fsub_rn(c.w, sq));
-        const float om = 1.0f - al;
-        const float Tb = S.T / om;
+        const float rom = 1.0f / (1.0f - al);
+        const float Tb = S.T * rom;
         const float w = al * Tb;
         const float dcr = w * S.gr, dcg = w * S.gg, dcb = w * S.gb;
-        const float dal = S.gr * (Tb * c.x - S.Sr / om) + S.gg * (Tb * c.y - S.Sg / om) +
-                          S.gb * (Tb * c.z - S.Sb / om);
+        const float dal = S.gr * (Tb * c.x - S.Sr * rom) + S.gg * (Tb * c.y - S.Sg * rom) +
+                          S.gb * (Tb * c.z - S.Sb * rom);
         S.Sr = fmaf(w, c.x, S.Sr);
         S.Sg = fmaf(w, c.y, S.Sg);
         S.Sb = fmaf(w, c.z, S.Sb);
@@ -231,14 +246,10 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(BwdArgs a) {
                                                     gqb != 0.f || gqc != 0.f || gop != 0.f ||
                                                     gcr != 0.f || gcg != 0.f || gcb != 0.f);
       if (any) {
-        float v[9] = {gmx, gmy, gqa, gqb, gqc, gop, gcr, gcg, gcb};
-#pragma unroll
-        for (int k = 0; k < 9; ++k) v[k] = warp_sum(v[k]);
-        if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < 9; ++k)
-            if (v[k] != 0.f) atomicAdd(&s_g[q][k], v[k]);
-        }
+        const float v[9] = {gmx, gmy, gqa, gqb, gqc, gop, gcr, gcg, gcb};
+        const float tot = warp_reduce_scatter9(v, lane);
+        const int idx = lane >> 1;
+        if ((lane & 1) == 0 && idx < 9 && tot != 0.f) atomicAdd(&s_g[q][idx], tot);
       }
     }
     __syncthreads();
@@ -446,24 +457,9 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd_plain(BwdArgs a) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) nz = nz || v[k] != 0.0f;
       if (__any_sync(0xffffffffu, nz)) {
-        // reduce-scatter: each halving step keeps half of the values and
-        // adds the partner's copy of them; lanes 2i, 2i + 1 end with total i
-        float r[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) r[k] = k < 9 ? v[k] : 0.0f;
-#pragma unroll
-        for (int off = 16, h = 8; off >= 2; off >>= 1, h >>= 1) {
-          const bool up = (lane & off) != 0;
-#pragma unroll
-          for (int i = 0; i < h; ++i) {
-            const float send = up ? r[i] : r[i + h];
-            const float keep = up ? r[i + h] : r[i];
-            r[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-          }
-        }
-        r[0] += __shfl_xor_sync(0xffffffffu, r[0], 1);
+        const float tot = warp_reduce_scatter9(v, lane);
         const int idx = lane >> 1;
-        if ((lane & 1) == 0 && idx < 9 && r[0] != 0.0f) atomicAdd(&sm.g[q][idx], r[0]);
+        if ((lane & 1) == 0 && idx < 9 && tot != 0.0f) atomicAdd(&sm.g[q][idx], tot);
       }
     }
     __syncthreads();
