@@ -76,12 +76,11 @@ struct Hdr {
   unsigned long long n_nonfinite;
   unsigned long long n_evals;     // (pixel, point) evaluations of the last stats render
   unsigned long long n_blends;    // blends of the last stats render
-  uint32_t ticket[32];            // work tickets (projection)
   uint32_t sel_depth;             // buffer holding the sorted depth order (0 = A)
   uint32_t sel_pair;              // buffer holding the sorted pairs (0 = A)
   uint32_t skip[8];               // per-pass "digit constant" flags
   uint32_t big_count;             // items queued for the large-item emit
-  uint32_t big_ticket;            // next queued item to expand
+  uint32_t pad2;
   uint32_t hist[2][4][256];       // digit histograms: [sort][pass][digit]
   unsigned long long queue;       // next work item of the chunked render
   uint32_t n_slots;               // chunk slots requested by the chunk plan
@@ -102,10 +101,6 @@ struct ViewDev {
   int32_t row_base;      // tile rows of the views before this one
 };
 
-// Lookback flags in the top two bits of a 64-bit slot.
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagPre = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 20;   // bounded waits (about a second), then GS_ERR_TIMEOUT
 
 constexpr int kSortThreads = 256;                     // upsweep / histogram blocks

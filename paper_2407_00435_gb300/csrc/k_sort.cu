@@ -655,7 +655,7 @@ struct EmitArgs {
   long long pair_capacity;
   uint32_t *pkey, *pval;
   uint32_t *bigq;                    // queue of items with more than kBigItem tiles
-  uint32_t *big_count, *big_ticket;
+  uint32_t *big_count;
   uint32_t *hist;                    // pair sort histograms [passes][256]
   const float4 *supp;                // tight support records, or null (whole rectangle)
   const float2 *supp2;
@@ -1027,8 +1027,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.status = &hdr->status;
   ea.bigq = region<uint32_t>(p, ws, R_BIGQ);
   ea.big_count = &hdr->big_count;
-  ea.big_ticket = &hdr->big_ticket;
-  e = cudaMemsetAsync(&hdr->big_count, 0, 2 * sizeof(uint32_t), s);
+  e = cudaMemsetAsync(&hdr->big_count, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const bool fov = ea.tile_level != nullptr;
   if (fov && tight) {
