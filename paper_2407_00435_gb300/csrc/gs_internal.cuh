@@ -151,6 +151,9 @@ inline T *region(const gs_plan *p, void *ws, int r) {
 cudaError_t launch_views(const gs_plan *p, void *ws, cudaStream_t s);
 cudaError_t launch_tile_levels(const gs_plan *p, void *ws, cudaStream_t s);
 cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s);
+// Tile pairs of every visible item (reads the projection's records; run by
+// gs_bin_sort beside the depth sort, which does not need them)
+cudaError_t launch_count_pairs(const gs_plan *p, void *ws, cudaStream_t s);
 cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s);
 cudaError_t launch_render(const gs_plan *p, void *ws, bool fov, const float bg[3],
                           float *rgb, float *T, int32_t *last, uint32_t *stats,

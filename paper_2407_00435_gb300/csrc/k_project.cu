@@ -868,8 +868,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
   }
 }
 
-cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
-  if (p->n == 0) return cudaSuccess;
+static ProjArgs make_proj_args(const gs_plan *p, void *ws) {
   ProjArgs a;
   a.n = p->n;
   a.V = p->V;
@@ -905,6 +904,12 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
   a.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
   a.opacity_lv = p->has_fov ? p->fov.opacity_lv : nullptr;
   a.n_opacity_lv = a.opacity_lv ? p->fov.n_levels - 1 : 0;
+  return a;
+}
+
+cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
+  if (p->n == 0) return cudaSuccess;
+  const ProjArgs a = make_proj_args(p, ws);
   unsigned grid = (unsigned)((p->n + kProjThreads - 1) / kProjThreads);
   switch (a.S) {
     case 1: k_project<1><<<grid, kProjThreads, 0, s>>>(a); break;
@@ -912,6 +917,12 @@ cudaError_t launch_project(const gs_plan *p, void *ws, cudaStream_t s) {
     case 9: k_project<9><<<grid, kProjThreads, 0, s>>>(a); break;
     default: k_project<16><<<grid, kProjThreads, 0, s>>>(a); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_pairs(const gs_plan *p, void *ws, cudaStream_t s) {
+  if (p->n == 0) return cudaSuccess;
+  const ProjArgs a = make_proj_args(p, ws);
   const long long slots = p->n * p->V;
   const long long cb = (slots + kCountThreads - 1) / kCountThreads;
   k_count_pairs<<<(unsigned)(cb < 65535 ? cb : 65535), kCountThreads, 0, s>>>(a);

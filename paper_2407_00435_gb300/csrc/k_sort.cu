@@ -934,6 +934,34 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *key_a, const uin
   }
 }
 
+// A side stream per device on which the pair count runs while the depth
+// sort runs on the caller's stream (the count's records are first read by
+// the pair offsets, the sort's by nothing the count does).  Fork and join
+// are events enqueued under one lock, so concurrent callers cannot
+// interleave them; both are capturable into a CUDA graph.
+struct SideStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream g_side[64];
+static std::mutex g_side_mu;
+
+static cudaError_t side_stream(int dev, SideStream *&out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  SideStream &ss = g_side[dev];
+  if (!ss.st) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ss.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  out = &ss;
+  return cudaSuccess;
+}
+
+static cudaError_t depth_sort_and_count(const gs_plan *p, void *ws, const SortArgs &d,
+                                        cudaStream_t s);
+
 cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   Hdr *hdr = region<Hdr>(p, ws, R_HDR);
   cudaError_t e;
@@ -974,7 +1002,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
     const long long q = (nparts + G - 1) / G;
     d.sub = (int)(q < 1 ? 1 : (q > kSortSub ? kSortSub : q));
   }
-  e = run_sort(d, s);
+  e = depth_sort_and_count(p, ws, d, s);
   if (e != cudaSuccess) return e;
   // 2. pair offsets in depth order
   ScanArgs sa = {};
@@ -1070,6 +1098,22 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   k_ranges<<<g_stream_blocks, 256, 0, s>>>(t.keys[0], t.keys[1], &hdr->sel_pair, &hdr->n_pairs,
                                          p->max_pairs, p->tiles_total, ranges, &hdr->status);
   return cudaGetLastError();
+}
+
+static cudaError_t depth_sort_and_count(const gs_plan *p, void *ws, const SortArgs &d,
+                                        cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  SideStream *ss = nullptr;
+  if ((e = side_stream(dev, ss)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(ss->fork, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(ss->st, ss->fork, 0)) != cudaSuccess) return e;
+  if ((e = launch_count_pairs(p, ws, ss->st)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(ss->join, ss->st)) != cudaSuccess) return e;
+  if ((e = run_sort(d, s)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s, ss->join, 0);
 }
 
 // ---- sort of caller keys with their indices (pruning by CE) --------------
