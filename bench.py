@@ -414,6 +414,9 @@ def extra_foveated(torch, gs, synth, flush, steps):
     of = rf.alloc_outputs(fov=True)
     rp = gs.Renderer(wl.scene.n, 3, wl.cams, tight=True)
     cp = rp.fit(sc)
+    op = rp.alloc_outputs(stats=True)
+    rp.render(op)
+    _, cntp = rp.counters()
     op = rp.alloc_outputs()
 
     def fov_step():
@@ -436,6 +439,10 @@ def extra_foveated(torch, gs, synth, flush, steps):
             "gpix_per_s_foveated": round(px / ms_f / 1e6, 3),
             "pairs_foveated": int(cf["n_pairs"]), "pairs_plain": int(cp["n_pairs"]),
             "blends_per_s_foveated": round(int(cntf["n_blends"]) * 1000 / ms_f, 1),
+            "per_pixel": {"walked_foveated": round(int(cntf["n_evals"]) / px, 1),
+                          "blended_foveated": round(int(cntf["n_blends"]) / px, 1),
+                          "walked_plain": round(int(cntp["n_evals"]) / px, 1),
+                          "blended_plain": round(int(cntp["n_blends"]) / px, 1)},
             "frame": "2 eyes"}
 
 
