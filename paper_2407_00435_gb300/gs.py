@@ -250,6 +250,12 @@ class Renderer:
 
     ``scene_t``: dict of device tensors means/scales/quats/opac/sh;
     ``cams``: (V, 20) packed float32 cameras (numpy).
+    Options map to ``gs_config``: ``tile`` 16 or 8; ``foveated`` reserves the
+    foveation state; ``backward`` the gradient scratch; ``tight`` the
+    opacity-aware tight support (same image, fewer pairs); ``multi_model`` a
+    separate model per foveation level (implies ``foveated``); ``chunk`` /
+    ``chunk_slots`` the heavy-tile chunked render; ``radix_bits`` the pair
+    sort's digit width; ``max_pairs`` the pair capacity (``fit`` grows it).
     """
 
     def __init__(self, n, sh_degree, cams, tile=16, foveated=False, backward=False,
