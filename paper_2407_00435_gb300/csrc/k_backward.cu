@@ -2,8 +2,11 @@
 // renderer (the pruning and foveated levels of Sec. 3.4 and Sec. 4.3 are
 // obtained by training through it).
 //
-// Pass 1 (k_render_bwd): one block per tile, one pixel per thread, walking
-// the tile's list back to front from the last blended point.  With the
+// Pass 1 (k_render_bwd_plain for plain views: two pixels per thread and
+// per-warp lists of the points that reach the warp; k_render_bwd for
+// foveated views: one pixel per thread, two accumulators): one block per
+// tile, walking the tile's list back to front from the last blended point.
+// With the
 // forward's final transmittance T_N and the colour S accumulated behind a
 // point (starting at T_N bg), each blended point i gives
 //   dL/dc_i     = T_i alpha_i g
@@ -11,9 +14,9 @@
 // and, below the 0.99 clamp, dL/dopacity = dL/dalpha alpha / o and
 // dL/dpower = dL/dalpha alpha with power = -1/2 d^T Q d, d = p - mu:
 //   dL/dmu = dL/dpower Q d,   dL/dQ = -1/2 dL/dpower d d^T.
-// Contributions are summed over each warp with shuffles, then over the block
-// in shared memory, then added once per (tile, point) to a per-item
-// gradient record.
+// Contributions are summed over each warp by a reduce-scatter of shuffles,
+// then over the block in shared memory, then added once per (tile, point)
+// to a per-item gradient record.
 //
 // Pass 2 (k_project_bwd): one thread per visible item chains the 2D
 // gradients to the 3D parameters (mean, scale, rotation, opacity, SH) through
