@@ -6,9 +6,8 @@
 // per-warp lists of the points that reach the warp; k_render_bwd for
 // foveated views: one pixel per thread, two accumulators): one block per
 // tile, walking the tile's list back to front from the last blended point.
-// With the
-// forward's final transmittance T_N and the colour S accumulated behind a
-// point (starting at T_N bg), each blended point i gives
+// With the forward's final transmittance T_N and the colour S accumulated
+// behind a point (starting at T_N bg), each blended point i gives
 //   dL/dc_i     = T_i alpha_i g
 //   dL/dalpha_i = g . (T_i c_i - S / (1 - alpha_i)),   T_i = T_{i+1} / (1 - alpha_i)
 // and, below the 0.99 clamp, dL/dopacity = dL/dalpha alpha / o and
