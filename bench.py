@@ -359,7 +359,8 @@ def gpu_arm(args):
         del rr, outr, sc
         torch.cuda.empty_cache()
         steps_x = max(3, min(args.steps, 10))
-        for name, fn in (("foveated_stereo", extra_foveated), ("multi_model_fr", extra_mmfr),
+        for name, fn in (("foveated_stereo", extra_foveated),
+                         ("foveated_ce_levels", extra_foveated_ce), ("multi_model_fr", extra_mmfr),
                          ("fwd_bwd", extra_fwd_bwd),
                          ("prune_round", extra_prune), ("batched_64_views", extra_batched)):
             if args.only and name not in args.only:
@@ -444,6 +445,63 @@ def extra_foveated(torch, gs, synth, flush, steps):
                           "walked_plain": round(int(cntp["n_evals"]) / px, 1),
                           "blended_plain": round(int(cntp["n_blends"]) / px, 1)},
             "frame": "2 eyes"}
+
+
+def extra_foveated_ce(torch, gs, synth, flush, steps):
+    """The foveated stereo frame with its nested levels built as the paper
+    builds them (Sec. 3.4, 4.2): each coarser level keeps the points of the
+    finer one with the highest computational efficiency (CE maximum over the
+    two eye poses and two orbit poses, from the render's statistics; the
+    library's stable mask), in the proportions of the random levels (N, N/2,
+    N/4, N/8).  Compared with the random levels of the same scene."""
+    import numpy as np
+    wl = synth.workload(2)
+    n = wl.scene.n
+    sc = gs.scene_to_device(wl.scene)
+    rng = np.random.default_rng(2025)
+    poses = np.concatenate([wl.cams, synth.orbit_cameras(rng, 2, 4.0, [(1920, 1920)] * 2)])
+    ce = torch.zeros(n, device="cuda")
+    last = None
+    for v in range(len(poses)):
+        rv = gs.Renderer(n, 3, poses[v:v + 1], tight=True)
+        rv.fit(sc, headroom=1.05)
+        o = rv.alloc_outputs(stats=True)
+        rv.render(o)
+        gs.gs_ce_update(n, o["stats"], ce)
+        if last is not None:
+            del last
+        last = rv
+    m = torch.ones(n, dtype=torch.uint8, device="cuda")
+    for frac in (0.5, 0.75, 0.875):          # levels 2, 3, 4 keep 1/2, 1/4, 1/8
+        m += last.prune_mask(ce, frac)
+    del last
+    torch.cuda.empty_cache()
+    res = {"workload": wl.name, "levels": "CE-ranked nested subsets (N, N/2, N/4, N/8)"}
+    for name, bound in (("ce_levels", m), ("random_levels", None)):
+        f = gs.fov_to_device(wl.fov)
+        if bound is not None:
+            f["bound_m"] = bound
+        r = gs.Renderer(n, 3, wl.cams, foveated=True, tight=True)
+        c = r.fit(sc, f)
+        o = r.alloc_outputs(fov=True, stats=True)
+        r.render(o, fov=True)
+        _, cnt = r.counters()
+        out = r.alloc_outputs(fov=True)
+
+        def step():
+            r.project(sc, f)
+            r.bin_sort()
+            r.render(out, fov=True)
+
+        ms = _ms(torch, step, steps, 2, flush)
+        res[name] = {"fps": round(1000.0 / ms, 2), "pairs": int(c["n_pairs"]),
+                     "walked_per_pixel": round(int(cnt["n_evals"]) / r.P, 1),
+                     "blended_per_pixel": round(int(cnt["n_blends"]) / r.P, 1)}
+        del r, o, out
+        torch.cuda.empty_cache()
+    del sc
+    torch.cuda.empty_cache()
+    return res
 
 
 def extra_mmfr(torch, gs, synth, flush, steps):
