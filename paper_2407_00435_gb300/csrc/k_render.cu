@@ -69,7 +69,7 @@ struct Acc {
 constexpr int kMaxLv = kMvMaxLevels - 1;
 
 // Records of one batch in shared memory (structure of arrays).
-constexpr int kBatch = 256;
+constexpr int kBatch = 128;   // points per batch: one per thread (measured faster than 256)
 
 // Prefetched global record of one pair (registers).
 struct Pre {
@@ -110,7 +110,7 @@ struct ItemSm {
 template <int B, bool FOV, bool MV, bool STATS, int PX>
 struct RSmem {
   static constexpr int NT = B * B / PX;                   // threads
-  static constexpr int NB = 2 * NT < kBatch ? 2 * NT : kBatch;   // points per batch
+  static constexpr int NB = 2 * NT < kBatch ? 2 * NT : (NT > kBatch ? NT : kBatch);
   static constexpr int SPT = NB / NT;                     // points staged per thread
   static constexpr int NWS = NT / 32;                     // staging warps
   static constexpr int NW = WarpGeom<B, PX>::kWarps;
