@@ -123,6 +123,11 @@ typedef struct gs_config {
                             0 = enough for any split (capped at max(tiles + 64, 65536)).
                             Tiles that do not fit are rendered whole. */
   int64_t max_pairs;     /* capacity of tile/point pairs; 0 = 4 * N * V */
+  int32_t wait_spins;    /* polls of gs_project's bounded bulk-copy waits before they give
+                            up with GS_ERR_TIMEOUT: 0 = default (2^20 polls, about a
+                            second); < 0 = give up without polling (exercises the failure
+                            path; the frame's records are then incomplete, see gs_project) */
+  int32_t reserved;
 } gs_config;
 
 #define GS_FLAG_FOVEATED 1u  /* reserve foveation state (levels, per-level params) */
@@ -176,7 +181,11 @@ size_t gs_workspace_size(const gs_plan *plan);
 /* Projection (+ FR tile levels).  scene: device arrays; cams_dev: device
  * array of n_views gs_camera; fov: NULL for plain rendering, else the
  * foveation of every view (requires GS_FLAG_FOVEATED).  Records the scene,
- * camera and fov in the plan for the calls below.
+ * camera and fov in the plan for the calls below.  The point parameters are
+ * staged by bulk copies whose waits are bounded (gs_config.wait_spins); a
+ * wait that gives up sets GS_ERR_TIMEOUT and leaves that block's records
+ * unwritten, so a caller that sees GS_ERR_TIMEOUT from gs_get_error after
+ * gs_project must project again before gs_bin_sort.
  * Errors: GS_ERR_INVALID_ARG (NULL pointer, ws too small or unaligned,
  * n mismatch, bad fov), GS_ERR_CUDA. */
 gs_status gs_project(gs_plan *plan, void *ws, size_t ws_bytes,
@@ -267,8 +276,8 @@ gs_status gs_ws_region(const gs_plan *plan, int32_t region, size_t *offset,
 gs_status gs_sorted_pairs(const gs_plan *plan, const void *ws, cudaStream_t stream,
                           const uint32_t **pair_tile, const uint32_t **pair_item);
 
-/* Allocation-free stable radix sort of (key, value) pairs by the low
- * key_bits bits of the key (1..32): the pair sort of gs_bin_sort for
+/* Allocation-free stable radix sort of (key, value) pairs by key, keys
+ * below 2^key_bits (key_bits 1..32): the pair sort of gs_bin_sort for
  * callers that cannot allocate device memory -- code inside a memory pool
  * that must not grow, plug-ins whose host application forbids cudaMalloc
  * after start-up, real-time paths where an allocation could block -- and so
@@ -278,19 +287,30 @@ gs_status gs_sorted_pairs(const gs_plan *plan, const void *ws, cudaStream_t stre
  *   keys_out, vals_out device, n entries each, overwritten with the pairs in
  *                      key order (equal keys keep their input order)
  * Scratch is one static device array of this library, sized for at most
- * GS_STATIC_SORT_MAX_PAIRS pairs (about 9 MB, held on every GPU that loads
- * the library until the process exits).  No call allocates or frees.
- * The first call on a device looks up the array's device address (a
- * one-time set-up); make that first call before any stream capture.  All
- * calls of this process on one device share the array and it keeps the
- * last call's contents: calls that may overlap on the GPU (for example on
- * different streams) race and must be serialised by the caller.  Errors: GS_ERR_INVALID_ARG (n < 0 or
- * n > GS_STATIC_SORT_MAX_PAIRS, key_bits out of range, NULL or overlapping
- * buffers), GS_ERR_CUDA. */
+ * GS_STATIC_SORT_MAX_PAIRS pairs: 12,587,264 bytes (about 12.6 MB), held on
+ * every GPU that loads the library until the process exits.  No call
+ * allocates or frees.  The first call on a device looks up the array's
+ * device address (a one-time set-up); make that first call before any
+ * stream capture.  All calls of this process on one device share the array
+ * and it keeps the last call's contents: calls that may overlap on the GPU
+ * (for example on different streams) race and must be serialised by the
+ * caller.  A device-side failure (a bounded wait that gave up, leaving the
+ * output incomplete) is recorded in the array's status word: read it with
+ * gs_sort_pairs_static_status after the call.  Errors: GS_ERR_INVALID_ARG
+ * (n < 0 or n > GS_STATIC_SORT_MAX_PAIRS, key_bits out of range, NULL or
+ * overlapping buffers), GS_ERR_CUDA. */
 #define GS_STATIC_SORT_MAX_PAIRS (1 << 20)
 gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_t *vals_in,
                                int64_t n, int32_t key_bits, uint32_t *keys_out,
                                uint32_t *vals_out, cudaStream_t stream);
+
+/* Device status of the last gs_sort_pairs_static on the current device:
+ * synchronises `stream` (the stream of that call), writes the status word
+ * (GS_OK, or GS_ERR_TIMEOUT when a bounded wait gave up and the output is
+ * incomplete) to *host_status (host memory) and returns it.  GS_OK when no
+ * such sort ran on this device.  Allocates nothing.  Errors:
+ * GS_ERR_INVALID_ARG (NULL host_status), GS_ERR_CUDA. */
+gs_status gs_sort_pairs_static_status(uint32_t *host_status, cudaStream_t stream);
 
 /* Geometry helpers (host): total tiles and pixels of the plan's views. */
 int64_t gs_plan_tiles(const gs_plan *plan);

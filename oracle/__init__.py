@@ -77,8 +77,8 @@ def lib():
         L.orc_sh_basis.argtypes = [p, p]
         L.orc_sh_basis.restype = None
         L.orc_render.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p, p,
-                                 C.c_int64, p, p, p, p, p, p, p]
-        L.orc_render_brute.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p, p, p,
+                                 C.c_int64, p, p, p, p, p, p, p, p]
+        L.orc_render_brute.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p, p,
                                        p, p, p]
         L.orc_backward.argtypes = [C.c_int, p, p, p, p, p, C.c_int, C.c_int, p, C.c_int,
                                    p, p, p, p, p, p, p, p, p, p, p, p]
@@ -262,9 +262,10 @@ class Image:
     rgb: np.ndarray      # (P, 3)
     T: np.ndarray        # (P, 2)
     last: np.ndarray     # (P, 2)
-    margin: np.ndarray   # (P,)
+    margin: np.ndarray   # (P,) smallest relative margin of any decision
     wband: np.ndarray    # (P,)
-    ambT: np.ndarray     # (P,)
+    ambB: np.ndarray     # (P,) what flipping the ambiguous decisions can change
+    amb: np.ndarray      # (P,) bool: a decision inside its FP32 uncertainty window
     stats: np.ndarray | None  # (4, N)
 
 
@@ -284,7 +285,8 @@ def render(scene, cams, tile, bins: Bins, fov: FovArrays | None = None, bg=(0, 0
     last = np.zeros((P, 2), np.int32)
     margin = np.zeros(P)
     wband = np.zeros(P)
-    ambT = np.zeros(P)
+    ambB = np.zeros(P)
+    amb = np.zeros(P, np.uint8)
     st = np.zeros((4, n), np.uint32) if (stats and pix is None) else None
     fs = fov.struct() if fov is not None else None
     bgv = _c64(bg)
@@ -292,16 +294,19 @@ def render(scene, cams, tile, bins: Bins, fov: FovArrays | None = None, bg=(0, 0
                           bins.vals.ctypes.data, bins.ranges.ctypes.data,
                           C.addressof(fs) if fs is not None else None, bgv.ctypes.data,
                           _ptr(pix_arr), P, rgb.ctypes.data, T.ctypes.data, last.ctypes.data,
-                          margin.ctypes.data, wband.ctypes.data, ambT.ctypes.data, _ptr(st))
+                          margin.ctypes.data, wband.ctypes.data, ambB.ctypes.data,
+                          amb.ctypes.data, _ptr(st))
     if rc != 0:
         raise RuntimeError(f"orc_render failed: {rc}")
-    return Image(rgb, T, last, margin, wband, ambT, st)
+    return Image(rgb, T, last, margin, wband, ambB, amb.astype(bool), st)
 
 
 def render_brute(scene, cams, tile, fov: FovArrays | None = None, bg=(0, 0, 0)):
+    """Per-pixel definition of Eq. 1 (no tile lists, no foveation tile
+    filter).  Returns (rgb, T, last_item): last_item is the item v*N + i of
+    the last blended point of each accumulator, -1 if none."""
     n, V = scene.n, len(cams)
     vis, dbits, rect = keyed_project(scene, cams, tile)
-    tl = tile_levels(cams, tile, fov) if fov is not None else None
     vp = project_values(scene, cams, vis)
     cs = cams_struct(cams)
     W, H, _, _ = view_dims(cams, tile)
@@ -313,7 +318,7 @@ def render_brute(scene, cams, tile, fov: FovArrays | None = None, bg=(0, 0, 0)):
     op = _c64(scene.opac)
     bgv = _c64(bg)
     rc = lib().orc_render_brute(n, V, C.addressof(cs), tile, vis.ctypes.data, dbits.ctypes.data,
-                                rect.ctypes.data, _ptr(tl), vp.ctypes.data, op.ctypes.data,
+                                rect.ctypes.data, vp.ctypes.data, op.ctypes.data,
                                 C.addressof(fs) if fs is not None else None, bgv.ctypes.data,
                                 rgb.ctypes.data, T.ctypes.data, last.ctypes.data)
     if rc != 0:

@@ -720,7 +720,10 @@ typedef struct {
   double C[3], T;
   int32_t last;     /* list position of the last blended point, -1 if none */
   double margin;
-  double amb_T;     /* largest T before a decision within AMB_REL of its threshold */
+  int amb;          /* some decision lies inside its uncertainty window */
+  double amb_floor; /* sum of T over ambiguous alpha-floor decisions */
+  double amb_stop;  /* T at an ambiguous stop decision (0 if none) */
+  double cmax;      /* largest colour channel of the points taking part */
   int64_t dom_item; /* item with the largest T alpha (first maximum) */
   double dom_w;
 } acc_t;
@@ -752,11 +755,30 @@ static double rel_margin(double a, double thr) {
   return fabs(a / thr - 1.0);
 }
 
-/* Decisions closer than this (relative) to their threshold are "ambiguous":
- * a finite-precision evaluation may take the other branch.  A flipped
- * decision at transmittance T changes the pixel by at most about T times
- * twice the largest colour, which the tests use as the bound. */
-#define AMB_REL 1e-3
+/* Decision ambiguity (test bookkeeping, not part of Eq. 1).  The GPU takes
+ * the alpha-floor and stop decisions in FP32; near a threshold it may take
+ * the other branch.  Error model of its FP32 evaluation:
+ *   alpha: log2(alpha) = log2(o) - |t|^2 with t the whitened offset of the
+ *     pixel (|t|^2 <= 8 at the floor).  Rounding of t (FMAs over tile-local
+ *     coordinates <= 16 px, whitening rows of relative error ~1e-6) and of
+ *     log2(o) bound the absolute error of log2(alpha) by ~5e-5, i.e. a
+ *     relative error of alpha below ALPHA_REL_ERR = 4e-5; ex2.approx adds
+ *     ~2e-7.
+ *   T: each blend multiplies by (1 - alpha) rounded twice, so T's relative
+ *     error grows per blend by 2 u + ALPHA_REL_ERR alpha / (1 - alpha)
+ *     (u = 2^-24; a clamped alpha is 0.99 in FP32, 1e-6 off in 1 - alpha).
+ * An alpha-floor decision is ambiguous when alpha lies within AMB_FLOOR
+ * (relative) of 1/255; a stop decision when T (1 - alpha) lies within
+ * AMB_FLOOR + AMB_SAFE times T's error bound of 1e-4.  Flipping a floor
+ * decision at transmittance T changes the pixel by at most 2 T c_max / 255
+ * (the point's own T alpha c plus the factor (1 - alpha) on what follows);
+ * flipping the stop decision by at most T c_max (everything from there on).
+ * A flipped floor decision moves the later T by alpha, which widens the
+ * later stop windows. */
+#define ALPHA_REL_ERR 4e-5
+#define AMB_FLOOR 1e-4
+#define AMB_SAFE 2.5
+#define U32 5.9604644775390625e-8
 
 /* Whether point i takes part at level lvl (see orc_fov.disjoint).  Without
  * foveation every point takes part. */
@@ -777,9 +799,13 @@ static void composite(int n, const double *vp, const double *opac,
   acc->T = 1.0;
   acc->last = -1;
   acc->margin = INFINITY;
-  acc->amb_T = 0.0;
+  acc->amb = 0;
+  acc->amb_floor = 0.0;
+  acc->amb_stop = 0.0;
+  acc->cmax = 0.0;
   acc->dom_item = -1;
   acc->dom_w = -1.0;
+  double errT = 0.0;  /* bound on the relative error of the FP32 T */
   for (int64_t k = s; k < e; ++k) {
     uint32_t id = vals[k];
     int i = (int)(id % (uint32_t)n);
@@ -789,15 +815,24 @@ static void composite(int n, const double *vp, const double *opac,
     double power = -0.5 * (pv[ORC_CA] * dx * dx + pv[ORC_CC] * dy * dy) - pv[ORC_CB] * dx * dy;
     double o = level_opacity(fov, opac, n, i, lvl);
     double alpha = o * exp(power);
-    if (alpha > ALPHA_MAX) alpha = ALPHA_MAX;
+    int clamped = alpha > ALPHA_MAX;
+    if (clamped) alpha = ALPHA_MAX;
     double m = rel_margin(alpha, ALPHA_MIN);
     if (m < acc->margin) acc->margin = m;
-    if (m < AMB_REL && acc->T > acc->amb_T) acc->amb_T = acc->T;
+    if (m < AMB_FLOOR) {
+      acc->amb = 1;
+      acc->amb_floor += acc->T;
+      errT += alpha; /* the other branch scales the later T by 1 - alpha */
+    }
     if (alpha < ALPHA_MIN) continue;
     double Tn = acc->T * (1.0 - alpha);
+    errT += 2.0 * U32 + (clamped ? 1e-6 : ALPHA_REL_ERR * alpha / (1.0 - alpha));
     m = rel_margin(Tn, T_MIN);
     if (m < acc->margin) acc->margin = m;
-    if (m < AMB_REL && acc->T > acc->amb_T) acc->amb_T = acc->T;
+    if (m < AMB_FLOOR + AMB_SAFE * errT) {
+      acc->amb = 1;
+      if (acc->T > acc->amb_stop) acc->amb_stop = acc->T;
+    }
     if (Tn < T_MIN) break;
     double col[3];
     level_colour(fov, pv, n, i, lvl, col, NULL);
@@ -807,6 +842,29 @@ static void composite(int n, const double *vp, const double *opac,
     acc->T = Tn;
     acc->last = (int32_t)(k - s);
   }
+  if (acc->amb) {
+    /* largest colour any point of the list contributes at this level: bounds
+     * what a flipped decision adds or removes */
+    for (int64_t k = s; k < e; ++k) {
+      uint32_t id = vals[k];
+      int i = (int)(id % (uint32_t)n);
+      if (!takes_part(fov, i, lvl)) continue;
+      double col[3];
+      level_colour(fov, &vp[(int64_t)id * ORC_NVAL], n, i, lvl, col, NULL);
+      for (int ch = 0; ch < 3; ++ch)
+        if (col[ch] > acc->cmax) acc->cmax = col[ch];
+    }
+  }
+}
+
+/* What flipping the ambiguous decisions of an accumulator can change in its
+ * colour (see the error model above); bg enters like a colour. */
+static double amb_bound(const acc_t *a, const double bg[3]) {
+  if (!a->amb) return 0.0;
+  double c = a->cmax;
+  for (int ch = 0; ch < 3; ++ch)
+    if (bg[ch] > c) c = bg[ch];
+  return (2.0 * ALPHA_MIN * (1.0 + AMB_FLOOR)) * c * a->amb_floor + c * a->amb_stop;
 }
 
 static int find_view(int V, const orc_cam *cams, int64_t gp, int *x, int *y) {
@@ -830,14 +888,15 @@ static void shade_pixel(int n, int V, const orc_cam *cams, const double *vp,
                         int64_t e, const orc_fov *fov, const double bg[3],
                         int v, int x, int y, double *rgb, double *T,
                         int32_t *last, double *margin, double *wband,
-                        double *ambT, acc_t *outA) {
+                        double *ambB, uint8_t *amb, acc_t *outA) {
   (void)V;
   fov_px fp = pixel_level(&cams[v], fov, v, x, y);
   double px = x + 0.5, py = y + 0.5;
   acc_t A, B;
   composite(n, vp, opac, vals, s, e, fov, fp.level, px, py, &A);
   double mg = A.margin;
-  double at = fp.in_band ? fp.w * A.amb_T : A.amb_T;
+  int am = A.amb;
+  double ab = (fp.in_band ? fp.w : 1.0) * amb_bound(&A, bg);
   double out[3];
   for (int ch = 0; ch < 3; ++ch) out[ch] = A.C[ch] + A.T * bg[ch];
   T[0] = A.T; last[0] = A.last;
@@ -845,7 +904,8 @@ static void shade_pixel(int n, int V, const orc_cam *cams, const double *vp,
   if (fp.in_band) {
     composite(n, vp, opac, vals, s, e, fov, fp.level - 1, px, py, &B);
     if (B.margin < mg) mg = B.margin;
-    if ((1.0 - fp.w) * B.amb_T > at) at = (1.0 - fp.w) * B.amb_T;
+    am |= B.amb;
+    ab += (1.0 - fp.w) * amb_bound(&B, bg);
     for (int ch = 0; ch < 3; ++ch)
       out[ch] = fp.w * out[ch] + (1.0 - fp.w) * (B.C[ch] + B.T * bg[ch]);
     T[1] = B.T; last[1] = B.last;
@@ -853,7 +913,8 @@ static void shade_pixel(int n, int V, const orc_cam *cams, const double *vp,
   for (int ch = 0; ch < 3; ++ch) rgb[ch] = out[ch];
   if (margin) *margin = mg;
   if (wband) *wband = fp.w;
-  if (ambT) *ambT = at;
+  if (ambB) *ambB = ab;
+  if (amb) *amb = (uint8_t)am;
   if (outA) *outA = A;
 }
 
@@ -861,8 +922,8 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
                const double *vp, const double *opac, const uint32_t *vals,
                const uint32_t *ranges, const orc_fov *fov, const double bg[3],
                const int64_t *pix, int64_t npix, double *rgb, double *T,
-               int32_t *last, double *margin, double *wband, double *ambT,
-               uint32_t *stats) {
+               int32_t *last, double *margin, double *wband, double *ambB,
+               uint8_t *amb, uint32_t *stats) {
   if (pix) {
     for (int64_t q = 0; q < npix; ++q) {
       int x, y;
@@ -874,7 +935,7 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
       shade_pixel(n, V, cams, vp, opac, vals, ranges[2 * gt], ranges[2 * gt + 1], fov,
                   bg, v, x, y, &rgb[3 * q], &T[2 * q], &last[2 * q],
                   margin ? &margin[q] : NULL, wband ? &wband[q] : NULL,
-                  ambT ? &ambT[q] : NULL, NULL);
+                  ambB ? &ambB[q] : NULL, amb ? &amb[q] : NULL, NULL);
     }
     return 0;
   }
@@ -910,7 +971,7 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
             shade_pixel(n, V, cams, vp, opac, vals, s, e, fov, bg, v, x, y,
                         &rgb[3 * q], &T[2 * q], &last[2 * q],
                         margin ? &margin[q] : NULL, wband ? &wband[q] : NULL,
-                        ambT ? &ambT[q] : NULL, &A);
+                        ambB ? &ambB[q] : NULL, amb ? &amb[q] : NULL, &A);
             if (stats && A.last >= 0) {
               /* re-walk to mark blended points (statistics of accumulator A) */
               fov_px fp = pixel_level(c, fov, v, x, y);
@@ -958,10 +1019,9 @@ static int cmp_bf(const void *pa, const void *pb) {
 
 int orc_render_brute(int n, int V, const orc_cam *cams, int tile,
                      const uint8_t *vis, const uint32_t *depth_bits,
-                     const int32_t *rect, const uint8_t *tile_level,
-                     const double *vp, const double *opac, const orc_fov *fov,
-                     const double bg[3], double *rgb, double *T,
-                     int32_t *last) {
+                     const int32_t *rect, const double *vp, const double *opac,
+                     const orc_fov *fov, const double bg[3], double *rgb,
+                     double *T, int32_t *last) {
   bf_t *lst = (bf_t *)malloc(sizeof(bf_t) * (size_t)(n > 0 ? n : 1));
   uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
   if (!lst || !ids) { free(lst); free(ids); return -1; }
@@ -969,19 +1029,16 @@ int orc_render_brute(int n, int V, const orc_cam *cams, int tile,
     const orc_cam *c = &cams[v];
     int tx, ty;
     view_tiles(c, tile, &tx, &ty);
-    int64_t tb = tile_base(V, cams, tile, v);
     int64_t pb0 = pix_base(cams, v);
     for (int y = 0; y < c->height; ++y)
       for (int x = 0; x < c->width; ++x) {
         int bx = x / tile, by = y / tile;
-        int64_t gt = tb + (int64_t)by * tx + bx;
         int cnt = 0;
         for (int i = 0; i < n; ++i) {
           int64_t id = (int64_t)v * n + i;
           if (vis[id] != 1) continue;
           const int32_t *rc = &rect[4 * id];
           if (bx < rc[0] || bx > rc[1] || by < rc[2] || by > rc[3]) continue;
-          if (tile_level && fov && fov->bound_m && tile_level[gt] > fov->bound_m[i]) continue;
           lst[cnt].dbits = depth_bits[id];
           lst[cnt].id = (uint32_t)id;
           ++cnt;
@@ -990,7 +1047,10 @@ int orc_render_brute(int n, int V, const orc_cam *cams, int tile,
         for (int k = 0; k < cnt; ++k) ids[k] = lst[k].id;
         int64_t q = pb0 + (int64_t)y * c->width + x;
         shade_pixel(n, V, cams, vp, opac, ids, 0, cnt, fov, bg, v, x, y,
-                    &rgb[3 * q], &T[2 * q], &last[2 * q], NULL, NULL, NULL, NULL);
+                    &rgb[3 * q], &T[2 * q], &last[2 * q], NULL, NULL, NULL, NULL, NULL);
+        /* list positions of this per-pixel list -> items */
+        for (int a = 0; a < 2; ++a)
+          if (last[2 * q + a] >= 0) last[2 * q + a] = (int32_t)ids[last[2 * q + a]];
       }
   }
   free(lst);

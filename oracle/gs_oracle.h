@@ -128,12 +128,13 @@ void orc_sh_basis(const double dir[3], double Y[16]);
  *              last blended point for accumulator A (the pixel's own level)
  *              and B (the next better level, only inside a band; else 1,-1)
  *   margin   : (npix,)   smallest relative distance of any alpha-floor or
- *              early-stop decision from its threshold (ambiguity flag)
+ *              early-stop decision from its threshold
  *   wband    : (npix,)   blend weight w of accumulator A (1 outside bands)
- *   ambT     : (npix,)   largest transmittance (weighted by the blend
- *              weight) at which a decision lies within 1e-3 (relative) of
- *              its threshold; 0 if none.  Bounds what a flipped decision
- *              can change.
+ *   ambB     : (npix,)   bound on what flipping the pixel's ambiguous
+ *              decisions can change in any channel (0 if none); see the
+ *              error model beside composite() in gs_oracle.c
+ *   amb      : (npix,)   1 if some alpha-floor or stop decision lies inside
+ *              the uncertainty window of an FP32 evaluation
  *   stats    : (4,N) uint32 or NULL: tiles_touched, tiles_used,
  *              pixels_blended, pixels_dominated (accumulator A); only
  *              meaningful when pix == NULL (the whole batch).
@@ -143,19 +144,21 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
                const uint32_t *vals, const uint32_t *ranges,
                const orc_fov *fov, const double bg[3],
                const int64_t *pix, int64_t npix, double *rgb, double *T,
-               int32_t *last, double *margin, double *wband, double *ambT,
-               uint32_t *stats);
+               int32_t *last, double *margin, double *wband, double *ambB,
+               uint8_t *amb, uint32_t *stats);
 
-/* Brute force: same output as orc_render for all pixels, but each pixel
- * scans every point (no tile lists): support = visible and the pixel's tile
- * inside the point's rectangle (and kept by the filter); order = (FP32
- * depth, point index). */
+/* Brute force of Eq. 1 by its per-pixel definition: each pixel scans every
+ * point (no tile lists, no foveation tile filter).  Support = visible and the
+ * pixel's tile inside the point's rectangle; order = (FP32 depth, point
+ * index); the pixel's level decides which points take part.  Same rgb and T
+ * as orc_render; last holds the ITEM (v*N + i) of the last blended point of
+ * each accumulator (-1 if none) instead of a list position. */
 int orc_render_brute(int n, int V, const orc_cam *cams, int tile,
                      const uint8_t *vis, const uint32_t *depth_bits,
-                     const int32_t *rect, const uint8_t *tile_level,
-                     const double *vals_proj, const double *opac,
-                     const orc_fov *fov, const double bg[3], double *rgb,
-                     double *T, int32_t *last);
+                     const int32_t *rect, const double *vals_proj,
+                     const double *opac, const orc_fov *fov,
+                     const double bg[3], double *rgb, double *T,
+                     int32_t *last);
 
 /* Analytic FP64 gradient of L = sum(dL_drgb * rgb) with respect to the scene
  * parameters, holding the binning fixed.  Output arrays are overwritten.

@@ -57,6 +57,7 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
       ~(GS_FLAG_FOVEATED | GS_FLAG_BACKWARD | GS_FLAG_TIGHT | GS_FLAG_MULTI_MODEL))
     return GS_ERR_INVALID_ARG;
   p->flags = (uint32_t)c.flags;
+  p->wait_spins = c.wait_spins;
   long long tiles = 0, pixels = 0, rows = 0;
   for (int v = 0; v < V; ++v) {
     const gs_camera &cam = cams[v];

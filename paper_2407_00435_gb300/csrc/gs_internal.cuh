@@ -127,6 +127,7 @@ struct gs_plan {
   int32_t radix_bits;     // requested digit width of the pair sort (0 = balanced)
   int64_t chunk_cap;      // chunk slots of the chunked render (0 = whole tiles only)
   int32_t sort_blocks;    // rows of the sort's block table (grid upper bound)
+  int32_t wait_spins;     // gs_config.wait_spins (projection staging waits)
   int32_t last_fov;       // last render was foveated
   size_t off[gs::R_COUNT_];
   size_t bytes[gs::R_COUNT_];

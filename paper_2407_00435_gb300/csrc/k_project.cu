@@ -207,6 +207,7 @@ struct ProjArgs {
   const uint32_t *level_rows;    // columns kept by the foveation filter, per row and level
   const float *opacity_lv;      // (L-1, N) level opacities the support must cover, or null
   int n_opacity_lv;
+  int spins;                    // polls of the staging wait before it gives up
 };
 
 struct Keyed {
@@ -793,10 +794,10 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
       bulk_g2s(&sm.qraw[0], a.quats + row0 * 4, bq, &s_bar);
       bulk_g2s(&sm.op[0], a.opac + row0, bo, &s_bar);
     }
-    const bool landed = mbar_wait_bounded(&s_bar, 0);
+    const bool landed = mbar_wait_bounded(&s_bar, 0, a.spins);
     if (__syncthreads_or(!landed)) {
-      // give up together: record it, wait (bounded) for the copies still in
-      // flight into this block's shared memory, then leave
+      // give up together: record it, wait (bounded, the full limit) for the
+      // copies still in flight into this block's shared memory, then leave
       if (tid == 0) set_status(&a.hdr->status, GS_ERR_TIMEOUT);
       mbar_wait_bounded(&s_bar, 0);
       return;
@@ -904,6 +905,7 @@ static ProjArgs make_proj_args(const gs_plan *p, void *ws) {
   a.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
   a.opacity_lv = p->has_fov ? p->fov.opacity_lv : nullptr;
   a.n_opacity_lv = a.opacity_lv ? p->fov.n_levels - 1 : 0;
+  a.spins = p->wait_spins == 0 ? kSpinLimit : (p->wait_spins < 0 ? 0 : p->wait_spins);
   return a;
 }
 

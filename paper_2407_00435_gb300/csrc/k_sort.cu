@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstddef>
 #include <mutex>
 
 #include "gs_internal.cuh"
@@ -1156,7 +1157,8 @@ cudaError_t launch_sort_indices(const gs_plan *p, void *ws, const uint32_t *keys
 // them gs_sort_pairs_static sorts caller-provided buffers using a fixed
 // scratch array that lives in this file as a static device variable, sized
 // for at most GS_STATIC_SORT_MAX_PAIRS pairs.  Every GPU that loads the
-// library holds that array (about 9 MB) until the process exits.
+// library holds that array (12,587,264 bytes: a 4,352-byte header, 8 MiB of
+// temporary keys and values, a 4 MiB block table) until the process exits.
 // --------------------------------------------------------------------------
 namespace {
 
@@ -1175,6 +1177,7 @@ constexpr size_t kStaticHdrBytes = (sizeof(StaticHdr) + 255) & ~size_t(255);
 constexpr size_t kStaticTmpBytes = 2 * sizeof(uint32_t) * (size_t)kStaticMax;   // keys + values
 constexpr size_t kStaticBsumBytes = 256 * sizeof(uint32_t) * kSortSub * (size_t)kStaticBlocks;
 constexpr size_t kStaticBytes = kStaticHdrBytes + kStaticTmpBytes + kStaticBsumBytes;
+static_assert(kStaticBytes == 12587264, "the documented footprint of the static scratch");
 
 // The scratch itself.  Host code must not take this symbol's address
 // directly (that would be a host-side stand-in); it asks the runtime for the
@@ -1254,4 +1257,26 @@ extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_
   a.no_skip = 1;
   a.status = &h->status;
   return run_sort(a, stream) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// Status word of the last gs_sort_pairs_static on the current device (a
+// bounded wait of the sort that gave up leaves GS_ERR_TIMEOUT there).
+extern "C" gs_status gs_sort_pairs_static_status(uint32_t *host_status, cudaStream_t stream) {
+  using namespace gs;
+  if (!host_status) return GS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GS_ERR_CUDA;
+  unsigned char *base;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    base = g_static_ptr[dev];
+  }
+  *host_status = GS_OK;
+  if (!base) return GS_OK;   // no sort ran on this device
+  const size_t off = offsetof(StaticHdr, status);
+  if (cudaMemcpyAsync(host_status, base + off, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                      stream) != cudaSuccess)
+    return GS_ERR_CUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return GS_ERR_CUDA;
+  return (gs_status)*host_status;
 }

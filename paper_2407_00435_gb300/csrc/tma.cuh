@@ -44,9 +44,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on phase `parity`; false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (int it = 0; it < kSpinLimit; ++it) {
+// Bounded wait on phase `parity` of at most `limit` polls; false if it gave
+// up (limit <= 0: at once).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  int limit = kSpinLimit) {
+  for (int it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     __nanosleep(32);
   }

@@ -61,7 +61,7 @@ class gs_fov(C.Structure):
 class gs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("chunk", C.c_int32), ("flags", C.c_int32),
                 ("max_levels", C.c_int32), ("radix_bits", C.c_int32), ("chunk_slots", C.c_int32),
-                ("max_pairs", C.c_int64)]
+                ("max_pairs", C.c_int64), ("wait_spins", C.c_int32), ("reserved", C.c_int32)]
 
 
 class gs_counters(C.Structure):
@@ -116,6 +116,10 @@ def _load():
     lib.gs_weighted_scale.restype = s
     lib.gs_peak_probe.argtypes = [s, s, p, p, p]
     lib.gs_peak_probe.restype = s
+    lib.gs_sort_pairs_static.argtypes = [p, p, C.c_int64, s, p, p, p]
+    lib.gs_sort_pairs_static.restype = s
+    lib.gs_sort_pairs_static_status.argtypes = [p, p]
+    lib.gs_sort_pairs_static_status.restype = s
     return lib
 
 
@@ -255,12 +259,14 @@ class Renderer:
     opacity-aware tight support (same image, fewer pairs); ``multi_model`` a
     separate model per foveation level (implies ``foveated``); ``chunk`` /
     ``chunk_slots`` the heavy-tile chunked render; ``radix_bits`` the pair
-    sort's digit width; ``max_pairs`` the pair capacity (``fit`` grows it).
+    sort's digit width; ``max_pairs`` the pair capacity (``fit`` grows it);
+    ``wait_spins`` the polls of the projection's bounded waits (0 = default,
+    < 0 = give up at once, which exercises the timeout path).
     """
 
     def __init__(self, n, sh_degree, cams, tile=16, foveated=False, backward=False,
                  max_pairs=0, max_levels=0, chunk=0, radix_bits=0, chunk_slots=0,
-                 tight=False, multi_model=False, device="cuda"):
+                 tight=False, multi_model=False, wait_spins=0, device="cuda"):
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.cams_np = np.asarray(cams, np.float32).reshape(-1, 20)
         self.V = len(self.cams_np)
@@ -270,7 +276,7 @@ class Renderer:
                              | (GS_FLAG_TIGHT if tight else 0)
                              | (GS_FLAG_MULTI_MODEL | GS_FLAG_FOVEATED if multi_model else 0),
                              max_levels,
-                             radix_bits, chunk_slots, max_pairs)
+                             radix_bits, chunk_slots, max_pairs, wait_spins, 0)
         self.plan = C.create_string_buffer(int(_lib.gs_plan_size()))
         self._cams_h = cams_host(self.cams_np)
         gs_plan_init(self.plan, self.n, self.sh_degree, self._cams_h, self.V, self.cfg)

@@ -6,33 +6,9 @@ import pytest
 
 from paper_2407_00435_gb300 import synth
 
+from helpers import compare_grads as _compare
+
 pytestmark = pytest.mark.gpu
-
-GRAD_REL = 1e-3
-
-
-@pytest.fixture(scope="module")
-def gs():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2407_00435_gb300 import gs as _gs
-    return _gs
-
-
-def _compare(name, got, ref):
-    got = np.asarray(got, np.float64).reshape(-1)
-    ref = np.asarray(ref, np.float64).reshape(-1)
-    nrm = np.linalg.norm(ref)
-    if nrm == 0:
-        assert np.abs(got).max() < 1e-6, name
-        return 0.0
-    rel = np.linalg.norm(got - ref) / nrm
-    assert rel <= GRAD_REL, f"{name}: relative error {rel:.3g}"
-    # no single element may be far off relative to the group's scale
-    assert np.abs(got - ref).max() <= 1e-2 * np.abs(ref).max() + 1e-7, name
-    return rel
-
 
 def _run(gs, orc, wl, fov=None, mv=None, seed=0):
     import torch

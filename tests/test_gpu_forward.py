@@ -79,7 +79,7 @@ def test_plain_128_n10k_bins_and_image(gs, orc):
     rgb = out["rgb"].cpu().numpy()
     mx, mean, namb = compare_images(rgb, img)
     T = out["T"].cpu().numpy()
-    amb = img.margin < 1e-4
+    amb = img.amb
     np.testing.assert_allclose(T[~amb], img.T[~amb, 0], atol=1e-5, rtol=1e-4)
     last = out["last"].cpu().numpy()
     assert np.array_equal(last[~amb], img.last[~amb, 0])
@@ -154,7 +154,7 @@ def test_foveated_multiview(gs, orc, mv):
     np.testing.assert_array_equal(tl, ob.tile_level)
     compare_images(out["rgb"].cpu().numpy(), img)
     T = out["T"].cpu().numpy().reshape(-1, 2)
-    amb = img.margin < 1e-4
+    amb = img.amb
     np.testing.assert_allclose(T[~amb], img.T[~amb], atol=1e-5, rtol=1e-4)
 
 

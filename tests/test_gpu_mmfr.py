@@ -7,7 +7,7 @@ import pytest
 
 from paper_2407_00435_gb300 import synth
 from helpers import compare_images, run_gpu
-from test_gpu_backward import _compare
+from helpers import compare_grads as _compare
 from test_gpu_forward import check_bins_exact, gpu_bins
 
 pytestmark = pytest.mark.gpu

@@ -155,6 +155,71 @@ def test_2d_covariance_against_scipy_rotation_and_numerical_jacobian(orc):
     assert checked > 20
 
 
+def _clamped_cov(p, Sig, fx, fy, cx, cy, limx, limy, how="right"):
+    """Sigma' = J Sigma J^T + 0.3 I with J the numerical Jacobian of the
+    pinhole map at the camera-space point whose x/z, y/z are clamped to
+    +-lim (camera rotation = identity).  `how` plants the mistakes the pin
+    must tell apart."""
+    tx, ty = p[0] / p[2], p[1] / p[2]
+    if how == "swap":            # the width's limit used for y and vice versa
+        limx, limy = limy, limx
+    if how == "sign":            # clamped to the wrong side
+        cxl = -np.clip(tx, -limx, limx) if abs(tx) > limx else tx
+        cyl = -np.clip(ty, -limy, limy) if abs(ty) > limy else ty
+    elif how == "none":
+        cxl, cyl = tx, ty
+    else:
+        cxl, cyl = np.clip(tx, -limx, limx), np.clip(ty, -limy, limy)
+    q = np.array([cxl * p[2], cyl * p[2], p[2]])
+    J = _num_jacobian(q, fx, fy, cx, cy)
+    return J @ Sig @ J.T + 0.3 * np.eye(2)
+
+
+def test_jacobian_clamp_outside_the_frustum(orc):
+    # Reading: J of the EWA splat is evaluated at the camera-space mean with
+    # x/z and y/z clamped to 1.3 tan(half field of view) of each axis
+    # (horizontal: (W/2)/fx, vertical: (H/2)/fy); the 2D mean is not
+    # clamped.  Points beyond the clamp on every side, the image wider than
+    # tall so that the two limits differ (1.3 vs 0.78).
+    W, H, f = 200, 120, 100.0
+    cam = axis_camera(W, H, f)
+    limx, limy = 1.3 * (W / 2) / f, 1.3 * (H / 2) / f
+    z = 2.0
+    ratios = [(1.6, 0.0), (-1.6, 0.2), (0.2, 1.0), (0.1, -1.0), (1.5, -0.9), (-1.5, 0.9),
+              (0.5, 0.3), (-1.45, -0.5)]
+    means = np.array([[a * z, b * z, z] for a, b in ratios])
+    rng = np.random.default_rng(17)
+    scales = np.exp(rng.normal(np.log(0.5), 0.3, (len(means), 3)))
+    quats = rng.normal(size=(len(means), 4))
+    sc = make_scene(means, scales, quats=quats)
+    vis, _, _, supp = orc.keyed_project(sc, cam, 16, tight=True)
+    assert np.all(vis == 1), vis
+    vp = orc.project_values(sc, cam, vis)
+    n_clamped = 0
+    mistakes = {"swap": 0.0, "sign": 0.0, "none": 0.0}
+    for i, (a, b) in enumerate(ratios):
+        p = sc.means[i].astype(np.float64)
+        Rq = _rotation_scipy(sc.quats[i].astype(np.float64) / np.linalg.norm(sc.quats[i]))
+        Sig = Rq @ np.diag(sc.scales[i].astype(np.float64) ** 2) @ Rq.T
+        S2 = _clamped_cov(p, Sig, f, f, W / 2, H / 2, limx, limy)
+        got = vp[i, [orc.ORC_SA, orc.ORC_SB, orc.ORC_SC]]
+        want = [S2[0, 0], S2[0, 1], S2[1, 1]]
+        np.testing.assert_allclose(got, want, rtol=1e-7, atol=1e-9 * S2[0, 0])
+        # the keyed FP32 covariance (binning) takes the same clamp
+        np.testing.assert_allclose(supp[i, 2:5], want, rtol=2e-5, atol=2e-6 * S2[0, 0])
+        # 2D mean: the unclamped pinhole projection
+        np.testing.assert_allclose(vp[i, [orc.ORC_U, orc.ORC_V]],
+                                   [f * p[0] / p[2] + W / 2, f * p[1] / p[2] + H / 2], rtol=1e-12)
+        n_clamped += abs(a) > limx or abs(b) > limy
+        for how in mistakes:
+            M = _clamped_cov(p, Sig, f, f, W / 2, H / 2, limx, limy, how)
+            d = np.abs(np.array([M[0, 0], M[0, 1], M[1, 1]]) - want).max() / S2[0, 0]
+            mistakes[how] = max(mistakes[how], d)
+    assert n_clamped >= 6
+    # each planted mistake moves some covariance far beyond the tolerance
+    assert all(v > 1e-3 for v in mistakes.values()), mistakes
+
+
 def test_keyed_rect_covers_three_sigma_and_depth_is_camera_z(orc):
     # The tile rectangle is the set of tiles overlapped by the square of
     # half-width ceil(3 sqrt(lambda_max)) around the 2D mean: it must contain
@@ -328,11 +393,79 @@ def test_tiled_equals_brute_force(orc, fov_mode):
         fa = orc.FovArrays.from_synth(f, op, dc)
     b = orc.bin_pairs(sc, cams, 16, fa)
     img = orc.render(sc, cams, 16, b, fa)
-    rgb, T, last = orc.render_brute(sc, cams, 16, fa)
+    # the brute force applies no tile filter: for foveated views the tiled
+    # result equals it only if the tile levels are conservative (Sec. 4.2)
+    rgb, T, last_item = orc.render_brute(sc, cams, 16, fa)
     np.testing.assert_array_equal(img.rgb, rgb)
     np.testing.assert_array_equal(img.T, T)
-    np.testing.assert_array_equal(img.last, last)
+    np.testing.assert_array_equal(_last_items(orc, b, cams, 16, img.last), last_item)
     assert (img.last[:, 0] >= 0).mean() > 0.1
+    if fa is not None:
+        # the filter does drop pairs here, so the comparison exercises it
+        b0 = orc.bin_pairs(sc, cams, 16)
+        assert b.K < b0.K
+
+
+def _last_items(orc, b, cams, tile, last):
+    """Tile-list positions of `last` (P, 2) -> items (v*N + i), -1 kept."""
+    W, H, tx, ty = orc.view_dims(cams, tile)
+    tbase = np.concatenate([[0], np.cumsum(tx * ty)])
+    out = np.full(last.shape, -1, np.int64)
+    q = 0
+    for v in range(len(cams)):
+        ys, xs = np.divmod(np.arange(W[v] * H[v]), W[v])
+        gt = tbase[v] + (ys // tile) * tx[v] + xs // tile
+        for a in range(2):
+            lv = last[q:q + W[v] * H[v], a].astype(np.int64)
+            ok = lv >= 0
+            out[q:q + W[v] * H[v], a][ok] = b.vals[b.ranges[gt[ok], 0] + lv[ok]]
+        q += W[v] * H[v]
+    return out
+
+
+def test_brute_force_detects_a_tile_filter_that_is_not_conservative(orc, monkeypatch):
+    # A planted mistake: tile levels one level too coarse.  The tiled render
+    # then drops points some band pixels need, and the comparison above fails.
+    rng = np.random.default_rng(21)
+    sc = synth.uniform_scene(rng, 64, degree=3, log_scale=(-2.8, 0.5), dc_mode="coef")
+    cams = synth.orbit_cameras(rng, 2, 3.0, [(32, 32), (48, 40)])
+    f, _, _ = _small_fov(rng, sc.n, 2, cams)
+    fa = orc.FovArrays.from_synth(f)
+    rgb, _, _ = orc.render_brute(sc, cams, 16, fa)
+    good = orc.tile_levels
+    monkeypatch.setattr(orc, "tile_levels",
+                        lambda c, t, fv: np.minimum(good(c, t, fv) + 1, fv.n_levels).astype(np.uint8))
+    b = orc.bin_pairs(sc, cams, 16, fa)
+    img = orc.render(sc, cams, 16, b, fa)
+    assert np.abs(img.rgb - rgb).max() > 1e-6
+
+
+def test_ambiguity_flags_cover_real_decision_flips(orc):
+    # The oracle flags pixels whose alpha-floor or stop decision lies inside
+    # the uncertainty window of an FP32 evaluation (alpha relative error below
+    # 4e-5) and bounds what a flipped decision can change.  Scaling every
+    # opacity by (1 + delta), |delta| below that error, flips exactly such
+    # decisions in FP64: every pixel that moves by more than the continuous
+    # change must be flagged, and move by no more than its bound.
+    rng = np.random.default_rng(41)
+    sc = synth.blob_scene(rng, 6000, n_blobs=8, degree=1, log_scale=(-3.2, 0.5))
+    cams = synth.orbit_cameras(rng, 3, 3.0, [(96, 80), (64, 64), (128, 96)])
+    b = orc.bin_pairs(sc, cams, 16)
+    img = orc.render(sc, cams, 16, b)
+    cont = 1e-4          # the continuous change of scaling alpha by |delta|
+    n_jumped = 0
+    for delta in (-3.5e-5, -2e-5, -1e-5, 1e-5, 2e-5, 3.5e-5):
+        op2 = sc.opac.astype(np.float64) * (1.0 + delta)
+        img2 = orc.render(sc, cams, 16, b, opac=op2)
+        d = np.abs(img2.rgb - img.rgb).max(axis=1)
+        jumped = d > cont
+        n_jumped += int(jumped.sum())
+        assert np.all(img.amb[jumped]), (delta, np.nonzero(jumped & ~img.amb)[0][:10])
+        assert np.all(d <= img.ambB + cont), delta
+    assert n_jumped > 0          # the perturbations do flip decisions here
+    # the flags stay rare
+    assert img.amb.mean() < 0.02, img.amb.mean()
+    assert (img.T[:, 0] < 1e-2).mean() > 0.2      # many pixels reach the stop decision
 
 
 # ---------------------------------------------------------------------------

@@ -24,10 +24,6 @@ def gs():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2407_00435_gb300 import gs as _gs
-    lib = _gs.lib()
-    lib.gs_sort_pairs_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
-                                         C.c_void_p, C.c_void_p, C.c_void_p]
-    lib.gs_sort_pairs_static.restype = C.c_int32
     return _gs
 
 
@@ -59,7 +55,9 @@ def _static_sort(gs, keys, vals, bits):
     code = gs.lib().gs_sort_pairs_static(kin.data_ptr(), vin.data_ptr(), n, bits,
                                          kout.data_ptr(), vout.data_ptr(), s)
     assert code == gs.GS_OK
-    torch.cuda.synchronize()
+    st = C.c_uint32(99)
+    assert gs.lib().gs_sort_pairs_static_status(C.byref(st), s) == gs.GS_OK
+    assert st.value == gs.GS_OK
     return kout.cpu().numpy().view(np.uint32), vout.cpu().numpy().view(np.uint32)
 
 
@@ -83,3 +81,36 @@ def test_static_sort_rejects_oversize_and_overlap(gs):
     assert lib.gs_sort_pairs_static(p, p + 16, (1 << 20) + 1, 8, p, p, s) == gs.GS_ERR_INVALID_ARG
     assert lib.gs_sort_pairs_static(p, p + 16, 4, 8, p, p + 16, s) == gs.GS_ERR_INVALID_ARG
     assert lib.gs_sort_pairs_static(p, p + 16, 4, 0, p, p, s) == gs.GS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bits,n", [(5, 70001), (13, 1 << 20), (20, 333333), (32, 123457)])
+def test_static_sort_random_keys_against_numpy(gs, bits, n):
+    # key widths of one to four passes (20 bits: three passes, the odd count
+    # that routes the result through the static scratch), the size limit,
+    # ragged sizes and inputs that start 4 bytes past a 16-byte boundary
+    # (the plain-load path of the sort's partition staging)
+    import torch
+    rng = np.random.default_rng(bits * 1000 + n % 997)
+    keys = rng.integers(0, 1 << bits, n, dtype=np.uint64).astype(np.uint32)
+    keys[: n // 7] = keys[n // 3]                  # a long run of equal keys
+    vals = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    order = np.argsort(keys, kind="stable")
+    s = torch.cuda.current_stream().cuda_stream
+    for offset in (0, 1):                          # in int32 elements
+        kin = torch.empty(n + 4, dtype=torch.int32, device="cuda")
+        vin = torch.empty(n + 4, dtype=torch.int32, device="cuda")
+        kin[offset:offset + n] = torch.from_numpy(keys.view(np.int32)).cuda()
+        vin[offset:offset + n] = torch.from_numpy(vals.view(np.int32)).cuda()
+        kout = torch.full((n + 4,), -1, dtype=torch.int32, device="cuda")
+        vout = torch.full((n + 4,), -1, dtype=torch.int32, device="cuda")
+        ptr = lambda t: t.data_ptr() + 4 * offset
+        code = gs.lib().gs_sort_pairs_static(ptr(kin), ptr(vin), n, bits, ptr(kout), ptr(vout), s)
+        assert code == gs.GS_OK
+        st = C.c_uint32(99)
+        assert gs.lib().gs_sort_pairs_static_status(C.byref(st), s) == gs.GS_OK
+        ko = kout.cpu().numpy().view(np.uint32)
+        vo = vout.cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(ko[offset:offset + n], keys[order])
+        np.testing.assert_array_equal(vo[offset:offset + n], vals[order])
+        # nothing written outside the n outputs
+        assert np.all(ko[:offset] == 0xffffffff) and np.all(ko[offset + n:] == 0xffffffff)
