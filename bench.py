@@ -112,8 +112,8 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 ALU issue peak: 152 SMs x 128 FP32 lanes per clock.
-N_SM = 152
+# FP32 ALU issue peak: SMs x 128 FP32 lanes per clock (the SM count is the
+# device's own, cudaDevAttrMultiProcessorCount).
 FP32_LANES = 128
 # Algorithmic FP32 operations of the render inner loop: per (pixel, point)
 # evaluation the whitened quadratic form and the floor test (2 sub, 2 mul +
@@ -125,7 +125,39 @@ OPS_PER_BLEND = 8
 
 
 RENDER_SOURCES = ("paper_2407_00435_gb300/csrc/k_render.cu", "paper_2407_00435_gb300/csrc/raster.cuh")
-RENDER_PROFILE = "profiles/render_plain_1080p_n1M.md"
+# DRAM bytes per launch of the headline render kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the
+# kernel's sources at capture time; the summary beside it gives the command.
+RENDER_TRAFFIC = "profiles/render_plain_1080p_n1M.json"
+
+
+def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov):
+    """Algorithmic DRAM bytes of one gs_bin_sort (the kernels' own minimal
+    reads and writes, no cache effects):
+      pair count   per visible item: rectangle 8 (+ tight support 24) read,
+                   count 4 + row table 16 written
+      depth sort   per item slot: histogram read 4; 4 passes x (upsweep read
+                   4, downsweep read 4 key + 4 value, write 4 + 4), the first
+                   pass reading no values
+      offsets      per visible item: item 4 + count 4 read twice, offset 4
+                   written
+      emit         per visible item: item, offset, count, view 16 + rectangle
+                   8 + row table 16 read; per pair 8 written
+      pair sort    per pair and pass: upsweep 4, downsweep 8 read, 8 written
+      ranges       per pair 4 read; per tile 8 written (+ 8 cleared)"""
+    count = m_visible * (8 + (24 if tight else 0) + 4 + 16)
+    depth = n_slots * (4 + 4 * (4 + 8 + 8) - 4)
+    offsets = m_visible * (8 + 8 + 4)
+    emit = m_visible * (16 + 8 + (16 if (tight or fov) else 0)) + 8 * k_pairs
+    pair = pair_passes * 20 * k_pairs
+    ranges = 4 * k_pairs + 16 * tiles
+    return count + depth + offsets + emit + pair + ranges
+
+
+def pair_passes(tiles, radix_bits=0):
+    bits = max(1, int(tiles - 1).bit_length())
+    want = radix_bits or 8
+    return min(4, (bits + want - 1) // want)
 
 
 def max_over_ranks(torch, dist, x, world, device):
@@ -174,24 +206,37 @@ def render_sources_sha1():
 
 
 def captured_traffic():
-    """DRAM bytes per launch of the render kernel from the committed ncu
-    summary, or None when the kernel's sources changed since the capture."""
+    """DRAM bytes per launch of the render kernel from the committed capture
+    record, or None when the kernel's sources changed since the capture."""
     try:
-        lines = open(os.path.join(ROOT, RENDER_PROFILE)).read().splitlines()
+        with open(os.path.join(ROOT, RENDER_TRAFFIC)) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None, None
+    if rec.get("kernel_source_sha1") != render_sources_sha1():
+        return None, rec.get("kernel_source_sha1")
+    try:
+        return int(rec["dram_bytes_per_launch"]), rec["kernel_source_sha1"]
+    except (KeyError, ValueError, TypeError):
+        return None, None
+
+
+def host_info():
+    """Host cores and CPU model (the CPU baseline's machine)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":", 1)[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
     except OSError:
-        return None, None
-    kv = {}
-    for ln in lines:
-        ln = ln.strip().lstrip("-* ").strip()
-        if ":" in ln and ln.startswith(("kernel_source_sha1", "dram_bytes_per_launch")):
-            k, v = ln.split(":", 1)
-            kv[k.strip()] = v.strip().strip("`")
-    if kv.get("kernel_source_sha1") != render_sources_sha1():
-        return None, kv.get("kernel_source_sha1")
-    try:
-        return int(float(kv["dram_bytes_per_launch"])), kv["kernel_source_sha1"]
-    except (KeyError, ValueError):
-        return None, None
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 class L2Flusher:
@@ -297,20 +342,36 @@ def gpu_arm(args):
     # roofline of the dominant kernel (render): FP32 issue bound
     peaks, src = _peaks()
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_tops = N_SM * FP32_LANES * mhz * 1e6 / 1e12
+    n_sm = int(torch.cuda.get_device_properties(local).multi_processor_count)
+    peak_tops = n_sm * FP32_LANES * mhz * 1e6 / 1e12
     achieved_tops = (OPS_PER_EVAL * n_evals + OPS_PER_BLEND * n_blends) / (render_ms * 1e-3) / 1e12
     traffic, _ = captured_traffic()
     probe = peak_probe(torch, gs)
     roofline = {"bound": "alu", "kernel": "k_render", "achieved": round(achieved_tops, 3),
                 "peak": round(peak_tops, 3), "unit": "TFLOP/s (FP32 lane-ops)",
                 "frac": round(achieved_tops / peak_tops, 4), "traffic": traffic,
-                "traffic_source": RENDER_PROFILE if traffic else None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src} sm_max_mhz)",
+                "traffic_source": RENDER_TRAFFIC if traffic else None,
+                "sm_count": n_sm,
+                "peak_source": f"{n_sm} SMs (device attribute) x {FP32_LANES} FP32 lanes x "
+                               f"{mhz:.0f} MHz ({src} sm_max_mhz); of measured",
                 "render_ms": round(render_ms, 4),
                 "probe": {"fma_tops": probe[0], "ex2_tops": probe[1],
                           "frac_of_fma_probe": round(achieved_tops / probe[0], 4) if probe[0] else None,
                           "note": "measured issue rates of independent FP32 FMA / ex2 chains on "
                                   "every SM (gs_peak_probe), at the clock of the run"}}
+    # the binning and sorting stage (pair count, depth sort, offsets, emit,
+    # pair sort, ranges): HBM bound by design, algorithmic bytes / stage time
+    bs_bytes = bin_sort_bytes(r.n * r.V, int(c["n_visible"]), int(c["n_pairs"]), r.T_tiles,
+                              pair_passes(r.T_tiles), True, False)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bs_gbs = bs_bytes / (stages["bin_sort"] * 1e-3) / 1e9
+    roofline_bin_sort = {"bound": "hbm", "stage": "gs_bin_sort", "achieved": round(bs_gbs, 1),
+                         "peak": hbm, "unit": "GB/s", "frac": round(bs_gbs / hbm, 4),
+                         "bytes_per_frame": int(bs_bytes), "stage_ms": stages["bin_sort"],
+                         "peak_source": f"{src} hbm_gbs (copy); of measured",
+                         "note": "algorithmic bytes per kernel in bench.bin_sort_bytes; at this "
+                                 "size much of the stage's working set is served from the "
+                                 "129 MB L2"}
 
     # ---- end to end through the public API with host buffers ----------------
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(wl.scene, k2))).pin_memory()
@@ -383,6 +444,7 @@ def gpu_arm(args):
         "evals_per_s": round(n_evals * value, 1),
         "stages_ms": stages,
         "roofline": roofline,
+        "roofline_bin_sort": roofline_bin_sort,
         "e2e": {"value": round(job_rate(e2e_ms, world), 2), "unit": "frames/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "pipelined": "scene upload of frame i+1 and image read-back of frame i-1 "
@@ -547,23 +609,30 @@ def extra_mmfr(torch, gs, synth, flush, steps):
 
 
 def extra_fwd_bwd(torch, gs, synth, flush, steps):
-    """500k points, SH3, 8 views at 1024^2, L1 loss: one batched plan vs 8
-    per-view plans, forward + backward."""
+    """500k points, SH3, 8 views at 1024^2, L1 loss, forward + backward:
+    the views foveated in one batched plan (4 nested levels, rings at
+    10/20/35 degrees, 32-px band: retraining through the foveated renderer,
+    Sec. 4.3) against 8 plain per-view plans, and the plain batched plan."""
     import numpy as np
     from paper_2407_00435_gb300 import autograd as ga
     wl = synth.workload(3)
+    wf = synth.fov_fwd_bwd_workload()
     sc = gs.scene_to_device(wl.scene)
+    f = gs.fov_to_device(wf.fov)
     V = len(wl.cams)
     rng = np.random.default_rng(1003)
     target = torch.from_numpy(rng.uniform(0, 1, (V * 1024 * 1024, 3)).astype(np.float32)).cuda()
     rb = gs.Renderer(wl.scene.n, 3, wl.cams, backward=True, tight=True)
     rb.fit(sc)
+    rf = gs.Renderer(wl.scene.n, 3, wf.cams, foveated=True, backward=True, tight=True)
+    cf = rf.fit(sc, f)
     per = [gs.Renderer(wl.scene.n, 3, wl.cams[v:v + 1], backward=True, tight=True)
            for v in range(V)]
     for r in per:
         r.fit(sc)
     g = {k: torch.empty_like(v) for k, v in sc.items()}
     ob = rb.alloc_outputs()
+    of = rf.alloc_outputs(fov=True)
     ov = [r.alloc_outputs() for r in per]
     npx = 1024 * 1024
 
@@ -573,6 +642,13 @@ def extra_fwd_bwd(torch, gs, synth, flush, steps):
         rb.render(ob)
         dL = torch.sign(ob["rgb"] - target) / ob["rgb"].numel()
         rb.backward(dL, ob, g)
+
+    def batched_fov():
+        rf.project(sc, f)
+        rf.bin_sort()
+        rf.render(of, fov=True)
+        dL = torch.sign(of["rgb"] - target) / of["rgb"].numel()
+        rf.backward(dL, of, g)
 
     def per_view():
         for v, r in enumerate(per):
@@ -587,10 +663,17 @@ def extra_fwd_bwd(torch, gs, synth, flush, steps):
         dL = torch.sign(ob["rgb"] - target) / ob["rgb"].numel()
         rb.backward(dL, ob, g)
 
+    def bwd_only_fov():
+        dL = torch.sign(of["rgb"] - target) / of["rgb"].numel()
+        rf.backward(dL, of, g)
+
     ms_b = _ms(torch, batched, steps, 2, flush)
+    ms_f = _ms(torch, batched_fov, steps, 2, flush)
     ms_v = _ms(torch, per_view, steps, 2, flush)
     batched()
     ms_bwd = _ms(torch, bwd_only, steps, 2, flush)
+    batched_fov()
+    ms_bwd_f = _ms(torch, bwd_only_fov, steps, 2, flush)
     # autograd path (L1 loss through torch.autograd.Function)
     scg = {k: v.clone().requires_grad_(True) for k, v in sc.items()}
 
@@ -601,11 +684,20 @@ def extra_fwd_bwd(torch, gs, synth, flush, steps):
         loss.backward()
 
     ms_ag = _ms(torch, autograd_step, steps, 2, flush)
-    del rb, per, sc
+    pairs_plain = int(rb.counters()[1]["n_pairs"])
+    del rb, rf, per, sc
     torch.cuda.empty_cache()
     return {"workload": wl.name, "views": V, "fwd_bwd_ms_batched": round(ms_b, 3),
             "fwd_bwd_ms_per_view_plans": round(ms_v, 3), "speedup": round(ms_v / ms_b, 3),
-            "bwd_ms_per_view": round(ms_bwd / V, 4), "autograd_step_ms": round(ms_ag, 3)}
+            "bwd_ms_per_view": round(ms_bwd / V, 4), "autograd_step_ms": round(ms_ag, 3),
+            "foveated": {"workload": wf.name, "fwd_bwd_ms_batched_foveated": round(ms_f, 3),
+                         "speedup_vs_plain_per_view_plans": round(ms_v / ms_f, 3),
+                         "speedup_vs_plain_batched": round(ms_b / ms_f, 3),
+                         "bwd_ms_per_view_foveated": round(ms_bwd_f / V, 4),
+                         "pairs_foveated": int(cf["n_pairs"]), "pairs_plain": pairs_plain,
+                         "note": "batched foveated forward+backward against plain per-view "
+                                 "forward+backward of the same views; gradient parity of this "
+                                 "plan at full size in tests/test_gpu_fullsize.py"}}
 
 
 def extra_prune(torch, gs, synth, flush, steps):
@@ -717,39 +809,58 @@ def extra_batched(torch, gs, synth, flush, steps):
 # --------------------------------------------------------------------------
 # CPU arm: the FP64 oracle on a bounded sample
 # --------------------------------------------------------------------------
-def cpu_oracle_fps(budget_s=20.0):
+def cpu_oracle_fps(budget_s=20.0, all_cores=True):
     """Frames/s of the oracle on the 1080p/1M workload: binning of the whole
-    frame plus compositing of a random sample of tiles, scaled to the
-    frame.  Single-threaded."""
+    frame plus compositing of a random sample of tiles, scaled to the frame.
+    ``all_cores``: the oracle's -fopenmp build (independent items and pixels
+    split over the host's cores, same arithmetic); else single-threaded."""
     import numpy as np
 
     import oracle
     from paper_2407_00435_gb300 import synth
     oracle.build()
-    wl = synth.workload(1)
-    t0 = time.perf_counter()
-    b = oracle.bin_pairs(wl.scene, wl.cams, 16, tight=True)
-    t_bin = time.perf_counter() - t0
-    vp = oracle.project_values(wl.scene, wl.cams, b.vis)
-    t_proj = time.perf_counter() - t0 - t_bin
-    rng = np.random.default_rng(0)
-    T = len(b.ranges)
-    order = rng.permutation(T)
-    done_tiles, t_render = 0, 0.0
-    for t in order:
-        ty, tx = divmod(int(t), 120)
-        pix = [y * 1920 + x for y in range(ty * 16, min(1080, ty * 16 + 16))
-               for x in range(tx * 16, tx * 16 + 16)]
-        s = time.perf_counter()
-        oracle.render(wl.scene, wl.cams, 16, b, pix=np.array(pix, np.int64), vp=vp)
-        t_render += time.perf_counter() - s
-        done_tiles += 1
-        if t_bin + t_proj + t_render > budget_s:
-            break
-    frame_s = t_bin + t_proj + t_render * T / done_tiles
-    return {"value": round(1.0 / frame_s, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
+    used = oracle.use_all_cores(all_cores)
+    try:
+        wl = synth.workload(1)
+        t0 = time.perf_counter()
+        b = oracle.bin_pairs(wl.scene, wl.cams, 16, tight=True)
+        t_bin = time.perf_counter() - t0
+        vp = oracle.project_values(wl.scene, wl.cams, b.vis)
+        t_proj = time.perf_counter() - t0 - t_bin
+        rng = np.random.default_rng(0)
+        T = len(b.ranges)
+        order = rng.permutation(T)
+        done_tiles, t_render = 0, 0.0
+        step = 64 if used else 1             # tiles per oracle call
+        for k in range(0, T, step):
+            pix = []
+            for t in order[k:k + step]:
+                ty, tx = divmod(int(t), 120)
+                pix += [y * 1920 + x for y in range(ty * 16, min(1080, ty * 16 + 16))
+                        for x in range(tx * 16, tx * 16 + 16)]
+            s = time.perf_counter()
+            oracle.render(wl.scene, wl.cams, 16, b, pix=np.array(pix, np.int64), vp=vp)
+            t_render += time.perf_counter() - s
+            done_tiles += len(order[k:k + step])
+            if t_bin + t_proj + t_render > budget_s:
+                break
+        frame_s = t_bin + t_proj + t_render * T / done_tiles
+        cores = oracle.threads()
+    finally:
+        oracle.use_all_cores(False)
+    return {"value": round(1.0 / frame_s, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "build": "all cores (-fopenmp over items and pixels)" if used else "single-threaded",
             "sample": f"full-frame binning + FP64 projection, {done_tiles}/{T} random tiles "
-                      f"composited and scaled to the frame ({t_bin + t_proj + t_render:.1f} s)"}
+                      f"composited and scaled to the frame ({t_bin + t_proj + t_render:.1f} s)",
+            **host_info()}
+
+
+def cpu_baseline():
+    """The all-core oracle, with the single-threaded one beside it."""
+    allc = cpu_oracle_fps(12.0, all_cores=True)
+    one = cpu_oracle_fps(12.0, all_cores=False)
+    allc["single_core"] = {k: one[k] for k in ("value", "cores", "sample")}
+    return allc
 
 
 def reference_arm(args):
@@ -757,7 +868,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per = max(5.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    per = max(4.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_oracle_fps(per)
     vals = [cpu_oracle_fps(per) for _ in range(args.steps)]
@@ -781,7 +892,7 @@ def main():
     res, rank, world = gpu_arm(args)
     if rank == 0:
         if world == 1 and not args.no_cpu:
-            res["cpu_baseline"] = cpu_oracle_fps(20.0)
+            res["cpu_baseline"] = cpu_baseline()
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -20,6 +20,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# The same source built with -fopenmp: its independent per-item and per-pixel
+# loops run on all host cores (same arithmetic per item and pixel).
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 ORC_NVAL = 15
 ORC_SUPP = 6            # tight-support record: keyed u, v, covariance a b c, tau
@@ -27,17 +30,31 @@ ORC_SUPP = 6            # tight-support record: keyed u, v, covariance a b c, ta
  ORC_RB, ORC_DEPTH, ORC_SA, ORC_SB, ORC_SC) = range(15)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (gcc, -O2, no FP contraction, no fast-math)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                              os.path.getmtime(os.path.join(_HERE, "gs_oracle.h")))):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+def _compile(out, extra):
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-Wall", "-Wno-unused-function", _SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared", "-Wall", "-Wno-unused-function", "-Wno-unknown-pragmas",
+           *extra, _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    os.replace(tmp, out)
+
+
+def _stale(path):
+    return (not os.path.exists(path)
+            or os.path.getmtime(path) < max(os.path.getmtime(_SRC),
+                                            os.path.getmtime(os.path.join(_HERE, "gs_oracle.h"))))
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, no FP contraction, no fast-math), the
+    single-threaded library and its all-core (-fopenmp) build."""
+    if force or _stale(_LIB):
+        _compile(_LIB, [])
+    if force or _stale(_LIB_OMP):
+        try:
+            _compile(_LIB_OMP, ["-fopenmp"])
+        except subprocess.CalledProcessError:
+            pass   # no OpenMP runtime: only the single-threaded build
     return _LIB
 
 
@@ -56,13 +73,33 @@ class _Fov(C.Structure):
 
 
 _lib = None
+_threads = False
+
+
+def use_all_cores(on: bool = True) -> bool:
+    """Switch the wrappers to the all-core build (True) or back to the
+    single-threaded one.  Returns whether the all-core build is in use."""
+    global _lib, _threads
+    build()
+    on = bool(on) and os.path.exists(_LIB_OMP)
+    if on != _threads:
+        _threads = on
+        _lib = None
+    return _threads
+
+
+def threads() -> int:
+    """Host threads the current build uses."""
+    if not _threads:
+        return 1
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
+        L = C.CDLL(_LIB_OMP if _threads else _LIB)
         p = C.c_void_p
         L.orc_keyed_project.argtypes = [C.c_int, p, p, p, p, p, C.c_int, C.c_int, p, C.c_int, p, p,
                                         p, p, p]

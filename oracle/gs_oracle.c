@@ -292,6 +292,8 @@ int orc_keyed_project(int n, const float *means, const float *scales,
   for (int v = 0; v < V; ++v) {
     int tx, ty;
     view_tiles(&cams[v], tile, &tx, &ty);
+    /* items are independent: the all-core build (-fopenmp) splits them */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
       int64_t it = (int64_t)v * n + i;
       int fin = 1;
@@ -693,6 +695,7 @@ int orc_project_values(int n, const double *means, const double *scales,
                        double *out) {
   int S = (sh_degree + 1) * (sh_degree + 1);
   for (int v = 0; v < V; ++v)
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
       int64_t id = (int64_t)v * n + i;
       double *o = &out[id * ORC_NVAL];
@@ -769,7 +772,8 @@ static double rel_margin(double a, double thr) {
  *     (u = 2^-24; a clamped alpha is 0.99 in FP32, 1e-6 off in 1 - alpha).
  * An alpha-floor decision is ambiguous when alpha lies within AMB_FLOOR
  * (relative) of 1/255; a stop decision when T (1 - alpha) lies within
- * AMB_FLOOR + AMB_SAFE times T's error bound of 1e-4.  Flipping a floor
+ * AMB_FLOOR + AMB_SAFE times T's error bound of 1e-4 (the bound adds the
+ * per-blend worst cases linearly, so it needs no further safety factor).  Flipping a floor
  * decision at transmittance T changes the pixel by at most 2 T c_max / 255
  * (the point's own T alpha c plus the factor (1 - alpha) on what follows);
  * flipping the stop decision by at most T c_max (everything from there on).
@@ -777,7 +781,7 @@ static double rel_margin(double a, double thr) {
  * later stop windows. */
 #define ALPHA_REL_ERR 4e-5
 #define AMB_FLOOR 1e-4
-#define AMB_SAFE 2.5
+#define AMB_SAFE 1.0
 #define U32 5.9604644775390625e-8
 
 /* Whether point i takes part at level lvl (see orc_fov.disjoint).  Without
@@ -925,10 +929,16 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
                int32_t *last, double *margin, double *wband, double *ambB,
                uint8_t *amb, uint32_t *stats) {
   if (pix) {
+    int bad = 0;
+    /* pixels are independent: the all-core build (-fopenmp) splits them */
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
     for (int64_t q = 0; q < npix; ++q) {
       int x, y;
       int v = find_view(V, cams, pix[q], &x, &y);
-      if (v < 0) return -1;
+      if (v < 0) {
+        bad = 1;
+        continue;
+      }
       int tx, ty;
       view_tiles(&cams[v], tile, &tx, &ty);
       int64_t gt = tile_base(V, cams, tile, v) + (int64_t)(y / tile) * tx + x / tile;
@@ -937,7 +947,7 @@ int orc_render(int n, int V, const orc_cam *cams, int tile,
                   margin ? &margin[q] : NULL, wband ? &wband[q] : NULL,
                   ambB ? &ambB[q] : NULL, amb ? &amb[q] : NULL, NULL);
     }
-    return 0;
+    return bad ? -1 : 0;
   }
   /* whole batch, tile by tile (so that per-tile statistics are exact) */
   uint32_t *tt = stats, *tu = stats ? stats + n : NULL, *pb = stats ? stats + 2 * (int64_t)n : NULL,

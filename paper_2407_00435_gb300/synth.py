@@ -298,6 +298,20 @@ def multi_model_workload(n=None, views=None) -> Workload:
 # --------------------------------------------------------------------------
 # the five workloads
 # --------------------------------------------------------------------------
+def fov_fwd_bwd_workload(n=None, views=None) -> Workload:
+    """The forward + backward workload (500k points, SH3, 8 views of 1024^2
+    on the orbit, L1 loss) with each view foveated as in the stereo workload:
+    4 nested levels by a seeded rank (100/50/25/12.5 % of the points), rings
+    at 10/20/35 degrees, a 32-px blend band, a gaze per view uniform in the
+    central 50 %.  Retraining through the foveated renderer (Sec. 4.3)."""
+    wl = workload(3, n=n, views=views)
+    rng = np.random.default_rng(config_seed(3) + 200)
+    m = nested_levels(rng, wl.scene.n, 4)
+    gaze = random_gaze(rng, wl.cams)
+    fov = Foveation(4, m, ring_tangents([10, 20, 35]), 32.0, gaze)
+    return Workload(wl.name.replace("fwd_bwd", "fov_fwd_bwd"), wl.scene, wl.cams, wl.tile, fov)
+
+
 def config_seed(idx: int) -> int:
     return 1000 + idx
 

@@ -8,7 +8,7 @@ IMG_MEAN_ABS = 1e-5
 # A pixel whose alpha-floor or early-stop decision lies inside the
 # uncertainty window of an FP32 evaluation (flagged by the oracle: alpha
 # within 1e-4 relative of 1/255, against a derived FP32 alpha error below
-# 4e-5; T (1 - alpha) within 1e-4 plus 2.5 times the running bound of T's
+# 4e-5; T (1 - alpha) within 1e-4 plus the running worst-case bound of T's
 # FP32 relative error of 1e-4) may take the other branch; it is compared
 # against what a flipped decision can change (the oracle's ambB:
 # 2 T c_max / 255 per flipped floor decision, T c_max for the stop).

@@ -10,6 +10,16 @@ from helpers import compare_grads as _compare
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(scope="module")
+def gs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_00435_gb300 import gs as _gs
+    return _gs
+
+
 def _run(gs, orc, wl, fov=None, mv=None, seed=0):
     import torch
     sc = gs.scene_to_device(wl.scene)

@@ -574,3 +574,26 @@ def test_fov_levels_and_band_weights_by_geometry(orc):
         assert img.wband[q] == pytest.approx(w, abs=1e-12)
         expect = colf[lvl - 1] if w == 1.0 else w * colf[lvl - 1] + (1 - w) * colf[lvl - 2]
         np.testing.assert_allclose(img.rgb[q, 0] / alpha, expect, rtol=1e-9)
+
+
+def test_all_core_build_gives_identical_results(orc):
+    # the -fopenmp build splits independent items and pixels over threads and
+    # must not change a single bit (timed as the all-core CPU baseline)
+    rng = np.random.default_rng(51)
+    sc = synth.blob_scene(rng, 4000, n_blobs=6, degree=2, log_scale=(-3.2, 0.5))
+    cams = synth.orbit_cameras(rng, 2, 3.0, [(96, 80), (64, 64)])
+    pix = np.arange(0, 96 * 80 + 64 * 64, 7, dtype=np.int64)
+    orc.use_all_cores(False)
+    b1 = orc.bin_pairs(sc, cams, 16, tight=True)
+    i1 = orc.render(sc, cams, 16, b1, pix=pix)
+    try:
+        if not orc.use_all_cores(True):
+            pytest.skip("no OpenMP runtime")
+        b2 = orc.bin_pairs(sc, cams, 16, tight=True)
+        i2 = orc.render(sc, cams, 16, b2, pix=pix)
+    finally:
+        orc.use_all_cores(False)
+    np.testing.assert_array_equal(b1.keys, b2.keys)
+    np.testing.assert_array_equal(b1.vals, b2.vals)
+    for a, b in ((i1.rgb, i2.rgb), (i1.T, i2.T), (i1.last, i2.last), (i1.ambB, i2.ambB)):
+        np.testing.assert_array_equal(a, b)
