@@ -65,17 +65,20 @@ def compare_images(rgb_gpu, img, sel=None, label=""):
 
 # Gradients (backward vs the FP64 oracle's analytic gradient).
 GRAD_REL = 1e-3
-# Absolute part of the per-element bound: FP32 rounding of one element is
-# relative to the magnitude of the terms it sums, which is at least the
-# point's own gradient in that group.  1e-4 of the largest component of the
-# point's row (about 2^-24 times the ~10^3 pixel terms a point sums, with
-# headroom) plus 1e-6 of the group's largest element for rows that cancel.
+# Absolute part of the per-element bound.  FP32 rounding of one element is
+# relative to the magnitude of the terms it sums (10^3 to 10^4 pixel terms
+# per point, each through ~30 chained operations: n u ~ 6e-4 of the largest
+# term in the worst case), which cancellation can leave far above the
+# element itself: 1e-4 of the largest component of the point's row (the
+# point's own terms) plus 1e-5 of the group's largest element (rows whose
+# components all cancel, such as the quaternion gradient after its
+# projection onto the unit sphere's tangent).
 ROW_EPS = 1e-4
-GROUP_EPS = 1e-6
+GROUP_EPS = 1e-5
 
 
 def compare_grads(name, got, ref):
-    """Element by element: |g - r| <= 1e-3 |r| + 1e-4 max|r_row| + 1e-6 max|r|,
+    """Element by element: |g - r| <= 1e-3 |r| + 1e-4 max|r_row| + 1e-5 max|r|,
     a row being one point's components in this parameter group."""
     n = ref.shape[0]
     got = np.asarray(got, np.float64).reshape(n, -1)

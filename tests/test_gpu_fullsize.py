@@ -149,7 +149,7 @@ def test_batched_views_full_size_subset_autotuned_plan(gs, orc):
     ob = orc.bin_pairs(wl.scene, cams, 16, fa, tight=True)
     check_bins_exact(gpu_bins(gs, r), ob, wl.scene.n)
     rng = np.random.default_rng(44)
-    base = np.concatenate([[0], np.cumsum(cams[:, 16].astype(np.int64) * cams[:, 17])])
+    base = np.concatenate([[0], np.cumsum(cams[:, 16].astype(np.int64) * cams[:, 17].astype(np.int64))])
     pix = np.concatenate([base[v] + rng.choice(base[v + 1] - base[v], 800, replace=False)
                           for v in range(4)])
     pix = np.sort(pix)
