@@ -312,6 +312,13 @@ gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_t *vals_in,
  * GS_ERR_INVALID_ARG (NULL host_status), GS_ERR_CUDA. */
 gs_status gs_sort_pairs_static_status(uint32_t *host_status, cudaStream_t stream);
 
+/* 1 if, on the current device, each radix sort of gs_bin_sort (and of
+ * gs_prune_mask, gs_sort_pairs_static) runs as one cooperative launch of one
+ * block per SM whose passes are separated by bounded grid barriers; 0 if it
+ * runs as three launches per pass (cooperative launch unavailable).  For
+ * launch accounting; no counterpart in the paper. */
+int32_t gs_sort_is_cooperative(void);
+
 /* Geometry helpers (host): total tiles and pixels of the plan's views. */
 int64_t gs_plan_tiles(const gs_plan *plan);
 int64_t gs_plan_pixels(const gs_plan *plan);

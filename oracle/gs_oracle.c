@@ -820,8 +820,12 @@ static void composite(int n, const double *vp, const double *opac,
     double o = level_opacity(fov, opac, n, i, lvl);
     double alpha = o * exp(power);
     int clamped = alpha > ALPHA_MAX;
+    /* the 0.99 clamp leaves the colour continuous but decides whether the
+     * point's geometry and opacity get a gradient: part of the margin */
+    double m = rel_margin(alpha, ALPHA_MAX);
+    if (m < acc->margin) acc->margin = m;
     if (clamped) alpha = ALPHA_MAX;
-    double m = rel_margin(alpha, ALPHA_MIN);
+    m = rel_margin(alpha, ALPHA_MIN);
     if (m < acc->margin) acc->margin = m;
     if (m < AMB_FLOOR) {
       acc->amb = 1;

@@ -127,8 +127,9 @@ void orc_sh_basis(const double dir[3], double Y[16]);
  *   T, last  : (npix,2)  final transmittance and tile-list position of the
  *              last blended point for accumulator A (the pixel's own level)
  *              and B (the next better level, only inside a band; else 1,-1)
- *   margin   : (npix,)   smallest relative distance of any alpha-floor or
- *              early-stop decision from its threshold
+ *   margin   : (npix,)   smallest relative distance of any alpha-floor,
+ *              alpha-clamp or early-stop decision from its threshold (the
+ *              clamp leaves the colour continuous but switches gradients)
  *   wband    : (npix,)   blend weight w of accumulator A (1 outside bands)
  *   ambB     : (npix,)   bound on what flipping the pixel's ambiguous
  *              decisions can change in any channel (0 if none); see the

@@ -87,6 +87,7 @@ struct Hdr {
   uint32_t pad1;
   unsigned long long aux_n;       // key count of a sort outside the frame (pruning)
   unsigned long long aux_out;     // result count of such a pass (compaction)
+  uint32_t coop_bar[2];           // grid barrier of the cooperative sort (count, generation)
 };
 
 // Per-view constants, computed on the device from the cameras.

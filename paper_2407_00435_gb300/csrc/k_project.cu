@@ -571,11 +571,10 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
     const uint32_t dkey = in ? a.rec_depth[j] : 0xffffffffu;
     const uint2 rr = in ? a.rec_rect[j] : make_uint2(0u, 0u);
     float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
-    float spc = 0.f, op0 = 0.f;
+    float2 sp2 = make_float2(0.f, 0.f);
     if (tight && in) {
       sp = a.rec_supp[j];
-      spc = a.rec_supp2[j].x;
-      op0 = a.opac[j / a.V];
+      sp2 = a.rec_supp2[j];
     }
     const int mrec = (fov && in) ? (int)a.rec_m[j] : 0;
     bool vis = false;
@@ -613,15 +612,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
     SuppPre pre = {};
     int m = 0, rbase = 0;
     if (rows) {
-      if (tight) {
-        const long long i = j / a.V;
-        float o_max = op0;
-        for (int l = 0; l < a.n_opacity_lv; ++l)
-          o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
-        const float2 s1 = make_float2(spc, tight_tau(o_max));
-        a.rec_supp2[j] = s1;
-        pre = supp_prep(sp, s1);
-      }
+      if (tight) pre = supp_prep(sp, sp2);
       if (fov) {
         m = mrec;
         rbase = a.views[j % a.V].row_base;
@@ -690,11 +681,8 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
       const long long jb = base + src;
       const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
       const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
-      const long long i = jb / a.V;
-      float o_max = __shfl_sync(0xffffffffu, op0, src);
-      for (int l = 0; l < a.n_opacity_lv; ++l)
-        o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
-      const float2 s1 = make_float2(__shfl_sync(0xffffffffu, spc, src), tight_tau(o_max));
+      const float2 s1 = make_float2(__shfl_sync(0xffffffffu, sp2.x, src),
+                                    __shfl_sync(0xffffffffu, sp2.y, src));
       const float4 bsp = make_float4(
           __shfl_sync(0xffffffffu, sp.x, src), __shfl_sync(0xffffffffu, sp.y, src),
           __shfl_sync(0xffffffffu, sp.z, src), __shfl_sync(0xffffffffu, sp.w, src));
@@ -716,10 +704,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
         if (xa <= xb) bpairs += (uint32_t)(xb - xa + 1);
       }
       for (int o = 16; o > 0; o >>= 1) bpairs += __shfl_xor_sync(0xffffffffu, bpairs, o);
-      if (lane == 0) {
-        a.rec_supp2[jb] = s1;
-        a.rec_count[jb] = bpairs;
-      }
+      if (lane == 0) a.rec_count[jb] = bpairs;
     }
     if (rows) {
       uint32_t tb[4] = {0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu};
@@ -840,6 +825,15 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
     const bool fin = all_finite(mu, 3) && all_finite(sc, 3) && all_finite(q, 4) &&
                      isfinite(sm.op[tid]) && all_finite(sm.sh[tid], S * 3);
     if (!fin) atomicAdd(&s_nonfinite, (uint32_t)a.V);
+    // tight support: tau bounds 2 ln(255 o) for the largest opacity any level
+    // composites the point with (one value per point, shared by its views)
+    float tau = 0.0f;
+    if (a.rec_supp) {
+      float o_max = sm.op[tid];
+      for (int l = 0; l < a.n_opacity_lv; ++l)
+        o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
+      tau = tight_tau(o_max);
+    }
     for (int v = 0; v < a.V; ++v) {
       const long long j = i * a.V + v;
       const gs_camera cam = a.cams[v];
@@ -847,9 +841,9 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
       Keyed k;
       if (fin && keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) {
         if (a.rec_supp) {
-          // keyed mean and covariance; k_count_pairs adds tau
+          // keyed mean and covariance, tau
           a.rec_supp[j] = make_float4(k.u, k.v, k.a, k.b);
-          a.rec_supp2[j] = make_float2(k.cc, 0.0f);
+          a.rec_supp2[j] = make_float2(k.cc, tau);
         }
         Rec r;
         project_value<S>(a, sm, tid, i, mu, cam, vd, k, r);

@@ -305,24 +305,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pa
 // issues them; an mbarrier per half counts the bytes in).  Partitions that
 // are not full, or inputs that are not 16-byte aligned, are read with plain
 // loads instead.
-struct DownSmem {
+template <int NT>
+struct DownSmemT {
   uint32_t in_k[2][kSortPart];
   uint32_t in_v[2][kSortPart];
   uint32_t key[kSortPart];            // staging in digit order
   uint32_t val[kSortPart];
-  uint16_t wh[kDownThreads / 32][256];   // per-warp digit counts, then offsets
+  uint16_t wh[NT / 32][256];          // per-warp digit counts, then offsets
   uint32_t base[256], carry[256], dstart[256];
   uint32_t wsum[8];                   // the 256 digit threads' warp sums
   uint64_t bar[2];
 };
+using DownSmem = DownSmemT<kDownThreads>;
+constexpr int kCoopThreads = 1024;    // one block of 32 warps per SM
+using CoopSmem = DownSmemT<kCoopThreads>;
 
-__global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int pass) {
-  extern __shared__ __align__(128) unsigned char dyn_smem[];
-  DownSmem &sm = *reinterpret_cast<DownSmem *>(dyn_smem);
-  constexpr int NW = kDownThreads / 32;
-  if (a.skip[pass]) return;
-  const uint32_t n = sort_n(a);
-  const int before = passes_before(a, pass);
+// Bookkeeping of the two halves of the downsweep's double buffer (copies
+// issued and consumed); block-uniform, kept across the passes of one launch.
+struct DownBufs {
+  uint32_t issued0, issued1, used0, used1;
+};
+
+// Walks partitions [p0, p1) of pass `pass` in order, sm.carry[d] holding
+// the output position of the next key of digit d.  `before` = executed
+// passes before this one (selects the buffers).  Returns false if a bounded
+// wait gave up (status set, copies in flight drained).
+template <int NT>
+__device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int before,
+                                                DownSmemT<NT> &sm, DownBufs &db, long long p0,
+                                                long long p1, uint32_t n) {
+  constexpr int NW = NT / 32;
+  constexpr int ITEMS = kSortPart / NT;
   const bool odd = (before & 1) != 0;   // (no dynamic indexing of the parameter arrays)
   const uint32_t *kin = before == 0 ? a.first_keys : (odd ? a.keys[1] : a.keys[0]);
   const uint32_t *vin = before == 0 ? a.first_vals : (odd ? a.vals[1] : a.vals[0]);
@@ -333,21 +346,9 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ltmask = lanemask_lt();
-  long long p0, p1;
-  block_parts(n, a.blocks, blockIdx.x, p0, p1);
-  if (p0 >= p1) return;
-  if (tid < 256) sm.carry[tid] = a.bsum[(long long)blockIdx.x * a.sub * 256 + tid];
   const bool aligned = ((uintptr_t)kin & 15u) == 0 && (iota || ((uintptr_t)vin & 15u) == 0);
   const long long full = (long long)n / kSortPart;   // partitions [0, full) hold 4096 keys
   constexpr uint32_t kBytes = kSortPart * sizeof(uint32_t);
-  if (tid == 0) {
-    mbar_init(&sm.bar[0], 1);
-    mbar_init(&sm.bar[1], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  // block-uniform bookkeeping of the two halves: copies issued / consumed
-  uint32_t issued0 = 0, issued1 = 0, used0 = 0, used1 = 0;
   auto issue = [&](long long part, int h) {
     if (tid == 0) {
       fence_proxy_async_smem();
@@ -355,45 +356,47 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
       bulk_g2s(sm.in_k[h], kin + part * kSortPart, kBytes, &sm.bar[h]);
       if (!iota) bulk_g2s(sm.in_v[h], vin + part * kSortPart, kBytes, &sm.bar[h]);
     }
-    if (h) ++issued1; else ++issued0;
+    if (h) ++db.issued1; else ++db.issued0;
   };
-  if (aligned && p0 < full) issue(p0, 0);
+  // half 0 is refilled first in every range (the previous range consumed
+  // every copy it issued)
+  if (aligned && p0 < p1 && p0 < full) issue(p0, 0);
   int h = 0;
   for (long long part = p0; part < p1; ++part, h ^= 1) {
     const bool bulk = aligned && part < full;
     // the other half was last read before the barrier ending the previous
     // partition: refill it with the next partition
     if (part + 1 < p1 && aligned && part + 1 < full) issue(part + 1, h ^ 1);
-    for (int q = tid; q < NW * 256 / 2; q += kDownThreads)
+    for (int q = tid; q < NW * 256 / 2; q += NT)
       reinterpret_cast<uint32_t *>(&sm.wh[0][0])[q] = 0u;
-    const long long wbase = part * kSortPart + warp * (32 * kDownItems);
-    const int lbase = warp * (32 * kDownItems);
-    uint32_t key[kDownItems], rank[kDownItems];
+    const long long wbase = part * kSortPart + warp * (32 * ITEMS);
+    const int lbase = warp * (32 * ITEMS);
+    uint32_t key[ITEMS], rank[ITEMS];
     if (bulk) {
-      const uint32_t u = h ? used1 : used0;
+      const uint32_t u = h ? db.used1 : db.used0;
       const bool landed = mbar_wait_bounded(&sm.bar[h], u & 1u);
-      if (h) ++used1; else ++used0;
+      if (h) ++db.used1; else ++db.used0;
       if (__syncthreads_or(!landed)) {
         // give up: record it, let the copies in flight land, leave
         if (tid == 0) set_status(a.status, GS_ERR_TIMEOUT);
-        if (issued0 > used0) mbar_wait_bounded(&sm.bar[0], used0 & 1u);
-        if (issued1 > used1) mbar_wait_bounded(&sm.bar[1], used1 & 1u);
-        return;
+        if (db.issued0 > db.used0) mbar_wait_bounded(&sm.bar[0], db.used0 & 1u);
+        if (db.issued1 > db.used1) mbar_wait_bounded(&sm.bar[1], db.used1 & 1u);
+        return false;
       }
 #pragma unroll
-      for (int k = 0; k < kDownItems; ++k) key[k] = sm.in_k[h][lbase + k * 32 + lane];
+      for (int k = 0; k < ITEMS; ++k) key[k] = sm.in_k[h][lbase + k * 32 + lane];
     } else {
 #pragma unroll
-      for (int k = 0; k < kDownItems; ++k) {
+      for (int k = 0; k < ITEMS; ++k) {
         const long long idx = wbase + k * 32 + lane;
-        key[k] = idx < (long long)n ? kin[idx] : 0u;
+        key[k] = idx < (long long)n ? __ldcg(&kin[idx]) : 0u;
       }
     }
     __syncthreads();
     // warp-level stable ranking (original order = (k, lane)); the lanes
     // holding the same digit are found with one ballot per digit bit
 #pragma unroll
-    for (int k = 0; k < kDownItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       long long idx = wbase + k * 32 + lane;
       bool valid = idx < (long long)n;
       uint32_t d = (key[k] >> shift) & dmask;
@@ -445,21 +448,21 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
     // stage the partition in digit order, then write runs of equal digits
     // to consecutive global addresses
 #pragma unroll
-    for (int k = 0; k < kDownItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const long long idx = wbase + k * 32 + lane;
       if (idx < (long long)n) {
         uint32_t d = (key[k] >> shift) & dmask;
         uint32_t lp = sm.dstart[d] + (uint32_t)sm.wh[warp][d] + rank[k];
         sm.key[lp] = key[k];
-        sm.val[lp] = iota ? (uint32_t)idx : (bulk ? sm.in_v[h][lbase + k * 32 + lane] : vin[idx]);
+        sm.val[lp] = iota ? (uint32_t)idx : (bulk ? sm.in_v[h][lbase + k * 32 + lane] : __ldcg(&vin[idx]));
       }
     }
     __syncthreads();
     const long long pbase = part * kSortPart;
     const uint32_t pcount = (uint32_t)min((long long)kSortPart, (long long)n - pbase);
 #pragma unroll
-    for (int k = 0; k < kDownItems; ++k) {
-      const uint32_t lp = (uint32_t)(k * kDownThreads + tid);
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint32_t lp = (uint32_t)(k * NT + tid);
       if (lp < pcount) {
         const uint32_t kk = sm.key[lp];
         const uint32_t d = (kk >> shift) & dmask;
@@ -472,22 +475,221 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
     }
     __syncthreads();
   }
+  return true;
+}
+
+__global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int pass) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  DownSmem &sm = *reinterpret_cast<DownSmem *>(dyn_smem);
+  if (a.skip[pass]) return;
+  const uint32_t n = sort_n(a);
+  long long p0, p1;
+  block_parts(n, a.blocks, blockIdx.x, p0, p1);
+  if (p0 >= p1) return;
+  const int tid = threadIdx.x;
+  if (tid < 256) sm.carry[tid] = a.bsum[(long long)blockIdx.x * a.sub * 256 + tid];
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  DownBufs db = {0u, 0u, 0u, 0u};
+  downsweep_range<kDownThreads>(a, pass, passes_before(a, pass), sm, db, p0, p1, n);
+}
+
+// ---- the whole sort in one cooperative launch -------------------------------
+// Every pass of the sort in one launch of G co-resident blocks (cooperative
+// launch), block b owning the partitions block_parts(n, G, b):
+//   count    block b's digit counts -> row b of a table (double-buffered by
+//            pass parity)
+//   barrier  every row written
+//   bases    each block reads the table's columns: the digit totals (digit
+//            starts by an exclusive scan) and the counts of the blocks
+//            before it -> its running per-digit output positions; a digit
+//            that every key shares skips the pass (all blocks agree)
+//   scatter  downsweep_range over the block's partitions
+//   barrier  the pass's output complete before the next pass reads it
+// The barriers count arrivals on a global word and wait (bounded) for a
+// generation word to move; they replace the 3 launches per pass (and the
+// fixed latency of each) of the multi-kernel sort.
+struct CoopBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch, bounded: false (status set)
+// if the other blocks did not all arrive within the limit.
+__device__ __forceinline__ bool grid_barrier(CoopBar *bar, uint32_t *status, int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g0 = ld_acquire_u32(&bar->gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    bool ok = true;
+    if (arrived == gridDim.x - 1) {
+      bar->count = 0u;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      int it = 0;
+      while (ld_acquire_u32(&bar->gen) == g0) {
+        if (++it > kSpinLimit) {
+          ok = false;
+          set_status(status, GS_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    // the bulk copies this thread issues next read, through the async
+    // proxy, what other blocks wrote through the generic proxy
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    *s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+constexpr int kCountUnroll = 8;
+
+__global__ void __launch_bounds__(kCoopThreads, 1) k_sort_coop(SortArgs a, CoopBar *bar) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  CoopSmem &sm = *reinterpret_cast<CoopSmem *>(dyn_smem);
+  constexpr int NQ = kCoopThreads / 256;   // threads per digit in the bases phase
+  __shared__ uint32_t s_cnt[256], s_half[NQ][256], s_pre[NQ][256];
+  __shared__ uint32_t s_wsum[8];
+  __shared__ int s_ok, s_skip;
+  const uint32_t n = sort_n(a);
+  const int G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  long long p0, p1;
+  block_parts(n, G, b, p0, p1);
+  const long long k0 = p0 * kSortPart;
+  const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
+  const uint32_t dmask = (1u << a.digit_bits) - 1u;
+  const bool force_first = a.first_vals == nullptr;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  DownBufs db = {0u, 0u, 0u, 0u};
+  int executed = 0;
+  for (int pass = 0; pass < a.passes; ++pass) {
+    const bool odd = (executed & 1) != 0;
+    const uint32_t *kin = executed == 0 ? a.first_keys : (odd ? a.keys[1] : a.keys[0]);
+    const int shift = a.digit_bits * pass;
+    uint32_t *table = a.bsum + (size_t)(pass & 1) * (size_t)G * 256;
+    // count
+    if (tid < 256) s_cnt[tid] = 0u;
+    __syncthreads();
+    const int warp = tid >> 5;
+    for (long long base = k0 + (long long)warp * 32 * kCountUnroll; base < k1;
+         base += (long long)kCoopThreads * kCountUnroll) {
+      uint32_t key[kCountUnroll];
+#pragma unroll
+      for (int u = 0; u < kCountUnroll; ++u) {
+        const long long idx = base + u * 32 + lane;
+        key[u] = idx < k1 ? __ldcg(&kin[idx]) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kCountUnroll; ++u)
+        warp_count(s_cnt, base + u * 32 + lane < k1, (key[u] >> shift) & dmask, lane);
+    }
+    __syncthreads();
+    if (tid < 256) table[(size_t)b * 256 + tid] = s_cnt[tid];
+    if (!grid_barrier(bar, a.status, &s_ok)) return;
+    // bases: digit d's total over all blocks and its count in blocks < b
+    {
+      const int d = tid & 255, hh = tid >> 8;
+      const int half = (G + NQ - 1) / NQ;
+      const int r0 = min(G, hh * half), r1 = min(G, r0 + half);
+      uint32_t tot = 0, pre = 0;
+      for (int r = r0; r < r1; r += 8) {
+        uint32_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = r + u < r1 ? __ldcg(&table[(size_t)(r + u) * 256 + d]) : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          tot += v[u];
+          pre += (r + u < b) ? v[u] : 0u;
+        }
+      }
+      s_half[hh][d] = tot;
+      s_pre[hh][d] = pre;
+    }
+    if (tid == 0) s_skip = 0;
+    __syncthreads();
+    uint32_t tot = 0, incl = 0;
+    if (tid < 256) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) tot += s_half[q][tid];
+      if (tot == n) s_skip = 1;   // one digit holds every key
+      incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (lane == 31) s_wsum[tid >> 5] = incl;
+    }
+    __syncthreads();
+    const bool skip = (s_skip || n == 0) && !(force_first && executed == 0 && pass == a.passes - 1) &&
+                      !a.no_skip;
+    if (skip) continue;   // nothing written: no barrier needed before the next count
+    if (tid < 256) {
+      uint32_t wofs = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) wofs += w < (tid >> 5) ? s_wsum[w] : 0u;
+      uint32_t pre = 0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) pre += s_pre[q][tid];
+      sm.carry[tid] = wofs + incl - tot + pre;
+    }
+    __syncthreads();
+    if (p0 < p1 && !downsweep_range<kCoopThreads>(a, pass, executed, sm, db, p0, p1, n)) {
+      // leave the grid barrier to time out in the other blocks
+      return;
+    }
+    ++executed;
+    if (!grid_barrier(bar, a.status, &s_ok)) return;
+  }
+  if (b == 0 && tid == 0) *a.sel = (uint32_t)(executed & 1);
 }
 
 static int g_sort_blocks = 0;
 static int g_stream_blocks = 0;   // grid of the streaming kernels (emit, offsets, ranges, hist)
 static std::mutex g_grid_mu;
 static bool g_smem_attr[64] = {};
+static int g_coop_grid[64] = {};  // blocks of the cooperative sort per device, 0 = unavailable
 
 static void init_grids() {
   std::lock_guard<std::mutex> lock(g_grid_mu);
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
-  // the downsweep's shared memory exceeds the default 48 KB: opt in on
-  // every device that sorts
+  // the sort kernels' shared memory exceeds the default 48 KB: opt in on
+  // every device that sorts; the cooperative sort runs one block per SM
+  // (co-resident, as its grid barriers require) if the device can launch
+  // cooperative grids
   if (dev >= 0 && dev < 64 && !g_smem_attr[dev]) {
     cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(DownSmem));
+    cudaFuncSetAttribute(k_sort_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(CoopSmem));
+    int coop = 0, pc = 0, nsm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_sort_coop, kCoopThreads, sizeof(CoopSmem));
+    g_coop_grid[dev] = (coop && pc > 0 && nsm > 0) ? nsm : 0;
+    cudaGetLastError();
     g_smem_attr[dev] = true;
   }
   if (g_sort_blocks) return;
@@ -514,6 +716,42 @@ static cudaError_t run_sort(const SortArgs &a0, cudaStream_t s, bool hist_done =
     k_downsweep<<<a.blocks, kDownThreads, sizeof(DownSmem), s>>>(a, p);
   }
   return cudaGetLastError();
+}
+
+// Blocks of the cooperative sort on the current device (0: the multi-kernel
+// sort is used).
+static int coop_grid() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  return g_coop_grid[dev];
+}
+
+// The whole sort in one cooperative launch of G blocks; the digit tables
+// (2 x G x 256) live in a.bsum.
+static cudaError_t run_sort_coop(const SortArgs &a, CoopBar *bar, int G, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(CoopBar), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(kCoopThreads);
+  cfg.dynamicSmemBytes = sizeof(CoopSmem);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_sort_coop, a, bar);
+}
+
+// One sort: cooperative when the device allows it and the table fits
+// (table_rows rows of 256 counts available in a.bsum), else multi-kernel
+// (hist_done: the global histograms are already in a.hist).
+static cudaError_t sort_any(const SortArgs &a, CoopBar *bar, long long table_rows, cudaStream_t s,
+                            bool hist_done = false) {
+  const int G = coop_grid();
+  if (G > 0 && 2LL * G <= table_rows) return run_sort_coop(a, bar, G, s);
+  return run_sort(a, s, hist_done);
 }
 
 // ---- exclusive scan of pair counts in depth order -> emit offsets --------
@@ -1051,7 +1289,10 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.pkey = region<uint32_t>(p, ws, R_PKEY_A);
   ea.pval = region<uint32_t>(p, ws, R_PVAL_A);
   ea.hist = &hdr->hist[1][0][0];
-  ea.passes = pair_passes;
+  // the cooperative pair sort counts its own digits: the emit's histograms
+  // are only needed by the multi-kernel sort
+  const bool coop = coop_grid() > 0 && 2LL * coop_grid() <= (long long)p->sort_blocks * kSortSub;
+  ea.passes = coop ? 0 : pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
   ea.bigq = region<uint32_t>(p, ws, R_BIGQ);
@@ -1090,7 +1331,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.passes = pair_passes;
   t.digit_bits = pair_bits;
   t.status = &hdr->status;
-  e = run_sort(t, s, /*hist_done=*/true);
+  e = sort_any(t, reinterpret_cast<CoopBar *>(hdr->coop_bar), (long long)p->sort_blocks * kSortSub,
+               s, /*hist_done=*/!coop);
   if (e != cudaSuccess) return e;
   // 5. ranges (the pointer pair lives in the header's spare words)
   uint2 *ranges = region<uint2>(p, ws, R_RANGES);
@@ -1113,7 +1355,10 @@ static cudaError_t depth_sort_and_count(const gs_plan *p, void *ws, const SortAr
   if ((e = cudaStreamWaitEvent(ss->st, ss->fork, 0)) != cudaSuccess) return e;
   if ((e = launch_count_pairs(p, ws, ss->st)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(ss->join, ss->st)) != cudaSuccess) return e;
-  if ((e = run_sort(d, s)) != cudaSuccess) return e;
+  Hdr *hdr = region<Hdr>(p, ws, R_HDR);
+  if ((e = sort_any(d, reinterpret_cast<CoopBar *>(hdr->coop_bar),
+                    (long long)p->sort_blocks * kSortSub, s)) != cudaSuccess)
+    return e;
   return cudaStreamWaitEvent(s, ss->join, 0);
 }
 
@@ -1145,7 +1390,8 @@ cudaError_t launch_sort_indices(const gs_plan *p, void *ws, const uint32_t *keys
   d.digit_bits = 8;
   d.no_skip = 1;                          // four passes: the result ends in buffer 0
   d.status = &hdr->status;
-  return run_sort(d, s);
+  return sort_any(d, reinterpret_cast<CoopBar *>(hdr->coop_bar), (long long)p->sort_blocks * kSortSub,
+                  s);
 }
 
 // --------------------------------------------------------------------------
@@ -1171,6 +1417,7 @@ struct StaticHdr {
   uint32_t skip[4];
   uint32_t sel;
   uint32_t status;
+  uint32_t coop_bar[2];
 };
 
 constexpr size_t kStaticHdrBytes = (sizeof(StaticHdr) + 255) & ~size_t(255);
@@ -1256,7 +1503,10 @@ extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_
   a.blocks = g_sort_blocks < kStaticBlocks ? g_sort_blocks : kStaticBlocks;
   a.no_skip = 1;
   a.status = &h->status;
-  return run_sort(a, stream) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  return sort_any(a, reinterpret_cast<CoopBar *>(h->coop_bar), (long long)kStaticBlocks * kSortSub,
+                  stream) == cudaSuccess
+             ? GS_OK
+             : GS_ERR_CUDA;
 }
 
 // Status word of the last gs_sort_pairs_static on the current device (a
@@ -1279,4 +1529,10 @@ extern "C" gs_status gs_sort_pairs_static_status(uint32_t *host_status, cudaStre
     return GS_ERR_CUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return GS_ERR_CUDA;
   return (gs_status)*host_status;
+}
+
+// Whether the sorts run as one cooperative launch each on the current device.
+extern "C" int32_t gs_sort_is_cooperative(void) {
+  gs::init_grids();
+  return gs::coop_grid() > 0 ? 1 : 0;
 }

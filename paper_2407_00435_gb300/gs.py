@@ -120,6 +120,8 @@ def _load():
     lib.gs_sort_pairs_static.restype = s
     lib.gs_sort_pairs_static_status.argtypes = [p, p]
     lib.gs_sort_pairs_static_status.restype = s
+    lib.gs_sort_is_cooperative.argtypes = []
+    lib.gs_sort_is_cooperative.restype = s
     return lib
 
 
@@ -388,10 +390,14 @@ class Renderer:
         passes = min(4, (tile_bits + want - 1) // want)
         # views, levels (+ level rows), project, pair count
         project = 1 + (2 if fov else 0) + (2 if self.n > 0 else 0)
-        # depth sort (hist, scan, 4 passes of upsweep + scan + downsweep),
-        # offsets (upsweep, scan, downsweep), emit + large-item emit, pair
-        # sort (scan + 3 kernels per pass), ranges
-        sort = 0 if self.n == 0 else (2 + 4 * 3) + 3 + 2 + (1 + 3 * passes) + 1
+        # depth sort (one cooperative launch, or hist, scan and 4 passes of
+        # upsweep + scan + downsweep), offsets (upsweep, scan, downsweep),
+        # emit + large-item emit, pair sort (one cooperative launch, or scan
+        # + 3 kernels per pass), ranges
+        if _lib.gs_sort_is_cooperative():
+            sort = 0 if self.n == 0 else 1 + 3 + 2 + 1 + 1
+        else:
+            sort = 0 if self.n == 0 else (2 + 4 * 3) + 3 + 2 + (1 + 3 * passes) + 1
         render = 1 + (1 if stats and self.n > 0 else 0)
         if self.cfg.chunk > 0 and not stats and self.T_tiles > 0:
             render += 1     # work list of the chunked render

@@ -95,6 +95,11 @@ def compare_grads(name, got, ref):
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     print(f"[grad {name}] elements {ref.size}: worst err/tol {ratio.max():.3g} at {worst} "
           f"(got {got[worst]:.6g}, ref {ref[worst]:.6g}); 2-norm rel {rel:.3g}")
+    if not np.all(err <= tol):
+        bad = np.argwhere(err > tol)[:5]
+        for i, j in bad:
+            print(f"  beyond: [{i},{j}] got {got[i, j]:.6g} ref {ref[i, j]:.6g} row max "
+                  f"{row[i, 0]:.3g} group max {gmax:.3g} tol {tol[i, j]:.3g}")
     assert np.all(err <= tol), (f"{name}: {int((err > tol).sum())} elements beyond "
                                 f"1e-3 |r| + {ROW_EPS} row max + {GROUP_EPS} group max")
     return rel
