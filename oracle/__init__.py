@@ -118,7 +118,7 @@ def lib():
         L.orc_render_brute.argtypes = [C.c_int, C.c_int, p, C.c_int, p, p, p, p, p, p, p,
                                        p, p, p]
         L.orc_backward.argtypes = [C.c_int, p, p, p, p, p, C.c_int, C.c_int, p, C.c_int,
-                                   p, p, p, p, p, p, p, p, p, p, p, p]
+                                   p, p, p, p, p, p, p, p, p, p, p, p, p]
         _lib = L
     return _lib
 
@@ -372,6 +372,13 @@ class Grads:
     sh: np.ndarray
     opac_lv: np.ndarray | None
     dc_lv: np.ndarray | None
+    # sum of |term| behind each element (same keys), or None
+    mag: dict | None = None
+
+
+class _GradMag(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("means", "scales", "quats", "opac", "sh", "opac_lv",
+                                          "dc_lv")]
 
 
 def backward(scene, cams, tile, bins: Bins, dL_drgb, fov: FovArrays | None = None,
@@ -393,12 +400,21 @@ def backward(scene, cams, tile, bins: Bins, dL_drgb, fov: FovArrays | None = Non
     ddl = np.zeros((L - 1, n, 3)) if (fov is not None and fov.dc_lv is not None) else None
     fs = fov.struct() if fov is not None else None
     bgv = _c64(bg)
+    mag = {k: np.zeros_like(v) for k, v in (("means", dm), ("scales", ds), ("quats", dq),
+                                            ("opac", do), ("sh", dh))}
+    if dol is not None:
+        mag["opac_lv"] = np.zeros_like(dol)
+    if ddl is not None:
+        mag["dc_lv"] = np.zeros_like(ddl)
+    ms = _GradMag(*[_ptr(mag.get(k)) for k in ("means", "scales", "quats", "opac", "sh",
+                                                "opac_lv", "dc_lv")])
     rc = lib().orc_backward(n, m.ctypes.data, s.ctypes.data, q.ctypes.data, o.ctypes.data,
                             h.ctypes.data, scene.sh_degree, V, C.addressof(cs), tile,
                             bins.vals.ctypes.data, bins.ranges.ctypes.data,
                             C.addressof(fs) if fs is not None else None, bgv.ctypes.data,
                             g.ctypes.data, dm.ctypes.data, ds.ctypes.data, dq.ctypes.data,
-                            do.ctypes.data, dh.ctypes.data, _ptr(dol), _ptr(ddl))
+                            do.ctypes.data, dh.ctypes.data, _ptr(dol), _ptr(ddl),
+                            C.addressof(ms))
     if rc != 0:
         raise RuntimeError(f"orc_backward failed: {rc}")
-    return Grads(dm, ds, dq, do, dh, dol, ddl)
+    return Grads(dm, ds, dq, do, dh, dol, ddl, mag)

@@ -573,6 +573,81 @@ static void sh_basis_grad(const double d[3], double dY[16][3]) {
   dY[15][1] = -k3a * (-6.0 * x * y);
 }
 
+/* The basis polynomials and their gradients with every monomial in absolute
+ * value (test bookkeeping: the magnitude of the terms behind a gradient,
+ * see orc_grad_mag). */
+static void sh_basis_abs(const double d[3], double Y[16]) {
+  const double x = fabs(d[0]), y = fabs(d[1]), z = fabs(d[2]);
+  const double PI = 3.14159265358979323846;
+  const double k1 = sqrt(3.0 / (4.0 * PI));
+  const double k2a = 0.5 * sqrt(15.0 / PI);
+  const double k2b = 0.25 * sqrt(5.0 / PI);
+  const double k2c = 0.25 * sqrt(15.0 / PI);
+  const double k3a = 0.25 * sqrt(35.0 / (2.0 * PI));
+  const double k3b = 0.5 * sqrt(105.0 / PI);
+  const double k3c = 0.25 * sqrt(21.0 / (2.0 * PI));
+  const double k3d = 0.25 * sqrt(7.0 / PI);
+  const double k3e = 0.25 * sqrt(105.0 / PI);
+  const double xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = 0.5 / sqrt(PI);
+  Y[1] = +k1 * y;
+  Y[2] = k1 * z;
+  Y[3] = +k1 * x;
+  Y[4] = k2a * x * y;
+  Y[5] = +k2a * y * z;
+  Y[6] = k2b * (2.0 * zz + xx + yy);
+  Y[7] = +k2a * x * z;
+  Y[8] = k2c * (xx + yy);
+  Y[9] = +k3a * y * (3.0 * xx + yy);
+  Y[10] = k3b * x * y * z;
+  Y[11] = +k3c * y * (4.0 * zz + xx + yy);
+  Y[12] = k3d * z * (2.0 * zz + 3.0 * xx + 3.0 * yy);
+  Y[13] = +k3c * x * (4.0 * zz + xx + yy);
+  Y[14] = k3e * z * (xx + yy);
+  Y[15] = +k3a * x * (xx + 3.0 * yy);
+}
+
+static void sh_basis_grad_abs(const double d[3], double dY[16][3]) {
+  const double x = fabs(d[0]), y = fabs(d[1]), z = fabs(d[2]);
+  const double PI = 3.14159265358979323846;
+  const double k1 = sqrt(3.0 / (4.0 * PI));
+  const double k2a = 0.5 * sqrt(15.0 / PI);
+  const double k2b = 0.25 * sqrt(5.0 / PI);
+  const double k2c = 0.25 * sqrt(15.0 / PI);
+  const double k3a = 0.25 * sqrt(35.0 / (2.0 * PI));
+  const double k3b = 0.5 * sqrt(105.0 / PI);
+  const double k3c = 0.25 * sqrt(21.0 / (2.0 * PI));
+  const double k3d = 0.25 * sqrt(7.0 / PI);
+  const double k3e = 0.25 * sqrt(105.0 / PI);
+  const double xx = x * x, yy = y * y, zz = z * z;
+  memset(dY, 0, sizeof(double) * 48);
+  dY[1][1] = +k1;
+  dY[2][2] = k1;
+  dY[3][0] = +k1;
+  dY[4][0] = k2a * y;  dY[4][1] = k2a * x;
+  dY[5][1] = +k2a * z; dY[5][2] = +k2a * y;
+  dY[6][0] = +2.0 * k2b * x; dY[6][1] = +2.0 * k2b * y; dY[6][2] = 4.0 * k2b * z;
+  dY[7][0] = +k2a * z; dY[7][2] = +k2a * x;
+  dY[8][0] = 2.0 * k2c * x; dY[8][1] = +2.0 * k2c * y;
+  dY[9][0] = +k3a * 6.0 * x * y;
+  dY[9][1] = +k3a * (3.0 * xx + 3.0 * yy);
+  dY[10][0] = k3b * y * z; dY[10][1] = k3b * x * z; dY[10][2] = k3b * x * y;
+  dY[11][0] = +k3c * (+2.0 * x * y);
+  dY[11][1] = +k3c * (4.0 * zz + xx + 3.0 * yy);
+  dY[11][2] = +k3c * (8.0 * y * z);
+  dY[12][0] = k3d * (+6.0 * x * z);
+  dY[12][1] = k3d * (+6.0 * y * z);
+  dY[12][2] = k3d * (6.0 * zz + 3.0 * xx + 3.0 * yy);
+  dY[13][0] = +k3c * (4.0 * zz + 3.0 * xx + yy);
+  dY[13][1] = +k3c * (+2.0 * x * y);
+  dY[13][2] = +k3c * (8.0 * x * z);
+  dY[14][0] = k3e * 2.0 * x * z;
+  dY[14][1] = +k3e * 2.0 * y * z;
+  dY[14][2] = k3e * (xx + yy);
+  dY[15][0] = +k3a * (3.0 * xx + 3.0 * yy);
+  dY[15][1] = +k3a * (+6.0 * x * y);
+}
+
 static void quat_rot(const double *q, double r[9], double qn[4], double *qnorm) {
   double w = q[0], x = q[1], y = q[2], z = q[3];
   double n = sqrt(w * w + x * x + y * y + z * z);
@@ -1090,7 +1165,8 @@ static void backward_acc(int n, const double *vp, const double *opac,
                          const uint32_t *vals, int64_t s, int64_t e,
                          const orc_fov *fov, int lvl, double px, double py,
                          const double g[3], const double bg[3], g2d_t *g2,
-                         double *dop_lv, double *dcol_lv, int L, int64_t nitems) {
+                         double *dop_lv, double *dcol_lv, int L, int64_t nitems,
+                         g2d_t *g2a, double *dopa_lv, double *dcola_lv) {
   /* forward pass recording the blended points */
   int64_t cap = e - s > 0 ? e - s : 1;
   int64_t *bk = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
@@ -1127,11 +1203,15 @@ static void backward_acc(int n, const double *vp, const double *opac,
     int i = (int)(id % (uint32_t)n);
     const double *pv = &vp[(int64_t)id * ORC_NVAL];
     double a = ba[j], Ti = bT[j];
-    double dalpha = 0.0;
+    double dalpha = 0.0, dalpha_a = 0.0;
     for (int ch = 0; ch < 3; ++ch) {
       double dc = Ti * a * g[ch];
       dcol_lv[((int64_t)(lvl - 1) * nitems + id) * 3 + ch] += dc;
       dalpha += g[ch] * (Ti * bc[3 * j + ch] - S[ch] / (1.0 - a));
+      if (g2a) {
+        dcola_lv[((int64_t)(lvl - 1) * nitems + id) * 3 + ch] += fabs(dc);
+        dalpha_a += fabs(g[ch]) * (Ti * bc[3 * j + ch] + S[ch] / (1.0 - a));
+      }
     }
     for (int ch = 0; ch < 3; ++ch) S[ch] += Ti * a * bc[3 * j + ch];
     if (bcl[j]) continue; /* clamped at 0.99: no gradient to o or geometry */
@@ -1146,9 +1226,156 @@ static void backward_acc(int n, const double *vp, const double *opac,
     g2[id].dconic[0] += dpow * (-0.5 * dx * dx);
     g2[id].dconic[1] += dpow * (-dx * dy);
     g2[id].dconic[2] += dpow * (-0.5 * dy * dy);
+    if (g2a) {
+      /* the same terms in absolute value (test bookkeeping, see orc_grad_mag) */
+      double dpa = dalpha_a * a;
+      dopa_lv[(int64_t)(lvl - 1) * nitems + id] += dalpha_a * ex;
+      g2a[id].dmu2[0] += dpa * (fabs(pv[ORC_CA] * dx) + fabs(pv[ORC_CB] * dy));
+      g2a[id].dmu2[1] += dpa * (fabs(pv[ORC_CB] * dx) + fabs(pv[ORC_CC] * dy));
+      g2a[id].dconic[0] += dpa * (0.5 * dx * dx);
+      g2a[id].dconic[1] += dpa * fabs(dx * dy);
+      g2a[id].dconic[2] += dpa * (0.5 * dy * dy);
+    }
   }
   (void)L;
   free(bk); free(ba); free(bT); free(bc); free(bcl);
+}
+
+/* The chain of one item to its point's parameters with every term in
+ * absolute value (test bookkeeping): a bound of the sum of the magnitudes of
+ * the terms each gradient element sums, the scale of its rounding error in
+ * a finite-precision evaluation.  Inputs: the absolute 2D and per-level
+ * sums of the item (ga, dopa, dcola); adds into mag. */
+static void chain_item_abs(const item_t *it, const orc_cam *c, const double *shi, int S, int L,
+                           const orc_fov *fov, int n, int i, const double *scales,
+                           const g2d_t *ga, const double *dopa, const double *dcola,
+                           int64_t nitems, int64_t id, const orc_grad_mag *mag) {
+  double R[9];
+  for (int k = 0; k < 9; ++k) R[k] = fabs((double)c->R[k]);
+  double Ya[16];
+  sh_basis_abs(it->dir, Ya);
+  double dcb[3] = {0, 0, 0};
+  for (int l = 1; l <= L; ++l) {
+    double dop_l = dopa[(int64_t)(l - 1) * nitems + id];
+    const double *dc = &dcola[((int64_t)(l - 1) * nitems + id) * 3];
+    if (l >= 2 && fov && fov->opacity_lv) {
+      if (mag->opac_lv) mag->opac_lv[(int64_t)(l - 2) * n + i] += dop_l;
+    } else if (mag->opac) {
+      mag->opac[i] += dop_l;
+    }
+    if (l >= 2 && fov && fov->dc_lv) {
+      for (int ch = 0; ch < 3; ++ch) {
+        if (mag->dc_lv) mag->dc_lv[((int64_t)(l - 2) * n + i) * 3 + ch] += Y00 * dc[ch];
+        if (mag->sh)
+          for (int k = 1; k < S; ++k) mag->sh[(int64_t)3 * S * i + 3 * k + ch] += Ya[k] * dc[ch];
+      }
+    } else {
+      for (int ch = 0; ch < 3; ++ch) dcb[ch] += dc[ch];
+    }
+  }
+  double dY[16];
+  for (int k = 0; k < 16; ++k) dY[k] = 0.0;
+  for (int ch = 0; ch < 3; ++ch)
+    for (int k = 0; k < S; ++k) {
+      if (mag->sh) mag->sh[(int64_t)3 * S * i + 3 * k + ch] += Ya[k] * dcb[ch];
+      dY[k] += fabs(shi[3 * k + ch]) * dcb[ch];
+    }
+  if (fov && fov->dc_lv)
+    for (int l = 2; l <= L; ++l) {
+      const double *dc = &dcola[((int64_t)(l - 1) * nitems + id) * 3];
+      for (int ch = 0; ch < 3; ++ch)
+        for (int k = 1; k < S; ++k) dY[k] += fabs(shi[3 * k + ch]) * dc[ch];
+    }
+  double gY[16][3];
+  sh_basis_grad_abs(it->dir, gY);
+  double ddir[3] = {0, 0, 0};
+  for (int k = 1; k < S; ++k)
+    for (int a = 0; a < 3; ++a) ddir[a] += dY[k] * gY[k][a];
+  double dd = ddir[0] * fabs(it->dir[0]) + ddir[1] * fabs(it->dir[1]) + ddir[2] * fabs(it->dir[2]);
+  double dm[3];
+  for (int a = 0; a < 3; ++a) dm[a] = (ddir[a] + dd * fabs(it->dir[a])) / it->dist;
+  /* conic -> 2D covariance -> T, Sigma -> M -> scales, rotation */
+  double Q[4] = {fabs(it->conic[0]), fabs(it->conic[1]), fabs(it->conic[1]), fabs(it->conic[2])};
+  double dQ[4] = {ga->dconic[0], 0.5 * ga->dconic[1], 0.5 * ga->dconic[1], ga->dconic[2]};
+  double tmp[4], dS2[4];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) tmp[2 * a + b] = dQ[2 * a] * Q[b] + dQ[2 * a + 1] * Q[2 + b];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) dS2[2 * a + b] = Q[2 * a] * tmp[b] + Q[2 * a + 1] * tmp[2 + b];
+  double Ta[6], Sa[9], Ma[9], ra[9];
+  for (int k = 0; k < 6; ++k) Ta[k] = fabs(it->T[k]);
+  for (int k = 0; k < 9; ++k) { Sa[k] = fabs(it->Sig[k]); Ma[k] = fabs(it->M[k]); ra[k] = fabs(it->r[k]); }
+  double TS[6];
+  for (int a = 0; a < 2; ++a)
+    for (int k = 0; k < 3; ++k) {
+      double acc = 0.0;
+      for (int j = 0; j < 3; ++j) acc += Ta[3 * a + j] * Sa[3 * j + k];
+      TS[3 * a + k] = acc;
+    }
+  double dT[6];
+  for (int a = 0; a < 2; ++a)
+    for (int k = 0; k < 3; ++k) dT[3 * a + k] = 2.0 * (dS2[2 * a] * TS[k] + dS2[2 * a + 1] * TS[3 + k]);
+  double dSig[9];
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) {
+      double acc = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) acc += Ta[3 * a + j] * dS2[2 * a + b] * Ta[3 * b + k];
+      dSig[3 * j + k] = acc;
+    }
+  double dM[9];
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) {
+      double acc = 0.0;
+      for (int l = 0; l < 3; ++l) acc += (dSig[3 * j + l] + dSig[3 * l + j]) * Ma[3 * l + k];
+      dM[3 * j + k] = acc;
+    }
+  const double *s3 = &scales[3 * i];
+  double dR[9];
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) {
+      if (mag->scales) mag->scales[3 * i + k] += dM[3 * j + k] * ra[3 * j + k];
+      dR[3 * j + k] = dM[3 * j + k] * fabs(s3[k]);
+    }
+  double w = fabs(it->qn[0]), x = fabs(it->qn[1]), y = fabs(it->qn[2]), z = fabs(it->qn[3]);
+  double dq[4];
+  dq[0] = 2.0 * (z * dR[1] + y * dR[2] + z * dR[3] + x * dR[5] + y * dR[6] + x * dR[7]);
+  dq[1] = 2.0 * (y * dR[1] + z * dR[2] + y * dR[3] + 2.0 * x * dR[4] + w * dR[5] + z * dR[6] +
+                 w * dR[7] + 2.0 * x * dR[8]);
+  dq[2] = 2.0 * (2.0 * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] + w * dR[6] +
+                 z * dR[7] + 2.0 * y * dR[8]);
+  dq[3] = 2.0 * (2.0 * z * dR[0] + w * dR[1] + x * dR[2] + w * dR[3] + 2.0 * z * dR[4] +
+                 y * dR[5] + x * dR[6] + y * dR[7]);
+  if (it->qnorm > 0.0 && mag->quats) {
+    double dot = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
+    mag->quats[4 * i + 0] += (dq[0] + dot * w) / it->qnorm;
+    mag->quats[4 * i + 1] += (dq[1] + dot * x) / it->qnorm;
+    mag->quats[4 * i + 2] += (dq[2] + dot * y) / it->qnorm;
+    mag->quats[4 * i + 3] += (dq[3] + dot * z) / it->qnorm;
+  }
+  /* T = J W -> J -> camera-space mean; 2D mean -> camera-space mean */
+  double dJ[6];
+  for (int a = 0; a < 2; ++a)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += dT[3 * a + k] * R[3 * j + k];
+      dJ[3 * a + j] = acc;
+    }
+  double pz = fabs(it->pc[2]), px = fabs(it->pc[0]), py = fabs(it->pc[1]);
+  double fx = fabs(c->fx), fy = fabs(c->fy), xcl = fabs(it->xcl), ycl = fabs(it->ycl);
+  double dpc[3] = {0, 0, 0};
+  dpc[2] += dJ[0] * fx / (pz * pz) + dJ[4] * fy / (pz * pz) + dJ[2] * 2.0 * fx * xcl / (pz * pz * pz) +
+            dJ[5] * 2.0 * fy * ycl / (pz * pz * pz);
+  double dxcl = dJ[2] * fx / (pz * pz), dycl = dJ[5] * fy / (pz * pz);
+  if (it->clx) dpc[2] += dxcl * it->limx; else dpc[0] += dxcl;
+  if (it->cly) dpc[2] += dycl * it->limy; else dpc[1] += dycl;
+  double du = ga->dmu2[0], dv = ga->dmu2[1];
+  dpc[0] += du * fx / pz;
+  dpc[1] += dv * fy / pz;
+  dpc[2] += du * fx * px / (pz * pz) + dv * fy * py / (pz * pz);
+  if (mag->means)
+    for (int a = 0; a < 3; ++a)
+      mag->means[3 * i + a] += dm[a] + R[a] * dpc[0] + R[3 + a] * dpc[1] + R[6 + a] * dpc[2];
 }
 
 int orc_backward(int n, const double *means, const double *scales,
@@ -1158,7 +1385,7 @@ int orc_backward(int n, const double *means, const double *scales,
                  const orc_fov *fov, const double bg[3],
                  const double *dL_drgb, double *d_means, double *d_scales,
                  double *d_quats, double *d_opac, double *d_sh,
-                 double *d_opac_lv, double *d_dc_lv) {
+                 double *d_opac_lv, double *d_dc_lv, const orc_grad_mag *mag) {
   int S = (sh_degree + 1) * (sh_degree + 1);
   int L = (fov && fov->n_levels > 1) ? fov->n_levels : 1;
   int64_t nitems = (int64_t)V * n;
@@ -1174,6 +1401,14 @@ int orc_backward(int n, const double *means, const double *scales,
   double *dop = (double *)calloc((size_t)nitems * L, sizeof(double));
   double *dcol = (double *)calloc((size_t)nitems * L * 3, sizeof(double));
   if (!vis || !vp || !items || !g2 || !dop || !dcol) return -1;
+  g2d_t *g2a = NULL;
+  double *dopa = NULL, *dcola = NULL;
+  if (mag) {
+    g2a = (g2d_t *)calloc((size_t)nitems, sizeof(g2d_t));
+    dopa = (double *)calloc((size_t)nitems * L, sizeof(double));
+    dcola = (double *)calloc((size_t)nitems * L * 3, sizeof(double));
+    if (!g2a || !dopa || !dcola) return -1;
+  }
   for (int v = 0; v < V; ++v)
     for (int i = 0; i < n; ++i) {
       int64_t id = (int64_t)v * n + i;
@@ -1204,10 +1439,10 @@ int orc_backward(int n, const double *means, const double *scales,
         double wA = fp.in_band ? fp.w : 1.0;
         for (int ch = 0; ch < 3; ++ch) { gA[ch] = wA * g[ch]; gB[ch] = (1.0 - wA) * g[ch]; }
         backward_acc(n, vp, opac, vals, s, e, fov, fp.level, x + 0.5, y + 0.5,
-                     gA, bg, g2, dop, dcol, L, nitems);
+                     gA, bg, g2, dop, dcol, L, nitems, g2a, dopa, dcola);
         if (fp.in_band)
           backward_acc(n, vp, opac, vals, s, e, fov, fp.level - 1, x + 0.5, y + 0.5,
-                       gB, bg, g2, dop, dcol, L, nitems);
+                       gB, bg, g2, dop, dcol, L, nitems, g2a, dopa, dcola);
       }
     tb += (int64_t)tx * ty;
     pb0 += (int64_t)c->width * c->height;
@@ -1220,6 +1455,15 @@ int orc_backward(int n, const double *means, const double *scales,
   memset(d_sh, 0, sizeof(double) * 3 * (size_t)S * n);
   if (d_opac_lv) memset(d_opac_lv, 0, sizeof(double) * (size_t)(L - 1) * n);
   if (d_dc_lv) memset(d_dc_lv, 0, sizeof(double) * (size_t)(L - 1) * n * 3);
+  if (mag) {
+    if (mag->means) memset(mag->means, 0, sizeof(double) * 3 * (size_t)n);
+    if (mag->scales) memset(mag->scales, 0, sizeof(double) * 3 * (size_t)n);
+    if (mag->quats) memset(mag->quats, 0, sizeof(double) * 4 * (size_t)n);
+    if (mag->opac) memset(mag->opac, 0, sizeof(double) * (size_t)n);
+    if (mag->sh) memset(mag->sh, 0, sizeof(double) * 3 * (size_t)S * n);
+    if (mag->opac_lv) memset(mag->opac_lv, 0, sizeof(double) * (size_t)(L - 1) * n);
+    if (mag->dc_lv) memset(mag->dc_lv, 0, sizeof(double) * (size_t)(L - 1) * n * 3);
+  }
   for (int v = 0; v < V; ++v) {
     const orc_cam *c = &cams[v];
     double R[9];
@@ -1229,6 +1473,8 @@ int orc_backward(int n, const double *means, const double *scales,
       if (!vis[id]) continue;
       item_t *it = &items[id];
       const double *shi = &sh[(int64_t)3 * S * i];
+      if (mag)
+        chain_item_abs(it, c, shi, S, L, fov, n, i, scales, &g2a[id], dopa, dcola, nitems, id, mag);
       /* opacity and colour, per level */
       double dcolor_base[3] = {0, 0, 0};
       for (int l = 1; l <= L; ++l) {
@@ -1372,5 +1618,6 @@ int orc_backward(int n, const double *means, const double *scales,
     }
   }
   free(vis); free(vp); free(items); free(g2); free(dop); free(dcol);
+  free(g2a); free(dopa); free(dcola);
   return 0;
 }

@@ -161,9 +161,20 @@ int orc_render_brute(int n, int V, const orc_cam *cams, int tile,
                      const double bg[3], double *rgb, double *T,
                      int32_t *last);
 
+/* Magnitude of the terms behind each gradient element (test bookkeeping):
+ * the same chain as the gradient with every product and sum taken in
+ * absolute value, i.e. sum |t| over the terms t whose sum is the element.
+ * A finite-precision evaluation errs by about its relative rounding times
+ * this, however much the terms cancel.  Arrays as the gradients', each
+ * nullable. */
+typedef struct {
+  double *means, *scales, *quats, *opac, *sh, *opac_lv, *dc_lv;
+} orc_grad_mag;
+
 /* Analytic FP64 gradient of L = sum(dL_drgb * rgb) with respect to the scene
  * parameters, holding the binning fixed.  Output arrays are overwritten.
- * d_opac_lv / d_dc_lv may be NULL (then fov->opacity_lv must be NULL). */
+ * d_opac_lv / d_dc_lv may be NULL (then fov->opacity_lv must be NULL).
+ * mag (nullable) receives the term magnitudes. */
 int orc_backward(int n, const double *means, const double *scales,
                  const double *quats, const double *opac, const double *sh,
                  int sh_degree, int V, const orc_cam *cams, int tile,
@@ -171,7 +182,7 @@ int orc_backward(int n, const double *means, const double *scales,
                  const orc_fov *fov, const double bg[3],
                  const double *dL_drgb, double *d_means, double *d_scales,
                  double *d_quats, double *d_opac, double *d_sh,
-                 double *d_opac_lv, double *d_dc_lv);
+                 double *d_opac_lv, double *d_dc_lv, const orc_grad_mag *mag);
 
 #ifdef __cplusplus
 }

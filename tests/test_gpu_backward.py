@@ -60,7 +60,7 @@ def test_backward_plain_matches_oracle(gs, orc):
     g, ref = _run(gs, orc, wl)
     for k, rk in (("means", ref.means), ("scales", ref.scales), ("quats", ref.quats),
                   ("opac", ref.opac), ("sh", ref.sh)):
-        _compare(k, g[k], rk)
+        _compare(k, g[k], rk, ref.mag[k])
 
 
 @pytest.mark.parametrize("mv", [False, True])
@@ -75,10 +75,10 @@ def test_backward_foveated_matches_oracle(gs, orc, mv):
     g, ref = _run(gs, orc, wl, fov=f, mv=mvp)
     for k, rk in (("means", ref.means), ("scales", ref.scales), ("quats", ref.quats),
                   ("opac", ref.opac), ("sh", ref.sh)):
-        _compare(k, g[k], rk)
+        _compare(k, g[k], rk, ref.mag[k])
     if mv:
-        _compare("opac_lv", g["opac_lv"], ref.opac_lv)
-        _compare("dc_lv", g["dc_lv"], ref.dc_lv)
+        _compare("opac_lv", g["opac_lv"], ref.opac_lv, ref.mag["opac_lv"])
+        _compare("dc_lv", g["dc_lv"], ref.dc_lv, ref.mag["dc_lv"])
 
 
 def test_autograd_l1_loss(gs, orc):
@@ -108,7 +108,7 @@ def test_autograd_l1_loss(gs, orc):
     r.backward(torch.from_numpy((dL * keep[:, None]).astype(np.float32)).cuda(), out, g2)
     for k, rk in (("means", ref.means), ("scales", ref.scales), ("opac", ref.opac),
                   ("sh", ref.sh)):
-        _compare(k, g2[k].cpu().numpy(), rk)
+        _compare(k, g2[k].cpu().numpy(), rk, ref.mag[k])
     # autograd's gradient equals the C-ABI backward on the full loss
     dLfull = torch.from_numpy(dL.astype(np.float32)).cuda()
     r.backward(dLfull, out, g2)

@@ -124,7 +124,7 @@ def test_backward_after_chunked_forward(gs, orc):
     ref = orc.backward(wl.scene, wl.cams, wl.tile, ob, dL.astype(np.float32).astype(np.float64))
     for k, rk in (("means", ref.means), ("scales", ref.scales), ("quats", ref.quats),
                   ("opac", ref.opac), ("sh", ref.sh)):
-        compare_grads(k, g[k].cpu().numpy(), rk)
+        compare_grads(k, g[k].cpu().numpy(), rk, ref.mag[k])
 
 
 def test_autotuner_picks_a_candidate_and_its_image_matches(gs, orc, tmp_path):

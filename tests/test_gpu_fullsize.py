@@ -122,7 +122,7 @@ def test_backward_full_size_views(gs, orc, foveated):
     ref = orc.backward(wl.scene, cams, 16, ob, dL.astype(np.float64), fa)
     for k, rk in (("means", ref.means), ("scales", ref.scales), ("quats", ref.quats),
                   ("opac", ref.opac), ("sh", ref.sh)):
-        compare_grads(k, g[k].cpu().numpy(), rk)
+        compare_grads(k, g[k].cpu().numpy(), rk, ref.mag[k])
 
 
 def test_batched_views_full_size_subset_autotuned_plan(gs, orc):

@@ -95,7 +95,7 @@ def test_mmfr_backward_matches_oracle(gs, orc):
     ref = orc.backward(wl.scene, wl.cams, wl.tile, ob, dL.astype(np.float32).astype(np.float64), fa)
     for k, rk in (("means", ref.means), ("scales", ref.scales), ("quats", ref.quats),
                   ("opac", ref.opac), ("sh", ref.sh)):
-        _compare(k, g[k].cpu().numpy(), rk)
+        _compare(k, g[k].cpu().numpy(), rk, ref.mag[k])
 
 
 def test_mmfr_argument_checks(gs):

@@ -92,7 +92,7 @@ def test_tight_backward_matches_oracle(gs, orc):
     ref = orc.backward(sc, cams, 16, ob, dL.astype(np.float32).astype(np.float64))
     for k, rk in (("means", ref.means), ("scales", ref.scales), ("quats", ref.quats),
                   ("opac", ref.opac), ("sh", ref.sh)):
-        compare_grads(k, g[k].cpu().numpy(), rk)
+        compare_grads(k, g[k].cpu().numpy(), rk, ref.mag[k])
 
 
 def test_tight_full_size_1080p_bins_exact_and_sampled_pixels(gs, orc):

@@ -94,3 +94,52 @@ def test_gradient_foveated_multiversion_matches_fd(orc):
     fa = orc.FovArrays.from_synth(f, op, dc)
     n_cmp, n_skip = _check(orc, sc, cams, fa, 8)
     assert n_cmp > 0.9 * (n_cmp + n_skip)
+
+
+@pytest.mark.parametrize("fov_mode", [False, True])
+def test_term_magnitudes_bound_every_gradient_element(orc, fov_mode):
+    # Grads.mag is the chain with every term in absolute value: by the
+    # triangle inequality it bounds |gradient| element by element (the GPU
+    # parity bound scales with it), and it exceeds the gradient where terms
+    # cancel, e.g. the quaternion of a needle-shaped point.
+    rng = np.random.default_rng(3100 + fov_mode)
+    sc = synth.blob_scene(rng, 400, n_blobs=5, degree=2, log_scale=(-3.0, 0.6))
+    cams = synth.orbit_cameras(rng, 2, 3.0, [(48, 40), (32, 32)])
+    fa = None
+    if fov_mode:
+        m = synth.nested_levels(rng, sc.n, 3)
+        f = synth.Foveation(3, m, synth.ring_tangents([5, 10]), 6.0, synth.random_gaze(rng, cams))
+        op, dc = synth.multiversion_params(rng, sc, 3)
+        fa = orc.FovArrays.from_synth(f, op, dc)
+    bins = orc.bin_pairs(sc, cams, 16, fa)
+    W, H, _, _ = orc.view_dims(cams, 16)
+    dL = rng.uniform(-1, 1, (int((W * H).sum()), 3))
+    g = orc.backward(sc, cams, 16, bins, dL, fa)
+    groups = {"means": g.means, "scales": g.scales, "quats": g.quats, "opac": g.opac, "sh": g.sh}
+    if fov_mode:
+        groups.update(opac_lv=g.opac_lv, dc_lv=g.dc_lv)
+    for k, v in groups.items():
+        mag = g.mag[k]
+        assert np.all(np.abs(v) <= mag * (1 + 1e-9) + 1e-300), k
+        assert (mag > 0).any(), k
+    # cancellation shows: somewhere the terms are far larger than their sum
+    assert (g.mag["quats"] > 10 * np.abs(g.quats)).any()
+
+
+def test_term_magnitude_of_a_single_term_is_its_value(orc):
+    # one isotropic point, one pixel with a loss weight: d_opac is one term,
+    # so its magnitude equals its absolute value
+    W = H = 16
+    row = np.zeros(20, np.float32)
+    row[[0, 4, 8]] = 1.0
+    row[12:20] = [20.0, 20.0, W / 2, H / 2, W, H, 0.2, 1000.0]
+    cams = row[None]
+    sc = synth.Scene(np.array([[0.0, 0.0, 3.0]], np.float32), np.full((1, 3), 0.05, np.float32),
+                     np.array([[1.0, 0.0, 0.0, 0.0]], np.float32), np.array([0.5], np.float32),
+                     np.full((1, 1, 3), 0.4, np.float32), 0)
+    bins = orc.bin_pairs(sc, cams, 16)
+    dL = np.zeros((W * H, 3))
+    dL[8 * W + 8] = [0.0, -0.7, 0.0]     # one channel, black background: one term
+    g = orc.backward(sc, cams, 16, bins, dL)
+    assert abs(g.opac[0]) > 0
+    np.testing.assert_allclose(g.mag["opac"][0], abs(g.opac[0]), rtol=1e-12)
