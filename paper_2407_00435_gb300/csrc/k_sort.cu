@@ -317,8 +317,6 @@ struct DownSmemT {
   uint64_t bar[2];
 };
 using DownSmem = DownSmemT<kDownThreads>;
-constexpr int kCoopThreads = 1024;    // one block of 32 warps per SM
-using CoopSmem = DownSmemT<kCoopThreads>;
 
 // Bookkeeping of the two halves of the downsweep's double buffer (copies
 // issued and consumed); block-uniform, kept across the passes of one launch.
@@ -560,9 +558,14 @@ __device__ __forceinline__ bool grid_barrier(CoopBar *bar, uint32_t *status, int
 
 constexpr int kCountUnroll = 8;
 
-__global__ void __launch_bounds__(kCoopThreads, 1) k_sort_coop(SortArgs a, CoopBar *bar) {
+// NT threads per block: 1024 with one block per SM (the depth sort, leaving
+// room for the pair count beside it), 512 with two (the pair sort: a block's
+// partitions overlap the other block's).
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a, CoopBar *bar) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  CoopSmem &sm = *reinterpret_cast<CoopSmem *>(dyn_smem);
+  DownSmemT<NT> &sm = *reinterpret_cast<DownSmemT<NT> *>(dyn_smem);
+  constexpr int kCoopThreads = NT;
   constexpr int NQ = kCoopThreads / 256;   // threads per digit in the bases phase
   __shared__ uint32_t s_cnt[256], s_half[NQ][256], s_pre[NQ][256];
   __shared__ uint32_t s_wsum[8];
@@ -655,7 +658,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort_coop(SortArgs a, CoopB
       sm.carry[tid] = wofs + incl - tot + pre;
     }
     __syncthreads();
-    if (p0 < p1 && !downsweep_range<kCoopThreads>(a, pass, executed, sm, db, p0, p1, n)) {
+    if (p0 < p1 && !downsweep_range<NT>(a, pass, executed, sm, db, p0, p1, n)) {
       // leave the grid barrier to time out in the other blocks
       return;
     }
@@ -669,7 +672,8 @@ static int g_sort_blocks = 0;
 static int g_stream_blocks = 0;   // grid of the streaming kernels (emit, offsets, ranges, hist)
 static std::mutex g_grid_mu;
 static bool g_smem_attr[64] = {};
-static int g_coop_grid[64] = {};  // blocks of the cooperative sort per device, 0 = unavailable
+static int g_coop_grid[64] = {};  // SMs of the device if it can launch cooperative sorts, else 0
+static int g_coop_two[64] = {};   // two 512-thread blocks of the cooperative sort fit an SM
 
 static void init_grids() {
   std::lock_guard<std::mutex> lock(g_grid_mu);
@@ -682,13 +686,19 @@ static void init_grids() {
   if (dev >= 0 && dev < 64 && !g_smem_attr[dev]) {
     cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(DownSmem));
-    cudaFuncSetAttribute(k_sort_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(CoopSmem));
-    int coop = 0, pc = 0, nsm = 0;
+    cudaFuncSetAttribute(k_sort_coop<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmemT<1024>));
+    cudaFuncSetAttribute(k_sort_coop<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmemT<512>));
+    int coop = 0, pc = 0, pc2 = 0, nsm = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_sort_coop, kCoopThreads, sizeof(CoopSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_sort_coop<1024>, 1024,
+                                                  sizeof(DownSmemT<1024>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc2, k_sort_coop<512>, 512,
+                                                  sizeof(DownSmemT<512>));
     g_coop_grid[dev] = (coop && pc > 0 && nsm > 0) ? nsm : 0;
+    g_coop_two[dev] = pc2 >= 2 ? 1 : 0;
     cudaGetLastError();
     g_smem_attr[dev] = true;
   }
@@ -719,38 +729,43 @@ static cudaError_t run_sort(const SortArgs &a0, cudaStream_t s, bool hist_done =
 }
 
 // Blocks of the cooperative sort on the current device (0: the multi-kernel
-// sort is used).
-static int coop_grid() {
+// sort is used): one 1024-thread block per SM, or two 512-thread blocks.
+static int coop_grid(bool two = false) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  return g_coop_grid[dev];
+  return two && g_coop_two[dev] ? 2 * g_coop_grid[dev] : g_coop_grid[dev];
 }
 
-// The whole sort in one cooperative launch of G blocks; the digit tables
-// (2 x G x 256) live in a.bsum.
+// The whole sort in one cooperative launch of G blocks of NT threads; the
+// digit tables (2 x G x 256) live in a.bsum.
+template <int NT>
 static cudaError_t run_sort_coop(const SortArgs &a, CoopBar *bar, int G, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(CoopBar), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
-  cfg.blockDim = dim3(kCoopThreads);
-  cfg.dynamicSmemBytes = sizeof(CoopSmem);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sizeof(DownSmemT<NT>);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_sort_coop, a, bar);
+  return cudaLaunchKernelEx(&cfg, k_sort_coop<NT>, a, bar);
 }
 
 // One sort: cooperative when the device allows it and the table fits
 // (table_rows rows of 256 counts available in a.bsum), else multi-kernel
-// (hist_done: the global histograms are already in a.hist).
+// (hist_done: the global histograms are already in a.hist).  `two`: two
+// blocks per SM (nothing runs beside the sort).
 static cudaError_t sort_any(const SortArgs &a, CoopBar *bar, long long table_rows, cudaStream_t s,
-                            bool hist_done = false) {
-  const int G = coop_grid();
-  if (G > 0 && 2LL * G <= table_rows) return run_sort_coop(a, bar, G, s);
+                            bool hist_done = false, bool two = false) {
+  const int G = coop_grid(two);
+  if (G > 0 && 2LL * G <= table_rows) {
+    if (G > coop_grid(false)) return run_sort_coop<512>(a, bar, G, s);
+    return run_sort_coop<1024>(a, bar, G, s);
+  }
   return run_sort(a, s, hist_done);
 }
 
@@ -963,7 +978,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
       r = a.rect[j];
     }
     const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-    const bool huge = valid && (cnt > kBigItem || (TABLE && !has_table(x0, x1, y0, y1)));
+    // slots with no pairs (invisible ones hold stale rectangles) are never
+    // queued for the large-item emit
+    const bool huge = valid && cnt > 0 && (cnt > kBigItem || (TABLE && !has_table(x0, x1, y0, y1)));
     const uint32_t hb = __ballot_sync(0xffffffffu, huge);
     if (hb) {
       uint32_t qb = 0;
@@ -1071,6 +1088,7 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
   for (uint32_t qi = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); qi < nbig; qi += warps) {
     const uint32_t k = a.bigq[qi];
     const uint32_t j = items[k];
+    if (a.count[j] == 0u) continue;   // (never queued; an empty slot's rectangle is stale)
     const uint32_t off = a.offsets[k];
     const uint2 r = a.rect[j];
     const ViewDev &vd = a.views[a.view[j]];
@@ -1291,7 +1309,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.hist = &hdr->hist[1][0][0];
   // the cooperative pair sort counts its own digits: the emit's histograms
   // are only needed by the multi-kernel sort
-  const bool coop = coop_grid() > 0 && 2LL * coop_grid() <= (long long)p->sort_blocks * kSortSub;
+  const bool coop = coop_grid(true) > 0 && 2LL * coop_grid(true) <= (long long)p->sort_blocks * kSortSub;
   ea.passes = coop ? 0 : pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
@@ -1332,7 +1350,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.digit_bits = pair_bits;
   t.status = &hdr->status;
   e = sort_any(t, reinterpret_cast<CoopBar *>(hdr->coop_bar), (long long)p->sort_blocks * kSortSub,
-               s, /*hist_done=*/!coop);
+               s, /*hist_done=*/!coop, /*two=*/true);
   if (e != cudaSuccess) return e;
   // 5. ranges (the pointer pair lives in the header's spare words)
   uint2 *ranges = region<uint2>(p, ws, R_RANGES);
@@ -1391,7 +1409,7 @@ cudaError_t launch_sort_indices(const gs_plan *p, void *ws, const uint32_t *keys
   d.no_skip = 1;                          // four passes: the result ends in buffer 0
   d.status = &hdr->status;
   return sort_any(d, reinterpret_cast<CoopBar *>(hdr->coop_bar), (long long)p->sort_blocks * kSortSub,
-                  s);
+                  s, false, /*two=*/true);
 }
 
 // --------------------------------------------------------------------------
@@ -1504,7 +1522,7 @@ extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_
   a.no_skip = 1;
   a.status = &h->status;
   return sort_any(a, reinterpret_cast<CoopBar *>(h->coop_bar), (long long)kStaticBlocks * kSortSub,
-                  stream) == cudaSuccess
+                  stream, false, /*two=*/true) == cudaSuccess
              ? GS_OK
              : GS_ERR_CUDA;
 }
