@@ -231,6 +231,20 @@ def ring_tangents(ring_deg):
     return np.tan(np.radians(np.asarray(ring_deg, np.float64))).astype(np.float32)
 
 
+def pooling_tangents(r0=1.0, k=0.025, r_max=64):
+    """Tangents of the eccentricities (degrees) at which a pooling half-width
+    r0 + k e^2 reaches floor(r0) + 1, ..., r_max: the thresholds of the HVSQ
+    pooling law (Sec. 2.2), float32, ascending.  Returns (tangents, r_base)."""
+    base = int(math.floor(r0))
+    out = []
+    for j in range(base + 1, int(r_max) + 1):
+        e = math.sqrt((j - r0) / k)
+        if e >= 89.0:
+            break
+        out.append(math.tan(math.radians(e)))
+    return np.asarray(out, np.float32), base
+
+
 def random_gaze(rng, cams):
     """Gaze pixel per view, uniform in the central 50% of each axis."""
     w = cams[:, 16].astype(np.float64)
