@@ -422,7 +422,7 @@ def gpu_arm(args):
         steps_x = max(3, min(args.steps, 10))
         for name, fn in (("foveated_stereo", extra_foveated),
                          ("foveated_ce_levels", extra_foveated_ce), ("multi_model_fr", extra_mmfr),
-                         ("fwd_bwd", extra_fwd_bwd),
+                         ("fwd_bwd", extra_fwd_bwd), ("hvsq", extra_hvsq),
                          ("prune_round", extra_prune), ("batched_64_views", extra_batched)):
             if args.only and name not in args.only:
                 continue
@@ -698,6 +698,52 @@ def extra_fwd_bwd(torch, gs, synth, flush, steps):
                          "note": "batched foveated forward+backward against plain per-view "
                                  "forward+backward of the same views; gradient parity of this "
                                  "plan at full size in tests/test_gpu_fullsize.py"}}
+
+
+def extra_hvsq(torch, gs, synth, flush, steps):
+    """HVSQ per quality level (Sec. 2.2; the quality loss of level training,
+    Sec. 4.3) of the foveated stereo frame against the plain render of the
+    same scene, both eyes at 1920^2, and its gradient: the loss a retraining
+    step through the foveated renderer evaluates.  Pooling law r = floor(1 +
+    0.025 e^2) px, regions = the frame's 4 levels (rings at 10/20/35 deg)."""
+    import numpy as np
+    wl = synth.workload(2)
+    sc = gs.scene_to_device(wl.scene)
+    f = gs.fov_to_device(wl.fov)
+    rf = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True, tight=True)
+    rf.fit(sc, f)
+    of = rf.alloc_outputs(fov=True)
+    rf.render(of, fov=True)
+    rp = gs.Renderer(wl.scene.n, 3, wl.cams, tight=True)
+    rp.fit(sc)
+    op = rp.alloc_outputs()
+    rp.render(op)
+    pool_tan, r_base = synth.pooling_tangents()
+    views = [gs.HvsqView(int(c[16]), int(c[17]), wl.fov.gaze[v], float(c[13]), wl.fov.ring_tan,
+                         pool_tan, r_base) for v, c in enumerate(wl.cams)]
+    npx = [v.W * v.H for v in views]
+    out = [torch.empty(v.n_regions, dtype=torch.float64, device="cuda") for v in views]
+    grad = torch.empty_like(of["rgb"])
+
+    def step(with_grad):
+        px = 0
+        for v, o, n in zip(views, out, npx):
+            v(of["rgb"][px:px + n], op["rgb"][px:px + n], o,
+              grad[px:px + n] if with_grad else None)
+            px += n
+
+    ms_fb = _ms(torch, lambda: step(True), steps, 2, flush)
+    ms_f = _ms(torch, lambda: step(False), steps, 2, flush)
+    per_level = np.stack([o.cpu().numpy() for o in out])
+    del rf, rp, sc, views
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "views": len(npx), "pixels": int(sum(npx)),
+            "hvsq_fwd_bwd_ms": round(ms_fb, 3), "hvsq_fwd_ms": round(ms_f, 3),
+            "gpix_per_s_fwd_bwd": round(sum(npx) / ms_fb / 1e6, 3),
+            "hvsq_per_level_eye0": [float(x) for x in per_level[0]],
+            "hvsq_per_level_eye1": [float(x) for x in per_level[1]],
+            "pooling": "r = floor(1 + 0.025 e^2) px, e in degrees (at most 64)",
+            "reference": "plain render of the same scene (altered: the foveated render)"}
 
 
 def extra_prune(torch, gs, synth, flush, steps):

@@ -361,6 +361,40 @@ gs_status gs_compact_points(gs_plan *plan, void *ws, int64_t n, int32_t sh_degre
 gs_status gs_weighted_scale(int64_t n, const float *scales, const uint32_t *stats, float T,
                             float gamma, double *ws_out, float *d_scales, cudaStream_t stream);
 
+/* ---- eccentricity-aware quality (HVSQ) ---------------------------------- */
+
+/* Bytes of device scratch gs_hvsq needs for a width x height image
+ * (18 FP64 planes of (width + 1) x (height + 1) plus accumulators); 0 for
+ * bad sizes. */
+size_t gs_hvsq_scratch_size(int32_t width, int32_t height);
+
+/* HVSQ of an altered image against a reference (Sec. 2.2, the HVSQ
+ * equation), per quality region (Sec. 4.3), and optionally its gradient:
+ *   HVSQ_g = (1/N_g) sum over the N_g pixels i of region g of
+ *            sum_c (mean_c(a, P_i) - mean_c(r, P_i))^2
+ *                  + (std_c(a, P_i) - std_c(r, P_i))^2
+ * with P_i the square box of half-width r_i around pixel i clipped to the
+ * image, mean / std (population) over the box per colour channel c.
+ * Geometry (FP32, the renderer's ring test): d_i^2 = (x + 0.5 - gaze_x)^2 +
+ * (y + 0.5 - gaze_y)^2; r_i = r_base + #{j : d_i^2 >= (focal pool_tan[j])^2}
+ * (the pooling grows with eccentricity: pool_tan are the tangents of the
+ * eccentricities where it gains a pixel, ascending, n_pool <= 64); region
+ * g_i = #{k : d_i^2 >= (focal ring_tan[k])^2} (quality level - 1; n_rings
+ * <= 7, 0 = one region).
+ *   alt, ref  device (width*height, 3) fp32, row-major (a gs_render image)
+ *   ring_tan, pool_tan  host arrays
+ *   scratch   device, gs_hvsq_scratch_size bytes, 256-byte aligned
+ *   hvsq_out  device, n_rings + 1 doubles, written
+ *   d_alt     device (width*height, 3) fp32 or NULL: gradient of the sum of
+ *             the regions' HVSQs with respect to alt (overwritten); at a
+ *             pooling whose std is 0 the std term contributes 0 (subgradient)
+ * Asynchronous on `stream`.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_hvsq(const float *alt, const float *ref, int32_t width, int32_t height,
+                  float gaze_x, float gaze_y, float focal, const float *ring_tan,
+                  int32_t n_rings, const float *pool_tan, int32_t n_pool, int32_t r_base,
+                  void *scratch, size_t scratch_bytes, double *hvsq_out, float *d_alt,
+                  cudaStream_t stream);
+
 /* ---- measurement -------------------------------------------------------- */
 
 /* Issue-rate probe of the two units the render is bound by (the roofline

@@ -105,3 +105,34 @@ def scale_decay(scales: torch.Tensor, stats: torch.Tensor, T: float, gamma: floa
     (4, N) statistics of the current render (U = tiles_used, treated as a
     constant of the iterate)."""
     return _WeightedScaleFn.apply(scales, stats, float(T), float(gamma))
+
+
+class _HvsqFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, alt, ref, views):
+        a = alt.detach().contiguous()
+        r = ref.detach().contiguous()
+        grad = torch.empty_like(a)
+        total = torch.zeros((), dtype=torch.float64, device=a.device)
+        px = 0
+        for v in views:
+            n = v.W * v.H
+            out = torch.empty(v.n_regions, dtype=torch.float64, device=a.device)
+            v(a[px:px + n], r[px:px + n], out, grad[px:px + n])
+            total = total + out.sum()
+            px += n
+        ctx.save_for_backward(grad)
+        return total.to(alt.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g, None, None
+
+
+def hvsq_loss(alt: torch.Tensor, ref: torch.Tensor, views) -> torch.Tensor:
+    """Sum over views and quality regions of HVSQ (Sec. 2.2; per region as the
+    quality loss of level training, Sec. 4.3) of the (P, 3) image ``alt``
+    against ``ref`` (no gradient), the views' pixels concatenated in order;
+    ``views``: list of gs.HvsqView.  Differentiable in ``alt``."""
+    return _HvsqFn.apply(alt, ref, list(views))

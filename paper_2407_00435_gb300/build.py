@@ -30,6 +30,7 @@ UNITS = {
     "k_backward.cu": [],
     "k_prune.cu": [],
     "k_peak.cu": [],
+    "k_hvsq.cu": [],
 }
 
 

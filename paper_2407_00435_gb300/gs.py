@@ -122,6 +122,11 @@ def _load():
     lib.gs_sort_pairs_static_status.restype = s
     lib.gs_sort_is_cooperative.argtypes = []
     lib.gs_sort_is_cooperative.restype = s
+    lib.gs_hvsq_scratch_size.argtypes = [s, s]
+    lib.gs_hvsq_scratch_size.restype = C.c_size_t
+    lib.gs_hvsq.argtypes = [p, p, s, s, C.c_float, C.c_float, C.c_float, p, s, p, s, s, p,
+                            C.c_size_t, p, p, p]
+    lib.gs_hvsq.restype = s
     return lib
 
 
@@ -240,6 +245,36 @@ def gs_peak_probe(kind, iters, sink, stream=None) -> int:
     _check(_lib.gs_peak_probe(int(kind), int(iters), _ptr(sink), C.byref(ops), _stream(stream)),
            "gs_peak_probe")
     return int(ops.value)
+
+
+class HvsqView:
+    """Scratch and geometry of the HVSQ of one view (Sec. 2.2): width x
+    height image, gaze pixel, focal length (pixels), quality rings (tangents,
+    ``ring_tan``, the regions of Sec. 4.3) and the pooling law's tangent
+    thresholds (``pool_tan``, ``r_base``: synth.pooling_tangents)."""
+
+    def __init__(self, width, height, gaze, focal, ring_tan, pool_tan, r_base, device="cuda"):
+        self.W, self.H = int(width), int(height)
+        self.gaze = (float(gaze[0]), float(gaze[1]))
+        self.focal = float(focal)
+        self.ring_tan = np.ascontiguousarray(ring_tan, np.float32)
+        self.pool_tan = np.ascontiguousarray(pool_tan, np.float32)
+        self.r_base = int(r_base)
+        nb = int(_lib.gs_hvsq_scratch_size(self.W, self.H))
+        if nb == 0:
+            raise GsError(GS_ERR_INVALID_ARG, "gs_hvsq_scratch_size")
+        self.scratch = torch.empty(nb, dtype=torch.uint8, device=device)
+        self.n_regions = len(self.ring_tan) + 1
+
+    def __call__(self, alt, ref, out, d_alt=None, stream=None):
+        """HVSQ per region into ``out`` (device float64, n_regions); the
+        gradient of their sum into ``d_alt`` (device (W*H, 3)) if given."""
+        rt = self.ring_tan.ctypes.data if len(self.ring_tan) else None
+        pt = self.pool_tan.ctypes.data if len(self.pool_tan) else None
+        _check(_lib.gs_hvsq(_ptr(alt), _ptr(ref), self.W, self.H, self.gaze[0], self.gaze[1],
+                            self.focal, rt, len(self.ring_tan), pt, len(self.pool_tan),
+                            self.r_base, _ptr(self.scratch), self.scratch.numel(), _ptr(out),
+                            _ptr(d_alt), _stream(stream)), "gs_hvsq")
 
 
 def gs_get_error(plan_buf, ws, stream=None):
