@@ -13,9 +13,10 @@
 // in FP32 with the expressions of the renderer's ring test.
 //
 // Data path (all FP64 where sums are formed):
-//   fill     per pixel and channel, v = x - 1/2 and v^2 of both images into
-//            12 planes of (H+1) x (W+1) (first row and column zero)
-//   scan     in-place inclusive 2D prefix: summed-area tables, so that a
+//   rows     per pixel and channel, v = x - 1/2 and v^2 of both images,
+//            prefix-summed along the image row into 12 planes of
+//            (H+1) x (W+1) (first row and column zero)
+//   columns  prefix sums down the columns: summed-area tables, so that a
 //            box sum is 4 lookups (shifting by 1/2 keeps the tables small)
 //   stats    per pixel: box statistics, the term, its region's sum; for the
 //            gradient the pooling's coefficients A, B (d L / d x_q =
@@ -69,27 +70,78 @@ __device__ __forceinline__ int count_reached(float d2, float focal, const float 
   return c;
 }
 
-__global__ void k_hvsq_fill(HvsqArgs a) {
-  const long long P = (long long)a.W * a.H;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / a.W), x = (int)(i - (long long)y * a.W);
-    const int g = count_reached(dist2(a, x, y), a.focal, a.ring_tan, a.n_rings);
-    atomicAdd(&a.npix[g], 1ull);
-    const long long o = (long long)(y + 1) * (a.W + 1) + (x + 1);
+// One warp per (image row, channel): the channel's 4 values of each pixel
+// (a - 1/2, its square, r - 1/2, its square), prefix-summed along the row
+// into the 4 planes at (y + 1, x + 1), 256 pixels at a time: lane l sums
+// pixels 8l .. 8l + 7 of the chunk in order, a warp scan of the 32 lane
+// totals gives each lane its offset (FP64 adds are scarce on this GPU: about
+// 2.5 per value instead of the 6 of a shuffle scan per value).  The region
+// count is taken by the channel-0 warps.
+constexpr int kRowRun = 8;
+
+__global__ void k_hvsq_rows(HvsqArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= 3LL * a.H) return;
+  const int y = (int)(warp / 3), c = (int)(warp % 3);
+  const int W1 = a.W + 1;
+  double *P0 = a.S + (4 * c) * a.plane + (long long)(y + 1) * W1 + 1;
+  double carry[4] = {0.0, 0.0, 0.0, 0.0};
+  uint32_t cnt[kMaxRings + 1] = {};   // this lane's pixels per region (channel-0 warps)
+  for (int x0 = 0; x0 < a.W; x0 += 32 * kRowRun) {
+    const int xs = x0 + lane * kRowRun;
+    double run[4][kRowRun];
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double va = (double)a.alt[3 * i + c] - 0.5, vr = (double)a.ref[3 * i + c] - 0.5;
-      a.S[(4 * c + 0) * a.plane + o] = va;
-      a.S[(4 * c + 1) * a.plane + o] = va * va;
-      a.S[(4 * c + 2) * a.plane + o] = vr;
-      a.S[(4 * c + 3) * a.plane + o] = vr * vr;
+    for (int u = 0; u < kRowRun; ++u) {
+      const int x = xs + u;
+      double v0 = 0.0, v2 = 0.0;
+      if (x < a.W) {
+        const long long i = (long long)y * a.W + x;
+        v0 = (double)a.alt[3 * i + c] - 0.5;
+        v2 = (double)a.ref[3 * i + c] - 0.5;
+        if (c == 0) {
+          const int g = count_reached(dist2(a, x, y), a.focal, a.ring_tan, a.n_rings);
+#pragma unroll
+          for (int k = 0; k <= kMaxRings; ++k) cnt[k] += g == k ? 1u : 0u;
+        }
+      }
+      tot[0] += v0;
+      tot[1] += v0 * v0;
+      tot[2] += v2;
+      tot[3] += v2 * v2;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) run[q][u] = tot[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double incl = tot[q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const double off = carry[q] + (incl - tot[q]);
+#pragma unroll
+      for (int u = 0; u < kRowRun; ++u)
+        if (xs + u < a.W) P0[q * a.plane + xs + u] = run[q][u] + off;
+      carry[q] += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (c == 0) {
+#pragma unroll
+    for (int k = 0; k <= kMaxRings; ++k) {
+      uint32_t t = cnt[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0 && t) atomicAdd(&a.npix[k], (unsigned long long)t);
     }
   }
 }
 
 // In-place inclusive prefix along each row of `planes` planes (rows of
-// W + 1 values): one warp per row, 32 values at a time with a carry.
+// W + 1 values): one warp per row, 256 values at a time, lane l summing
+// values 8l .. 8l + 7 in order and a warp scan of the lane totals.
 __global__ void k_scan_rows(double *P, int planes, int W1, int H1, long long plane) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -97,42 +149,58 @@ __global__ void k_scan_rows(double *P, int planes, int W1, int H1, long long pla
   if (warp >= rows) return;
   double *row = P + (warp / H1) * plane + (warp % H1) * (long long)W1;
   double carry = 0.0;
-  for (int x0 = 0; x0 < W1; x0 += 32) {
-    const int x = x0 + lane;
-    double v = x < W1 ? row[x] : 0.0;
+  for (int x0 = 0; x0 < W1; x0 += 32 * kRowRun) {
+    const int xs = x0 + lane * kRowRun;
+    double run[kRowRun];
+    double tot = 0.0;
+#pragma unroll
+    for (int u = 0; u < kRowRun; ++u) {
+      tot += xs + u < W1 ? row[xs + u] : 0.0;
+      run[u] = tot;
+    }
+    double incl = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const double t = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += t;
+      const double t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    v += carry;
-    if (x < W1) row[x] = v;
-    carry = __shfl_sync(0xffffffffu, v, 31);
+    const double off = carry + (incl - tot);
+#pragma unroll
+    for (int u = 0; u < kRowRun; ++u)
+      if (xs + u < W1) row[xs + u] = run[u] + off;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
-// In-place inclusive prefix down each column: one thread per (plane,
-// column), rows read 8 at a time.
-__global__ void k_scan_cols(double *P, int planes, int W1, int H1, long long plane) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)planes * W1) return;
-  double *col = P + (t / W1) * plane + (t % W1);
+// In-place inclusive prefix down each column: one block of 32 x 32 threads
+// per (plane, strip of 32 columns); thread (s, c) owns rows [s L, (s + 1) L)
+// of column c.  Each thread sums its segment, the segment sums are scanned in
+// shared memory, and each thread re-walks its segment from its offset.
+constexpr int kColSegs = 32;
+
+__global__ void __launch_bounds__(32 * kColSegs) k_scan_cols(double *P, int planes, int W1, int H1,
+                                                             long long plane) {
+  __shared__ double s_part[kColSegs][33];
+  const int strips = (W1 + 31) / 32;
+  const int pl = blockIdx.x / strips, strip = blockIdx.x % strips;
+  const int c = threadIdx.x & 31, sg = threadIdx.x >> 5;
+  const int x = strip * 32 + c;
+  const int L = (H1 + kColSegs - 1) / kColSegs;
+  const int y0 = min(H1, sg * L), y1 = min(H1, y0 + L);
+  double *col = P + (long long)pl * plane + x;
+  double sum = 0.0;
+  if (x < W1)
+    for (int y = y0; y < y1; ++y) sum += col[(long long)y * W1];
+  s_part[sg][c] = sum;
+  __syncthreads();
   double acc = 0.0;
-  int y = 0;
-  for (; y + 8 <= H1; y += 8) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = col[(long long)(y + u) * W1];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      acc += v[u];
-      col[(long long)(y + u) * W1] = acc;
+  for (int q = 0; q < sg; ++q) acc += s_part[q][c];
+  if (x < W1)
+    for (int y = y0; y < y1; ++y) {
+      acc += col[(long long)y * W1];
+      col[(long long)y * W1] = acc;
     }
-  }
-  for (; y < H1; ++y) {
-    acc += col[(long long)y * W1];
-    col[(long long)y * W1] = acc;
-  }
+  (void)planes;
 }
 
 __device__ __forceinline__ double box(const double *T, int W1, int x0, int y0, int x1, int y1) {
@@ -145,9 +213,14 @@ constexpr int kStatThreads = 256;
 
 template <bool GRAD>
 __global__ void __launch_bounds__(kStatThreads) k_hvsq_stats(HvsqArgs a) {
-  __shared__ double s_sum[kMaxRings + 1];
-  if (threadIdx.x <= kMaxRings) s_sum[threadIdx.x] = 0.0;
+  __shared__ double s_sum[kStatThreads / 32][kMaxRings + 1];
+  __shared__ double s_w[kMaxRings + 1];   // 1 / pixels of each region
+  if (threadIdx.x <= kMaxRings)
+    s_w[threadIdx.x] = a.npix[threadIdx.x] ? 1.0 / (double)a.npix[threadIdx.x] : 0.0;
   __syncthreads();
+  double acc[kMaxRings + 1];
+#pragma unroll
+  for (int k = 0; k <= kMaxRings; ++k) acc[k] = 0.0;
   const long long P = (long long)a.W * a.H;
   const int W1 = a.W + 1;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
@@ -158,24 +231,29 @@ __global__ void __launch_bounds__(kStatThreads) k_hvsq_stats(HvsqArgs a) {
     const int r = a.r_base + count_reached(d2, a.focal, a.pool_tan, a.n_pool);
     const int x0 = max(0, x - r), x1 = min(a.W - 1, x + r);
     const int y0 = max(0, y - r), y1 = min(a.H - 1, y + r);
-    const double n = (double)(x1 - x0 + 1) * (double)(y1 - y0 + 1);
-    const double w = 1.0 / (double)a.npix[g];
+    const double inv_n = 1.0 / ((double)(x1 - x0 + 1) * (double)(y1 - y0 + 1));
+    const double w = s_w[g];
     double term = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double ma = box(a.S + (4 * c + 0) * a.plane, W1, x0, y0, x1, y1) / n;
-      const double qa = box(a.S + (4 * c + 1) * a.plane, W1, x0, y0, x1, y1) / n;
-      const double mr = box(a.S + (4 * c + 2) * a.plane, W1, x0, y0, x1, y1) / n;
-      const double qr = box(a.S + (4 * c + 3) * a.plane, W1, x0, y0, x1, y1) / n;
-      const double sa = sqrt(fmax(qa - ma * ma, 0.0));
-      const double sr = sqrt(fmax(qr - mr * mr, 0.0));
+      // rounded products (no contraction into the differences below), so
+      // that equal statistics give exactly zero
+      const double ma = __dmul_rn(box(a.S + (4 * c + 0) * a.plane, W1, x0, y0, x1, y1), inv_n);
+      const double qa = __dmul_rn(box(a.S + (4 * c + 1) * a.plane, W1, x0, y0, x1, y1), inv_n);
+      const double mr = __dmul_rn(box(a.S + (4 * c + 2) * a.plane, W1, x0, y0, x1, y1), inv_n);
+      const double qr = __dmul_rn(box(a.S + (4 * c + 3) * a.plane, W1, x0, y0, x1, y1), inv_n);
+      // std = var / sqrt(var), and 1 / std = rsqrt(var) for the gradient
+      const double va = fmax(qa - ma * ma, 0.0), vr = fmax(qr - mr * mr, 0.0);
+      const double ia = va > 0.0 ? rsqrt(va) : 0.0;
+      const double sa = va * ia;
+      const double sr = vr > 0.0 ? vr * rsqrt(vr) : 0.0;
       const double dm = ma - mr, ds = sa - sr;
       term += dm * dm + ds * ds;
       if (GRAD) {
         // d/dx_q of w term_i for q in the box: A + (x_q - 1/2) B
-        double A = 2.0 * w * dm / n, B = 0.0;
+        double A = 2.0 * w * dm * inv_n, B = 0.0;
         if (sa > 0.0) {
-          B = 2.0 * w * ds / (n * sa);
+          B = 2.0 * w * ds * inv_n * ia;
           A -= B * ma;
         }
         double *DA = a.D + (2 * c) * a.plane, *DB = a.D + (2 * c + 1) * a.plane;
@@ -193,10 +271,24 @@ __global__ void __launch_bounds__(kStatThreads) k_hvsq_stats(HvsqArgs a) {
         }
       }
     }
-    atomicAdd(&s_sum[g], term);
+#pragma unroll
+    for (int k = 0; k <= kMaxRings; ++k) acc[k] += g == k ? term : 0.0;
+  }
+  // per region: warp sums, then the block's, then one global add
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k <= kMaxRings; ++k) {
+    double t = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s_sum[wid][k] = t;
   }
   __syncthreads();
-  if (threadIdx.x <= a.n_rings && s_sum[threadIdx.x] != 0.0) atomicAdd(&a.sums[threadIdx.x], s_sum[threadIdx.x]);
+  if (threadIdx.x <= a.n_rings) {
+    double t = 0.0;
+    for (int q = 0; q < kStatThreads / 32; ++q) t += s_sum[q][threadIdx.x];
+    if (t != 0.0) atomicAdd(&a.sums[threadIdx.x], t);
+  }
 }
 
 __global__ void k_hvsq_grad(HvsqArgs a) {
@@ -288,13 +380,13 @@ extern "C" gs_status gs_hvsq(const float *alt, const float *ref, int32_t width, 
                         stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const int W1 = width + 1, H1 = height + 1;
-  k_hvsq_fill<<<grid, 256, 0, stream>>>(a);
-  k_scan_rows<<<(int)(((long long)kValPlanes * H1 * 32 + 255) / 256), 256, 0, stream>>>(a.S, kValPlanes, W1, H1, a.plane);
-  k_scan_cols<<<(int)(((long long)kValPlanes * W1 + 255) / 256), 256, 0, stream>>>(a.S, kValPlanes, W1, H1, a.plane);
+  const int strips = (W1 + 31) / 32;
+  k_hvsq_rows<<<(int)((3LL * height * 32 + 255) / 256), 256, 0, stream>>>(a);
+  k_scan_cols<<<kValPlanes * strips, 32 * kColSegs, 0, stream>>>(a.S, kValPlanes, W1, H1, a.plane);
   if (d_alt) {
     k_hvsq_stats<true><<<grid, kStatThreads, 0, stream>>>(a);
     k_scan_rows<<<(int)(((long long)kDiffPlanes * H1 * 32 + 255) / 256), 256, 0, stream>>>(a.D, kDiffPlanes, W1, H1, a.plane);
-    k_scan_cols<<<(int)(((long long)kDiffPlanes * W1 + 255) / 256), 256, 0, stream>>>(a.D, kDiffPlanes, W1, H1, a.plane);
+    k_scan_cols<<<kDiffPlanes * strips, 32 * kColSegs, 0, stream>>>(a.D, kDiffPlanes, W1, H1, a.plane);
     k_hvsq_grad<<<grid, 256, 0, stream>>>(a);
   } else {
     k_hvsq_stats<false><<<grid, kStatThreads, 0, stream>>>(a);
