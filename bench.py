@@ -42,6 +42,14 @@ def parse(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--only", nargs="*", default=None, help="extras to run")
+    ap.add_argument("--batch-views", type=int, default=None,
+                    help="64-view batch extra: first N views only (profiling a smaller case)")
+    ap.add_argument("--batch-points", type=int, default=None,
+                    help="64-view batch extra: N points instead of 6M (profiling a smaller case)")
+    ap.add_argument("--no-separate-plans", action="store_true",
+                    help="64-view batch extra: skip the separate single-view plans")
+    ap.add_argument("--batch-options", default=None,
+                    help="64-view batch extra: tile,radix_bits,chunk instead of the autotuner")
     return ap.parse_args(argv)
 
 
@@ -427,7 +435,12 @@ def gpu_arm(args):
             if args.only and name not in args.only:
                 continue
             try:
-                extras[name] = fn(torch, gs, synth, flush, steps_x)
+                if name == "batched_64_views":
+                    extras[name] = fn(torch, gs, synth, flush, steps_x, args.batch_views,
+                                      args.batch_points, not args.no_separate_plans,
+                                      args.batch_options)
+                else:
+                    extras[name] = fn(torch, gs, synth, flush, steps_x)
             except Exception as e:  # report, never hide
                 extras[name] = {"error": f"{type(e).__name__}: {e}"}
     res = {
@@ -804,18 +817,30 @@ def extra_prune(torch, gs, synth, flush, steps):
     return res
 
 
-def extra_batched(torch, gs, synth, flush, steps):
+def extra_batched(torch, gs, synth, flush, steps, views=None, points=None, separate=True,
+                  options=None):
     """6M points, 64 views of uneven sizes, half foveated: project + sort +
     render of all views as one CUDA graph (one render launch for all tiles),
-    with the plan options picked by the autotuner."""
+    with the plan options picked by the autotuner (a coordinate search over
+    tile edge, pair-sort digit width and chunk length); the stages timed
+    apart, the bin/sort stage against HBM, and the same views rendered as 64
+    separate single-view plans."""
+    import numpy as np
     from paper_2407_00435_gb300.autotune import autotune
-    wl = synth.workload(4)
+    wl = synth.workload(4, n=points)
+    if views:
+        fv = wl.fov
+        wl = synth.Workload(wl.name + f"_first{views}", wl.scene, wl.cams[:views], wl.tile,
+                            synth.Foveation(fv.n_levels, fv.bound_m, fv.ring_tan, fv.band_px,
+                                            fv.gaze[:views], fv.view_fov[:views]))
     sc = gs.scene_to_device(wl.scene)
     f = gs.fov_to_device(wl.fov)
-    cands = [{"tile": 16, "radix_bits": 0, "chunk": 0}, {"tile": 16, "radix_bits": 7, "chunk": 0},
-             {"tile": 16, "radix_bits": 0, "chunk": 2048}, {"tile": 8, "radix_bits": 0, "chunk": 0}]
-    tune = autotune(sc, wl.scene.n, 3, wl.cams, f, candidates=cands, frames=2, warmup=1,
-                    tight=True)
+    if options:
+        t, rb, ch = (int(x) for x in options.split(","))
+        tune = {"options": {"tile": t, "radix_bits": rb, "chunk": ch}, "trials": "given"}
+    else:
+        tune = autotune(sc, wl.scene.n, 3, wl.cams, f, frames=2, warmup=1, tight=True,
+                        search="coordinate", sweeps=1)
     opt = tune["options"]
     r = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True, tight=True, tile=opt["tile"],
                     radix_bits=opt["radix_bits"], chunk=opt["chunk"])
@@ -829,6 +854,28 @@ def extra_batched(torch, gs, synth, flush, steps):
 
     frame()
     torch.cuda.synchronize()
+    # stages, timed apart (outside the graph)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    st = {"project": [], "bin_sort": [], "render": []}
+    for _ in range(max(2, steps // 2)):
+        flush()
+        ev[0].record()
+        r.project(sc, f)
+        ev[1].record()
+        r.bin_sort()
+        ev[2].record()
+        r.render(out, fov=True)
+        ev[3].record()
+        torch.cuda.synchronize()
+        for q, nm in enumerate(("project", "bin_sort", "render")):
+            st[nm].append(ev[q].elapsed_time(ev[q + 1]))
+    stages = {k: round(float(np.median(v)), 3) for k, v in st.items()}
+    # one more staged frame in an NVTX range (what kernel profiles of this
+    # workload select)
+    torch.cuda.nvtx.range_push("batched_frame")
+    frame()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     graph = torch.cuda.CUDAGraph()
@@ -841,13 +888,66 @@ def extra_batched(torch, gs, synth, flush, steps):
     code, c2 = r.counters()
     ms = _ms(torch, graph.replay, steps, 1, flush)
     code, c3 = r.counters()
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bs_bytes = bin_sort_bytes(r.n * r.V, int(c["n_visible"]), int(c["n_pairs"]), r.T_tiles,
+                              pair_passes(r.T_tiles, opt["radix_bits"]), True, True)
+    bs_gbs = bs_bytes / (stages["bin_sort"] * 1e-3) / 1e9
     res = {"workload": wl.name, "views": len(wl.cams), "pixels": r.P,
            "ms_per_batch": round(ms, 3), "views_per_s": round(len(wl.cams) * 1000 / ms, 2),
            "gpix_per_s": round(r.P / ms / 1e6, 3), "pairs": int(c["n_pairs"]),
            "visible": int(c["n_visible"]), "status": int(code),
            "kernel_launches_in_graph": r.launches_per_frame(fov=True),
+           "stages_ms": stages,
+           "roofline_bin_sort": {"bound": "hbm", "achieved": round(bs_gbs, 1), "peak": hbm,
+                                 "unit": "GB/s", "frac": round(bs_gbs / hbm, 4),
+                                 "bytes_per_batch": int(bs_bytes),
+                                 "peak_source": f"{src} hbm_gbs (copy); of measured"},
            "autotuned": opt, "autotune_trials": tune["trials"]}
-    del r, sc, graph
+    del r, graph, out
+    torch.cuda.empty_cache()
+    if not separate:
+        return res
+    # the same 64 views as separate single-view plans (one plan per view size
+    # and mode, its cameras swapped per view): every view projects all points,
+    # bins and sorts its own pairs, renders its own tiles
+    sides = wl.cams[:, 16].astype(int)
+    vf = wl.fov.view_fov
+    plans = {}
+    per_out = {}
+    for key in sorted(set(zip(sides.tolist(), vf.tolist()))):
+        idx = [v for v in range(len(wl.cams)) if (sides[v], vf[v]) == key]
+        fv = synth.Foveation(wl.fov.n_levels, wl.fov.bound_m, wl.fov.ring_tan, wl.fov.band_px,
+                             wl.fov.gaze[idx[:1]], np.ones(1, np.uint8))
+        rv = gs.Renderer(wl.scene.n, 3, wl.cams[idx[0]:idx[0] + 1], foveated=bool(key[1]),
+                         tight=True, tile=opt["tile"], radix_bits=opt["radix_bits"],
+                         chunk=opt["chunk"])
+        fd = gs.fov_to_device(fv) if key[1] else None
+        kmax = 0
+        for v in idx:
+            rv.set_cameras(wl.cams[v:v + 1])
+            if fd is not None:
+                fd["gaze"].copy_(torch.from_numpy(wl.fov.gaze[v:v + 1]).cuda())
+            kmax = max(kmax, int(rv.fit(sc, fd, headroom=1.05)["n_pairs"]))
+        plans[key] = (rv, fd, idx)
+        per_out[key] = rv.alloc_outputs(fov=bool(key[1]))
+    gaze_dev = {v: torch.from_numpy(wl.fov.gaze[v:v + 1]).cuda() for v in range(len(wl.cams))}
+    cams_dev = {v: gs.cams_device(wl.cams[v:v + 1]) for v in range(len(wl.cams))}
+
+    def per_view():
+        for key, (rv, fd, idx) in plans.items():
+            for v in idx:
+                rv.cams_d.copy_(cams_dev[v])
+                if fd is not None:
+                    fd["gaze"].copy_(gaze_dev[v])
+                rv.project(sc, fd)
+                rv.bin_sort()
+                rv.render(per_out[key], fov=fd is not None)
+
+    ms_pv = _ms(torch, per_view, max(2, steps // 2), 1, flush)
+    res.update({"ms_per_batch_separate_plans": round(ms_pv, 3),
+                "batched_speedup": round(ms_pv / ms, 3)})
+    del plans, per_out, sc
     torch.cuda.empty_cache()
     return res
 

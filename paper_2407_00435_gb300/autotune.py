@@ -2,8 +2,9 @@
 
 For a given scene, set of views and foveation it times complete frames
 (projection, binning and sorting, rendering) for each candidate option set
-and returns the fastest.  Candidates: tile edge (16 or 8 pixels), digit width
-of the pair sort's radix passes, and the heavy-tile chunk length.  Images do
+(a list, or a coordinate search over the options) and returns the fastest.
+Options: tile edge (16 or 8 pixels), digit width of the pair sort's radix
+passes, and the heavy-tile chunk length.  Images do
 not depend on these options (up to float rounding of the chunk merge), so the
 choice is free.  Results can be cached in a JSON file keyed by the workload's
 shape.
@@ -57,19 +58,37 @@ def _time_frames(r: Renderer, sc, fov, frames, warmup):
     return a.elapsed_time(b) / frames
 
 
+# The search space of the coordinate search: each option's values, the
+# first one the starting point.
+SEARCH_SPACE = {"tile": [16, 8], "radix_bits": [0, 5, 6, 7, 8], "chunk": [0, 512, 1024, 2048, 4096]}
+
+
 def autotune(sc: dict, n: int, sh_degree: int, cams, fov: dict | None = None,
              candidates=None, frames: int = 3, warmup: int = 1, cache_path: str | None = None,
-             headroom: float = 1.05, tight: bool = False, verbose: bool = False) -> dict:
-    """Return {"options": best option dict, "ms": its frame time, "trials": [...]}."""
-    key = workload_key(n, sh_degree, cams, fov, tight)
+             headroom: float = 1.05, tight: bool = False, verbose: bool = False,
+             search: str = "list", space: dict | None = None, sweeps: int = 2) -> dict:
+    """Return {"options": best option dict, "ms": its frame time, "trials": [...]}.
+
+    search="list" times every candidate (``candidates`` or the defaults);
+    search="coordinate" walks the search space one option at a time (tile
+    edge, then digit width, then chunk length), keeping the best value of each
+    before moving to the next, for up to ``sweeps`` sweeps or until a sweep
+    improves nothing; every configuration is timed once."""
+    key = workload_key(n, sh_degree, cams, fov, tight) + f";search={search}"
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
         if key in cache:
             return cache[key]
     trials = []
-    for opt in candidates or DEFAULT_CANDIDATES:
+    seen = {}
+
+    def trial(opt):
+        k = (opt["tile"], opt["radix_bits"], opt["chunk"])
+        if k in seen:
+            return seen[k]
         t0 = time.perf_counter()
+        r = None
         try:
             r = Renderer(n, sh_degree, cams, tile=opt["tile"], foveated=fov is not None,
                          radix_bits=opt["radix_bits"], chunk=opt["chunk"], tight=tight)
@@ -83,6 +102,26 @@ def autotune(sc: dict, n: int, sh_degree: int, cams, fov: dict | None = None,
             torch.cuda.empty_cache()
         if verbose:
             print(trials[-1], f"({time.perf_counter() - t0:.1f} s)")
+        seen[k] = trials[-1]["ms"]
+        return seen[k]
+
+    if search == "coordinate":
+        sp = space or SEARCH_SPACE
+        cur = {k: v[0] for k, v in sp.items()}
+        best_ms = trial(cur)
+        for _ in range(sweeps):
+            improved = False
+            for name, values in sp.items():
+                for v in values:
+                    cand = {**cur, name: v}
+                    ms = trial(cand)
+                    if ms is not None and (best_ms is None or ms < best_ms):
+                        best_ms, cur, improved = ms, cand, True
+            if not improved:
+                break
+    else:
+        for opt in candidates or DEFAULT_CANDIDATES:
+            trial(opt)
     ok = [t for t in trials if t["ms"] is not None]
     if not ok:
         raise RuntimeError(f"no candidate fits: {trials}")

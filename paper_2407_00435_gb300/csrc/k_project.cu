@@ -814,8 +814,10 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
     stage_rows(&sm.op[0], 1, a.opac, row0, cnt_rows, 1);
   }
   __syncthreads();
-  const long long i = row0 + tid;
-  uint32_t nvis = 0;
+  // per point: finite parameters, tight-support tau (the largest opacity
+  // any level composites the point with; one value shared by its views)
+  __shared__ uint8_t s_fin[kProjThreads];
+  __shared__ float s_tau[kProjThreads];
   if (tid < cnt_rows) {
     float mu[3], sc[3], q[4];
 #pragma unroll
@@ -825,28 +827,44 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
     const bool fin = all_finite(mu, 3) && all_finite(sc, 3) && all_finite(q, 4) &&
                      isfinite(sm.op[tid]) && all_finite(sm.sh[tid], S * 3);
     if (!fin) atomicAdd(&s_nonfinite, (uint32_t)a.V);
-    // tight support: tau bounds 2 ln(255 o) for the largest opacity any level
-    // composites the point with (one value per point, shared by its views)
     float tau = 0.0f;
     if (a.rec_supp) {
       float o_max = sm.op[tid];
       for (int l = 0; l < a.n_opacity_lv; ++l)
-        o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + i]);
+        o_max = fmaxf(o_max, a.opacity_lv[(long long)l * a.n + row0 + tid]);
       tau = tight_tau(o_max);
     }
-    for (int v = 0; v < a.V; ++v) {
+    s_fin[tid] = fin ? 1 : 0;
+    s_tau[tid] = tau;
+  }
+  __syncthreads();
+  // items (point, view) of the block, consecutive threads on consecutive
+  // slots j = i V + v (coalesced record writes; one view: one point each)
+  uint32_t nvis = 0;
+  const int items = cnt_rows * a.V;
+  for (int k = tid; k < items; k += kProjThreads) {
+    const int pl = a.V == 1 ? k : k / a.V;
+    const int v = k - pl * a.V;
+    const long long i = row0 + pl;
+    float mu[3], sc[3], q[4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { mu[c] = sm.mu[pl][c]; sc[c] = sm.sc[pl][c]; }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = sm.q[pl][c];
+    const bool fin = s_fin[pl] != 0;
+    {
       const long long j = i * a.V + v;
       const gs_camera cam = a.cams[v];
       const ViewDev &vd = a.views[v];
-      Keyed k;
-      if (fin && keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, k)) {
+      Keyed kk;
+      if (fin && keyed_project(mu, sc, q, cam, a.tile, vd.tx, vd.ty, kk)) {
         if (a.rec_supp) {
           // keyed mean and covariance, tau
-          a.rec_supp[j] = make_float4(k.u, k.v, k.a, k.b);
-          a.rec_supp2[j] = make_float2(k.cc, tau);
+          a.rec_supp[j] = make_float4(kk.u, kk.v, kk.a, kk.b);
+          a.rec_supp2[j] = make_float2(kk.cc, s_tau[pl]);
         }
         Rec r;
-        project_value<S>(a, sm, tid, i, mu, cam, vd, k, r);
+        project_value<S>(a, sm, pl, i, mu, cam, vd, kk, r);
         write_rec(a, (unsigned long long)j, r, (uint32_t)i, (uint32_t)v);
         ++nvis;
       } else {
