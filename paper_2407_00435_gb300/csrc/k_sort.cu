@@ -775,6 +775,8 @@ struct ScanArgs {
   const uint32_t *sorted_items[2];
   const uint32_t *sel;
   const uint32_t *count;            // rec_count (by item)
+  uint32_t *sorted_count[2];        // the counts in depth order: the depth sort's free key
+                                    //   buffer (written by the upsweep, read by the rest)
   const unsigned long long *n_items;
   long long capacity;
   uint32_t *offsets;
@@ -792,6 +794,7 @@ __global__ void __launch_bounds__(256) k_offsets_up(ScanArgs a) {
   __shared__ unsigned long long s_w[8];
   const uint32_t n = scan_n(a);
   const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
+  uint32_t *scount = *a.sel ? a.sorted_count[0] : a.sorted_count[1];
   long long p0, p1;
   block_parts(n, a.blocks, blockIdx.x, p0, p1);
   const long long k0 = p0 * kSortPart;
@@ -805,7 +808,11 @@ __global__ void __launch_bounds__(256) k_offsets_up(ScanArgs a) {
       c[u] = idx < k1 ? a.count[items[idx]] : 0u;
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) sum += c[u];
+    for (int u = 0; u < 16; ++u) {
+      const long long idx = base + u * 256 + threadIdx.x;
+      if (idx < k1) scount[idx] = c[u];
+      sum += c[u];
+    }
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
@@ -851,7 +858,7 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
   __shared__ unsigned long long s_w[8];
   __shared__ unsigned long long s_carry;
   const uint32_t n = scan_n(a);
-  const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
+  const uint32_t *scount = *a.sel ? a.sorted_count[0] : a.sorted_count[1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   long long p0, p1;
   block_parts(n, a.blocks, blockIdx.x, p0, p1);
@@ -863,7 +870,7 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       long long idx = base + k;
-      c[k] = idx < (long long)n ? a.count[items[idx]] : 0u;
+      c[k] = idx < (long long)n ? scount[idx] : 0u;
       tsum += c[k];
     }
     unsigned long long incl = tsum;
@@ -900,6 +907,7 @@ struct EmitArgs {
   long long item_capacity;
   const uint32_t *offsets;
   const uint32_t *count;
+  const uint32_t *sorted_count[2];   // counts in depth order (see ScanArgs)
   const uint2 *rect;
   const uint32_t *view;
   const ViewDev *views;
@@ -966,17 +974,39 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
     set_status(a.status, GS_ERR_CAPACITY);
   const long long warps = (long long)gridDim.x * (blockDim.x / 32);
   const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + wl;
+  const uint32_t *scount = *a.sel ? a.sorted_count[0] : a.sorted_count[1];
+  // software pipeline over the warp's groups of 32 items: the next group's
+  // item, offset and count loads, and its rectangle and row-table gathers,
+  // are in flight while this group's pairs are written
+  auto load_item = [&](long long k, uint32_t &j, uint32_t &off, uint32_t &cnt) {
+    j = 0; off = 0xffffffffu; cnt = 0;
+    if (k < n) {
+      j = items[k];
+      off = a.offsets[k];
+      cnt = scount[k];
+    }
+  };
+  auto load_rec = [&](long long k, uint32_t j, uint32_t cnt, uint2 &r, uint4 &t) {
+    r = make_uint2(0u, 0u);
+    t = make_uint4(0u, 0u, 0u, 0u);
+    if (k < n && cnt > 0) {
+      r = a.rect[j];
+      if (TABLE && cnt <= kBigItem) t = a.table[j];
+    }
+  };
+  uint32_t nj, noff, ncnt;
+  uint2 nr;
+  uint4 nt;
+  load_item(wid * 32 + lane, nj, noff, ncnt);
+  load_rec(wid * 32 + lane, nj, ncnt, nr, nt);
   for (long long base = wid * 32; base < n; base += warps * 32) {
     const long long k = base + lane;
     const bool valid = k < n;
-    uint32_t j = 0, cnt = 0, off = 0xffffffffu;
-    uint2 r = make_uint2(0u, 0u);
-    if (valid) {
-      j = items[k];
-      off = a.offsets[k];
-      cnt = a.count[j];
-      r = a.rect[j];
-    }
+    const uint32_t j = nj, off = noff, cnt = ncnt;
+    const uint2 r = nr;
+    const uint4 tload = nt;
+    load_item(base + warps * 32 + lane, nj, noff, ncnt);
+    load_rec(base + warps * 32 + lane, nj, ncnt, nr, nt);
     const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
     // slots with no pairs (invisible ones hold stale rectangles) are never
     // queued for the large-item emit
@@ -989,7 +1019,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
       if (huge) a.bigq[qb + __popc(hb & ltmask)] = (uint32_t)k;
     }
     uint4 tbl = make_uint4(0u, 0u, 0u, 0u);
-    if (TABLE && valid && !huge && cnt > 0) tbl = a.table[j];
+    if (TABLE && valid && !huge && cnt > 0) tbl = tload;
     // the pairs this kernel writes: the warp's items without the queued ones,
     // numbered by a warp scan (queued items take no iterations here)
     const uint32_t ce = (valid && !huge) ? cnt : 0u;
@@ -1270,6 +1300,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.n_items = &hdr->n_visible;
   sa.capacity = p->max_visible;
   sa.offsets = region<uint32_t>(p, ws, R_OFFSETS);
+  sa.sorted_count[0] = d.keys[0];    // the one of the two the depth sort did not end in
+  sa.sorted_count[1] = d.keys[1];
   sa.bsum = reinterpret_cast<unsigned long long *>(bsum + (size_t)p->sort_blocks * kSortSub * 256);
   sa.blocks = G;
   sa.n_pairs = &hdr->n_pairs;
@@ -1291,6 +1323,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.item_capacity = p->max_visible;
   ea.offsets = sa.offsets;
   ea.count = sa.count;
+  ea.sorted_count[0] = sa.sorted_count[0];
+  ea.sorted_count[1] = sa.sorted_count[1];
   ea.rect = region<uint2>(p, ws, R_REC_RECT);
   ea.view = region<uint32_t>(p, ws, R_REC_VIEW);
   ea.views = region<ViewDev>(p, ws, R_VIEWS);
