@@ -50,6 +50,10 @@ def parse(argv=None):
                     help="64-view batch extra: skip the separate single-view plans")
     ap.add_argument("--batch-options", default=None,
                     help="64-view batch extra: tile,radix_bits,chunk instead of the autotuner")
+    ap.add_argument("--fov-points", type=int, default=None,
+                    help="foveated stereo extra: N points instead of 3M (profiling a smaller case)")
+    ap.add_argument("--fwdbwd-views", type=int, default=None,
+                    help="forward+backward extra: first N views only (profiling a smaller case)")
     return ap.parse_args(argv)
 
 
@@ -439,6 +443,10 @@ def gpu_arm(args):
                     extras[name] = fn(torch, gs, synth, flush, steps_x, args.batch_views,
                                       args.batch_points, not args.no_separate_plans,
                                       args.batch_options)
+                elif name == "foveated_stereo":
+                    extras[name] = fn(torch, gs, synth, flush, steps_x, args.fov_points)
+                elif name == "fwd_bwd":
+                    extras[name] = fn(torch, gs, synth, flush, steps_x, args.fwdbwd_views)
                 else:
                     extras[name] = fn(torch, gs, synth, flush, steps_x)
             except Exception as e:  # report, never hide
@@ -477,9 +485,9 @@ def _ms(torch, fn, steps, warmup, flush):
     return total / steps
 
 
-def extra_foveated(torch, gs, synth, flush, steps):
+def extra_foveated(torch, gs, synth, flush, steps, points=None):
     """3M points, 2 eyes at 1920x1920, 4 nested levels: foveated vs plain."""
-    wl = synth.workload(2)
+    wl = synth.workload(2, n=points)
     sc = gs.scene_to_device(wl.scene)
     f = gs.fov_to_device(wl.fov)
     rf = gs.Renderer(wl.scene.n, 3, wl.cams, foveated=True, tight=True)
@@ -621,15 +629,15 @@ def extra_mmfr(torch, gs, synth, flush, steps):
     return res
 
 
-def extra_fwd_bwd(torch, gs, synth, flush, steps):
+def extra_fwd_bwd(torch, gs, synth, flush, steps, views=None):
     """500k points, SH3, 8 views at 1024^2, L1 loss, forward + backward:
     the views foveated in one batched plan (4 nested levels, rings at
     10/20/35 degrees, 32-px band: retraining through the foveated renderer,
     Sec. 4.3) against 8 plain per-view plans, and the plain batched plan."""
     import numpy as np
     from paper_2407_00435_gb300 import autograd as ga
-    wl = synth.workload(3)
-    wf = synth.fov_fwd_bwd_workload()
+    wl = synth.workload(3, views=views)
+    wf = synth.fov_fwd_bwd_workload(views=views)
     sc = gs.scene_to_device(wl.scene)
     f = gs.fov_to_device(wf.fov)
     V = len(wl.cams)
