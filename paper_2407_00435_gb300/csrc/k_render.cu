@@ -236,6 +236,74 @@ __device__ __forceinline__ void composite_fov_a(const uint16_t *list, int nlist,
   }
 }
 
+// Foveated views, warps with a pixel in a blend band (no per-level
+// parameters, no statistics): both accumulators from one evaluation of the
+// quadratic form, the decisions as data flow like composite_plain; a point
+// takes part in accumulator A where its level mask holds the pixel's level,
+// in B where it holds the level below (0 outside bands).
+template <int PX>
+__device__ __forceinline__ void composite_fov_ab(const uint16_t *list, int nlist,
+                                                 const float4 *ra, const float4 *rb,
+                                                 const float4 *rc, const int *rm, int base,
+                                                 const Pix<PX> &pp, Acc (&A)[PX], Acc (&Bq)[PX],
+                                                 uint32_t (&walk_end)[PX]) {
+  const unsigned long long px2 = f2_pack(pp.px, pp.px);
+  unsigned long long py2[PX];
+  uint32_t bitA[PX], bitB[PX];
+#pragma unroll
+  for (int k = 0; k < PX; ++k) {
+    py2[k] = f2_pack(pp.py[k], pp.py[k]);
+    bitA[k] = 1u << (pp.lvl[k] - 1);
+    bitB[k] = pp.lvl[k] >= 2 ? 1u << (pp.lvl[k] - 2) : 0u;
+  }
+#pragma unroll 4
+  for (int li = 0; li < nlist; ++li) {
+    const int q = list[li];
+    const float4 sa = ra[q], sb = rb[q], c = rc[q];
+    const uint32_t pm = (uint32_t)rm[q];
+    const int pos = base + q;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+      float t1, t2;
+      const float sq = eval_s2(px2, py2[k], sa, sb, t1, t2);
+      const float al = alpha_of(__fsub_rn(c.w, sq));
+      const bool in = sq <= sb.z;
+      {
+        const float Tn = A[k].T * (1.0f - al);
+        const bool hit = in && !A[k].done && (pm & bitA[k]) != 0u;
+        if (hit && !(Tn < kTMin)) {
+          const float w = al * A[k].T;
+          A[k].r = fmaf(w, c.x, A[k].r);
+          A[k].g = fmaf(w, c.y, A[k].g);
+          A[k].b = fmaf(w, c.z, A[k].b);
+          A[k].T = Tn;
+          A[k].last = pos;
+        }
+        if (hit && Tn < kTMin) {
+          A[k].done = true;
+          walk_end[k] = pos + 1;
+        }
+      }
+      {
+        const float Tn = Bq[k].T * (1.0f - al);
+        const bool hit = in && !Bq[k].done && (pm & bitB[k]) != 0u;
+        if (hit && !(Tn < kTMin)) {
+          const float w = al * Bq[k].T;
+          Bq[k].r = fmaf(w, c.x, Bq[k].r);
+          Bq[k].g = fmaf(w, c.y, Bq[k].g);
+          Bq[k].b = fmaf(w, c.z, Bq[k].b);
+          Bq[k].T = Tn;
+          Bq[k].last = pos;
+        }
+        if (hit && Tn < kTMin) Bq[k].done = true;
+      }
+      live = live || !A[k].done || !Bq[k].done;
+    }
+    if ((li & 3) == 3 && !__any_sync(0xffffffffu, live)) break;
+  }
+}
+
 // Composites the sorted points [begin, end) of a tile front to back into
 // every accumulator that is not done.  List positions (`last`) are reported
 // relative to `origin`, the first pair of the tile.  Starts and ends with a
@@ -373,10 +441,22 @@ __device__ __forceinline__ void walk(const RenderArgs &a, RSmem<B, FOV, MV, STAT
                  for (int k = 0; k < PX; ++k) nb = nb && Bq[k].done;
                  return nb;
                }())) {
-      // no pixel of the warp needs the second accumulator
+      // no pixel of the warp needs the second accumulator; if every pixel
+      // has the same level the warp's list holds exactly the points that
+      // level composites (the list excludes the others), so no level test
+      if (__any_sync(0xffffffffu, !all_done_here())) {
+        const int lo = sm.wlv[warp] & 0xff, hi = sm.wlv[warp] >> 8;
+        if (lo == hi)
+          composite_plain<PX>(sm.list[warp], sm.woff[warp][SPT * NWS], sm.a, sm.b, sm.c,
+                              (int)(b - origin), pp, A, walk_end);
+        else
+          composite_fov_a<PX>(sm.list[warp], sm.woff[warp][SPT * NWS], sm.a, sm.b, sm.c, sm.m,
+                              (int)(b - origin), pp, A, walk_end);
+      }
+    } else if (FOV && !MV && !STATS) {
       if (__any_sync(0xffffffffu, !all_done_here()))
-        composite_fov_a<PX>(sm.list[warp], sm.woff[warp][SPT * NWS], sm.a, sm.b, sm.c, sm.m,
-                            (int)(b - origin), pp, A, walk_end);
+        composite_fov_ab<PX>(sm.list[warp], sm.woff[warp][SPT * NWS], sm.a, sm.b, sm.c, sm.m,
+                             (int)(b - origin), pp, A, Bq, walk_end);
     } else if (__any_sync(0xffffffffu, !all_done_here())) {
       const int nlist = sm.woff[warp][SPT * NWS];
       const unsigned long long px2 = f2_pack(pp.px, pp.px);
