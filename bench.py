@@ -146,21 +146,26 @@ RENDER_TRAFFIC = "profiles/render_plain_1080p_n1M.json"
 def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov):
     """Algorithmic DRAM bytes of one gs_bin_sort (the kernels' own minimal
     reads and writes, no cache effects):
-      pair count   per visible item: rectangle 8 (+ tight support 24) read,
-                   count 4 + row table 16 written
-      depth sort   per item slot: histogram read 4; 4 passes x (upsweep read
-                   4, downsweep read 4 key + 4 value, write 4 + 4), the first
-                   pass reading no values
-      offsets      per visible item: item 4 + count 4 read twice, offset 4
-                   written
-      emit         per visible item: item, offset, count, view 16 + rectangle
-                   8 + row table 16 read; per pair 8 written
-      pair sort    per pair and pass: upsweep 4, downsweep 8 read, 8 written
+      pair count   per item slot: depth key 4 read; per visible item:
+                   rectangle 8 (+ tight support 24) read, count 4 + emit
+                   record 16 (+ row table 16 with a filter) written
+      depth sort   pass 0 over every slot: count read 4 + key read 4, the
+                   visible items' key and value written 8 (invisible slots
+                   are dropped); passes 1-3 per visible item: count read 4,
+                   key + value read 8 and written 8
+      offsets      per visible item: item 4 read, emit record 32 gathered,
+                   count 4 + record 32 written in depth order; count 4 read,
+                   offset 4 written
+      emit         per visible item: item 4 + offset 4 + record 16 (+ 16 row
+                   table) read; per pair 8 written
+      pair sort    per pair and pass: count read 4, key + value read 8 and
+                   written 8
       ranges       per pair 4 read; per tile 8 written (+ 8 cleared)"""
-    count = m_visible * (8 + (24 if tight else 0) + 4 + 16)
-    depth = n_slots * (4 + 4 * (4 + 8 + 8) - 4)
-    offsets = m_visible * (8 + 8 + 4)
-    emit = m_visible * (16 + 8 + (16 if (tight or fov) else 0)) + 8 * k_pairs
+    table = 16 if (tight or fov) else 0
+    count = n_slots * 4 + m_visible * (8 + (24 if tight else 0) + 4 + 16 + table)
+    depth = n_slots * 8 + m_visible * 8 + 3 * m_visible * 20
+    offsets = m_visible * (4 + 32 + 4 + 32 + 4 + 4)
+    emit = m_visible * (4 + 4 + 16 + table) + 8 * k_pairs
     pair = pair_passes * 20 * k_pairs
     ranges = 4 * k_pairs + 16 * tiles
     return count + depth + offsets + emit + pair + ranges

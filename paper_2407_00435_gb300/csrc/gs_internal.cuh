@@ -48,9 +48,11 @@ enum Region : int {
   R_REC_M,       // u8 quality bound (foveated)
   R_REC_SUPP,    // float4 tight support (keyed u, v, covariance a, b) [tight]
   R_REC_SUPP2,   // float2 tight support (covariance c, tau) [tight]
-  R_REC_TABLE,   // uint4 row intervals of rectangles of <= 8 rows [tight or foveated]
+  R_REC_EMIT,    // 2 x uint4 emit record per item slot: (corner tile, width | rows << 16,
+                 //   tiles per row, count), row intervals of rectangles of <= 8 rows
   R_DKEY_A, R_DKEY_B, R_DVAL_A, R_DVAL_B,   // depth sort ping-pong (M)
   R_OFFSETS,     // u32 exclusive pair offsets in depth order (M)
+  R_SORTED_EMIT, // 2 x uint4 the visible items' emit records in depth order (M)
   R_PKEY_A, R_PKEY_B, R_PVAL_A, R_PVAL_B,   // pair sort ping-pong (K)
   R_BIGQ,        // u32 items with many tiles, expanded by a separate kernel (M)
   R_RANGES,      // uint2 per tile
@@ -87,7 +89,6 @@ struct Hdr {
   uint32_t pad1;
   unsigned long long aux_n;       // key count of a sort outside the frame (pruning)
   unsigned long long aux_out;     // result count of such a pass (compaction)
-  uint32_t coop_bar[2];           // grid barrier of the cooperative sort (count, generation)
 };
 
 // Per-view constants, computed on the device from the cameras.

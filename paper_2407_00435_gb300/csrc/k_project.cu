@@ -203,7 +203,7 @@ struct ProjArgs {
   // opacity-aware tight support (null records = 3-sigma rectangle only)
   float4 *rec_supp;             // (u, v, a, b)
   float2 *rec_supp2;            // (c, tau)
-  uint4 *rec_table;              // row intervals of small rectangles (tight or foveated)
+  uint4 *rec_emit;               // emit records, 2 per slot (see k_count_pairs)
   const uint32_t *level_rows;    // columns kept by the foveation filter, per row and level
   const float *opacity_lv;      // (L-1, N) level opacities the support must cover, or null
   int n_opacity_lv;
@@ -554,6 +554,11 @@ __device__ __forceinline__ void project_value(const ProjArgs &a, const ProjSmem<
 // search over the row prefix sums, its constants fetched by shuffles) and
 // the per-row results meet in shared memory.  With the tight support, items
 // with more rows are taken by the whole warp, one at a time, lanes over rows.
+// Besides the count, every visible item gets its emit record (32 bytes, one
+// sector, so the emit gathers one sector per item):
+//   [0] = (global tile id of the rectangle's corner, width | rows << 16,
+//          tiles per row of the item's view, count)
+//   [1] = the row table (only written, and only read, for items that have one)
 constexpr int kCountThreads = 256;
 
 __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
@@ -585,9 +590,10 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
     }
     // rows this lane's item contributes to the cooperative pass
     int rows = 0;
+    uint32_t my_count = 0;
     if (vis) {
       if (!tight && !fov) {
-        a.rec_count[j] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+        my_count = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
       } else if (!has_table(x0, x1, y0, y1)) {
         if (tight) {
           // many rows: counted by the whole warp below
@@ -602,7 +608,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
             const int xa = max(x0, la), xb = min(x1, lb);
             if (xa <= xb) pairs += (uint32_t)(xb - xa + 1);
           }
-          a.rec_count[j] = pairs;
+          my_count = pairs;
         }
       } else {
         rows = y1 - y0 + 1;
@@ -704,7 +710,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
         if (xa <= xb) bpairs += (uint32_t)(xb - xa + 1);
       }
       for (int o = 16; o > 0; o >>= 1) bpairs += __shfl_xor_sync(0xffffffffu, bpairs, o);
-      if (lane == 0) a.rec_count[jb] = bpairs;
+      if (lane == src) my_count = bpairs;
     }
     if (rows) {
       uint32_t tb[4] = {0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu};
@@ -719,8 +725,15 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
         else if (r < 6) tb[2] = (tb[2] & ~(0xffffu << sh)) | (e << sh);
         else tb[3] = (tb[3] & ~(0xffffu << sh)) | (e << sh);
       }
-      a.rec_count[j] = pairs;
-      a.rec_table[j] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
+      my_count = pairs;
+      a.rec_emit[2 * j + 1] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
+    }
+    if (vis) {
+      const ViewDev &vd = a.views[a.V == 1 ? 0 : (int)(j % a.V)];
+      const uint32_t corner = (uint32_t)(vd.tile_base + (long long)y0 * vd.tx + x0);
+      a.rec_count[j] = my_count;
+      a.rec_emit[2 * j] = make_uint4(corner, (uint32_t)(x1 - x0 + 1) | ((uint32_t)(y1 - y0 + 1) << 16),
+                                     (uint32_t)vd.tx, my_count);
     }
     __syncwarp();
   }
@@ -913,7 +926,7 @@ static ProjArgs make_proj_args(const gs_plan *p, void *ws) {
   const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
   a.rec_supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
   a.rec_supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
-  a.rec_table = (tight || p->has_fov) ? region<uint4>(p, ws, R_REC_TABLE) : nullptr;
+  a.rec_emit = region<uint4>(p, ws, R_REC_EMIT);
   a.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
   a.opacity_lv = p->has_fov ? p->fov.opacity_lv : nullptr;
   a.n_opacity_lv = a.opacity_lv ? p->fov.n_levels - 1 : 0;

@@ -49,6 +49,8 @@ struct SortArgs {
   int passes;
   int digit_bits;                    // bits per pass (<= 8)
   int no_skip;                       // run every pass (fixed buffer parity)
+  int drop_max;                      // cooperative sort: the first pass drops keys equal
+                                     //   to 0xffffffff (the result holds the others only)
   uint32_t *status;
   int sub;                           // upsweep sub-ranges per block, 1..kSortSub (0: kSortSub)
 };
@@ -326,12 +328,14 @@ struct DownBufs {
 
 // Walks partitions [p0, p1) of pass `pass` in order, sm.carry[d] holding
 // the output position of the next key of digit d.  `before` = executed
-// passes before this one (selects the buffers).  Returns false if a bounded
-// wait gave up (status set, copies in flight drained).
+// passes before this one (selects the buffers).  `drop`: keys equal to
+// 0xffffffff are left out (not ranked, staged or written; the bases count
+// only the others).  Returns false if a bounded wait gave up (status set,
+// copies in flight drained).
 template <int NT>
 __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int before,
                                                 DownSmemT<NT> &sm, DownBufs &db, long long p0,
-                                                long long p1, uint32_t n) {
+                                                long long p1, uint32_t n, bool drop = false) {
   constexpr int NW = NT / 32;
   constexpr int ITEMS = kSortPart / NT;
   const bool odd = (before & 1) != 0;   // (no dynamic indexing of the parameter arrays)
@@ -367,7 +371,9 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
     if (part + 1 < p1 && aligned && part + 1 < full) issue(part + 1, h ^ 1);
     for (int q = tid; q < NW * 256 / 2; q += NT)
       reinterpret_cast<uint32_t *>(&sm.wh[0][0])[q] = 0u;
-    const long long wbase = part * kSortPart + warp * (32 * ITEMS);
+    const long long pbase = part * kSortPart;
+    // keys of this partition: local indices [0, rem)
+    const int rem = (int)min((long long)kSortPart, (long long)n - pbase);
     const int lbase = warp * (32 * ITEMS);
     uint32_t key[ITEMS], rank[ITEMS];
     if (bulk) {
@@ -386,28 +392,27 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
     } else {
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
-        const long long idx = wbase + k * 32 + lane;
-        key[k] = idx < (long long)n ? __ldcg(&kin[idx]) : 0u;
+        const int li = lbase + k * 32 + lane;
+        key[k] = li < rem ? __ldcg(&kin[pbase + li]) : 0u;
       }
     }
     __syncthreads();
     // warp-level stable ranking (original order = (k, lane)); the lanes
-    // holding the same digit are found with one ballot per digit bit
+    // holding the same digit are found with one ballot per digit bit (bits
+    // above the digit width are zero in every lane: their ballots are 0 and
+    // leave the mask as it is)
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      long long idx = wbase + k * 32 + lane;
-      bool valid = idx < (long long)n;
-      uint32_t d = (key[k] >> shift) & dmask;
+      const bool valid = (lbase + k * 32 + lane < rem) && !(drop && key[k] == 0xffffffffu);
+      const uint32_t d = (key[k] >> shift) & dmask;
       uint32_t peers = __ballot_sync(0xffffffffu, valid);
-      if (!valid) peers = ~peers;
 #pragma unroll
       for (int bit = 0; bit < 8; ++bit) {
-        if (bit < a.digit_bits) {
-          const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-          peers &= ((d >> bit) & 1u) ? bb : ~bb;
-        }
+        const bool set = ((d >> bit) & 1u) != 0u;
+        const uint32_t bb = __ballot_sync(0xffffffffu, set);
+        peers &= set ? bb : ~bb;
       }
-      uint32_t before_w = valid ? (uint32_t)sm.wh[warp][d] : 0u;
+      const uint32_t before_w = valid ? (uint32_t)sm.wh[warp][d] : 0u;
       rank[k] = before_w + __popc(peers & ltmask);
       __syncwarp();
       if (valid && (__ffs(peers) - 1) == lane) sm.wh[warp][d] = (uint16_t)(before_w + __popc(peers));
@@ -442,22 +447,27 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
       for (int w = 0; w < 8; ++w) wofs += w < warp ? sm.wsum[w] : 0u;
       sm.dstart[tid] = wofs + incl - tot;
     }
+    // keys staged: every key of the partition, or the kept ones
+    uint32_t pcount = (uint32_t)rem;
+    if (drop) {
+      pcount = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) pcount += sm.wsum[w];
+    }
     __syncthreads();
     // stage the partition in digit order, then write runs of equal digits
     // to consecutive global addresses
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      const long long idx = wbase + k * 32 + lane;
-      if (idx < (long long)n) {
-        uint32_t d = (key[k] >> shift) & dmask;
-        uint32_t lp = sm.dstart[d] + (uint32_t)sm.wh[warp][d] + rank[k];
+      const int li = lbase + k * 32 + lane;
+      if (li < rem && !(drop && key[k] == 0xffffffffu)) {
+        const uint32_t d = (key[k] >> shift) & dmask;
+        const uint32_t lp = sm.dstart[d] + (uint32_t)sm.wh[warp][d] + rank[k];
         sm.key[lp] = key[k];
-        sm.val[lp] = iota ? (uint32_t)idx : (bulk ? sm.in_v[h][lbase + k * 32 + lane] : __ldcg(&vin[idx]));
+        sm.val[lp] = iota ? (uint32_t)(pbase + li) : (bulk ? sm.in_v[h][li] : __ldcg(&vin[pbase + li]));
       }
     }
     __syncthreads();
-    const long long pbase = part * kSortPart;
-    const uint32_t pcount = (uint32_t)min((long long)kSortPart, (long long)n - pbase);
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const uint32_t lp = (uint32_t)(k * NT + tid);
@@ -508,13 +518,36 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
 //            that every key shares skips the pass (all blocks agree)
 //   scatter  downsweep_range over the block's partitions
 //   barrier  the pass's output complete before the next pass reads it
-// The barriers count arrivals on a global word and wait (bounded) for a
-// generation word to move; they replace the 3 launches per pass (and the
-// fixed latency of each) of the multi-kernel sort.
+// The barriers count arrivals on one global word that only grows (zeroed
+// before the launch): the e-th barrier is passed once it reaches e G.  They
+// replace the 3 launches per pass (and the fixed latency of each) of the
+// multi-kernel sort.
+//
+// So that no block reads the whole table, the count also adds each block's
+// digit counts, by atomics, to the digit totals and to the sums of its group
+// of kCoopGroup blocks: a block's bases are then the totals, the group sums
+// of the groups before it and the rows of its own group before it (at most
+// 1 + G / kCoopGroup + kCoopGroup - 1 rows instead of G).
+//
+// Layout after the two G x 256 tables in a.bsum (uint32 words): the barrier
+// word (64 words reserved), then per pass parity kCoopSumRows rows of 256:
+// row 0 the totals, row 1 + g the sums of group g.  The barrier word and
+// parity 0 are zeroed before the launch; parity q ^ 1 is zeroed by block 0
+// during a pass of parity q (after its first barrier: every block has left
+// the previous pass, and the next pass adds only after this pass's second
+// barrier).
 struct CoopBar {
   unsigned int count;
-  unsigned int gen;
+  unsigned int spare;
 };
+constexpr int kCoopGroup = 16;                      // blocks per group of the bases
+constexpr int kCoopMaxGroups = 64;                  // grids of up to 1024 blocks
+constexpr int kCoopSumRows = 1 + kCoopMaxGroups;    // totals + group sums, per parity
+constexpr int kCoopExtraWords = 64 + 2 * kCoopSumRows * 256;
+// rows of 256 words a cooperative sort of G blocks needs in a.bsum
+__host__ __device__ constexpr long long coop_table_rows(int G) {
+  return 2LL * G + (kCoopExtraWords + 255) / 256;
+}
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
   unsigned int v;
@@ -523,21 +556,22 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
 }
 
 // Grid-wide barrier of a cooperative launch, bounded: false (status set)
-// if the other blocks did not all arrive within the limit.
-__device__ __forceinline__ bool grid_barrier(CoopBar *bar, uint32_t *status, int *s_ok) {
+// if the other blocks did not all arrive within the limit.  `epoch`: the
+// barriers this block passed (thread 0's copy).  One atomic per block and
+// no second word: the last block to arrive releases the others by its add.
+__device__ __forceinline__ bool grid_barrier(CoopBar *bar, unsigned int &epoch, uint32_t *status,
+                                             int *s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int g0 = ld_acquire_u32(&bar->gen);
+    ++epoch;
+    const unsigned int target = epoch * gridDim.x;
     __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
     bool ok = true;
-    if (arrived == gridDim.x - 1) {
-      bar->count = 0u;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
+    if ((int)(arrived - target) < 0) {
+      // (blocks already past this barrier may have added for the next one)
       int it = 0;
-      while (ld_acquire_u32(&bar->gen) == g0) {
+      while ((int)(ld_acquire_u32(&bar->count) - target) < 0) {
         if (++it > kSpinLimit) {
           ok = false;
           set_status(status, GS_ERR_TIMEOUT);
@@ -558,27 +592,28 @@ __device__ __forceinline__ bool grid_barrier(CoopBar *bar, uint32_t *status, int
 
 constexpr int kCountUnroll = 8;
 
-// NT threads per block: 1024 with one block per SM (the depth sort, leaving
-// room for the pair count beside it), 512 with two (the pair sort: a block's
+// NT threads per block: launched with one block per SM (the depth sort:
+// half of each SM stays free for the pair count, which runs beside it and
+// fills the sort's barrier waits) or two (the pair sort: a block's
 // partitions overlap the other block's).
 template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a, CoopBar *bar) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   DownSmemT<NT> &sm = *reinterpret_cast<DownSmemT<NT> *>(dyn_smem);
   constexpr int kCoopThreads = NT;
-  constexpr int NQ = kCoopThreads / 256;   // threads per digit in the bases phase
-  __shared__ uint32_t s_cnt[256], s_half[NQ][256], s_pre[NQ][256];
+  __shared__ uint32_t s_cnt[256];
   __shared__ uint32_t s_wsum[8];
   __shared__ int s_ok, s_skip;
-  const uint32_t n = sort_n(a);
+  // keys of the current pass (after a dropping first pass: the kept ones)
+  uint32_t n = sort_n(a);
   const int G = gridDim.x, b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
-  long long p0, p1;
-  block_parts(n, G, b, p0, p1);
-  const long long k0 = p0 * kSortPart;
-  const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
   const bool force_first = a.first_vals == nullptr;
+  uint32_t *extra = a.bsum + (size_t)2 * G * 256;
+  CoopBar *bar = reinterpret_cast<CoopBar *>(extra);
+  uint32_t *sums_base = extra + 64;
+  const int grp = b / kCoopGroup;
   if (tid == 0) {
     mbar_init(&sm.bar[0], 1);
     mbar_init(&sm.bar[1], 1);
@@ -586,11 +621,18 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a, CoopBar
   }
   DownBufs db = {0u, 0u, 0u, 0u};
   int executed = 0;
+  unsigned int epoch = 0;
   for (int pass = 0; pass < a.passes; ++pass) {
     const bool odd = (executed & 1) != 0;
     const uint32_t *kin = executed == 0 ? a.first_keys : (odd ? a.keys[1] : a.keys[0]);
     const int shift = a.digit_bits * pass;
+    const bool drop = a.drop_max != 0 && pass == 0;
+    long long p0, p1;
+    block_parts(n, G, b, p0, p1);
+    const long long k0 = p0 * kSortPart;
+    const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
     uint32_t *table = a.bsum + (size_t)(pass & 1) * (size_t)G * 256;
+    uint32_t *sums = sums_base + (size_t)(pass & 1) * kCoopSumRows * 256;
     // count
     if (tid < 256) s_cnt[tid] = 0u;
     __syncthreads();
@@ -605,36 +647,64 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a, CoopBar
       }
 #pragma unroll
       for (int u = 0; u < kCountUnroll; ++u)
-        warp_count(s_cnt, base + u * 32 + lane < k1, (key[u] >> shift) & dmask, lane);
+        warp_count(s_cnt, base + u * 32 + lane < k1 && !(drop && key[u] == 0xffffffffu),
+                   (key[u] >> shift) & dmask, lane);
     }
     __syncthreads();
-    if (tid < 256) table[(size_t)b * 256 + tid] = s_cnt[tid];
-    if (!grid_barrier(bar, a.status, &s_ok)) return;
-    // bases: digit d's total over all blocks and its count in blocks < b
+    if (tid < 256) {
+      const uint32_t c = s_cnt[tid];
+      table[(size_t)b * 256 + tid] = c;
+      if (c) {
+        atomicAdd(&sums[tid], c);
+        atomicAdd(&sums[(size_t)(1 + grp) * 256 + tid], c);
+      }
+    }
+    if (!grid_barrier(bar, epoch, a.status, &s_ok)) return;
+    if (b == 0) {
+      // the other parity's sums, for the next pass
+      uint32_t *nxt = sums_base + (size_t)((pass + 1) & 1) * kCoopSumRows * 256;
+      for (int q = tid; q < kCoopSumRows * 256 / 4; q += kCoopThreads)
+        reinterpret_cast<uint4 *>(nxt)[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // bases: digit d's total over all blocks (row 0 of the sums) and its
+    // count in blocks < b: the sums of groups < grp and the table rows of
+    // blocks grp * kCoopGroup .. b - 1.  Thread t adds 4 digits (16-byte
+    // loads) of rows t / 64, + NG, ... of that list; the NG row groups'
+    // partial sums meet in the staging buffers (free between the passes'
+    // scatters)
     {
-      const int d = tid & 255, hh = tid >> 8;
-      const int half = (G + NQ - 1) / NQ;
-      const int r0 = min(G, hh * half), r1 = min(G, r0 + half);
-      uint32_t tot = 0, pre = 0;
-      for (int r = r0; r < r1; r += 8) {
-        uint32_t v[8];
+      constexpr int NG = kCoopThreads / 64;
+      static_assert(NG * 256 <= kSortPart, "partials fit the staging buffer");
+      const int dg = tid & 63, rg = tid >> 6;
+      const uint4 *tab4 = reinterpret_cast<const uint4 *>(table);
+      const uint4 *sum4 = reinterpret_cast<const uint4 *>(sums);
+      const int b0 = grp * kCoopGroup;
+      const int nrows = grp + (b - b0);   // group sums, then own group's earlier rows
+      uint4 p4 = make_uint4(0u, 0u, 0u, 0u);
+      for (int r0 = rg; r0 < nrows; r0 += NG * 4) {
+        uint4 v[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = r + u < r1 ? __ldcg(&table[(size_t)(r + u) * 256 + d]) : 0u;
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + u * NG;
+          v[u] = r >= nrows ? make_uint4(0u, 0u, 0u, 0u)
+                            : (r < grp ? __ldcg(&sum4[(size_t)(1 + r) * 64 + dg])
+                                       : __ldcg(&tab4[(size_t)(b0 + r - grp) * 64 + dg]));
+        }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          tot += v[u];
-          pre += (r + u < b) ? v[u] : 0u;
+        for (int u = 0; u < 4; ++u) {
+          p4.x += v[u].x; p4.y += v[u].y; p4.z += v[u].z; p4.w += v[u].w;
         }
       }
-      s_half[hh][d] = tot;
-      s_pre[hh][d] = pre;
+      reinterpret_cast<uint4 *>(sm.val)[rg * 64 + dg] = p4;
+      if (rg == 0) reinterpret_cast<uint4 *>(sm.key)[dg] = __ldcg(&sum4[dg]);
     }
     if (tid == 0) s_skip = 0;
     __syncthreads();
-    uint32_t tot = 0, incl = 0;
+    uint32_t tot = 0, incl = 0, pre = 0;
     if (tid < 256) {
+      tot = sm.key[tid];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) tot += s_half[q][tid];
+      for (int q = 0; q < kCoopThreads / 64; ++q) pre += sm.val[q * 256 + tid];
       if (tot == n) s_skip = 1;   // one digit holds every key
       incl = tot;
 #pragma unroll
@@ -645,25 +715,35 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a, CoopBar
       if (lane == 31) s_wsum[tid >> 5] = incl;
     }
     __syncthreads();
-    const bool skip = (s_skip || n == 0) && !(force_first && executed == 0 && pass == a.passes - 1) &&
-                      !a.no_skip;
-    if (skip) continue;   // nothing written: no barrier needed before the next count
+    // a dropping pass always runs (it changes the key set); the keys it keeps
+    // are the table's total (the same in every block)
+    uint32_t n_out = n;
+    if (drop) {
+      n_out = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) n_out += s_wsum[w];
+    }
+    const bool skip = (s_skip || n == 0) && !drop &&
+                      !(force_first && executed == 0 && pass == a.passes - 1) && !a.no_skip;
+    if (skip) {
+      // nothing written; the barrier keeps the sums' zeroing ordered
+      if (!grid_barrier(bar, epoch, a.status, &s_ok)) return;
+      continue;
+    }
     if (tid < 256) {
       uint32_t wofs = 0;
 #pragma unroll
       for (int w = 0; w < 8; ++w) wofs += w < (tid >> 5) ? s_wsum[w] : 0u;
-      uint32_t pre = 0;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) pre += s_pre[q][tid];
       sm.carry[tid] = wofs + incl - tot + pre;
     }
     __syncthreads();
-    if (p0 < p1 && !downsweep_range<NT>(a, pass, executed, sm, db, p0, p1, n)) {
+    if (p0 < p1 && !downsweep_range<NT>(a, pass, executed, sm, db, p0, p1, n, drop)) {
       // leave the grid barrier to time out in the other blocks
       return;
     }
     ++executed;
-    if (!grid_barrier(bar, a.status, &s_ok)) return;
+    n = n_out;
+    if (!grid_barrier(bar, epoch, a.status, &s_ok)) return;
   }
   if (b == 0 && tid == 0) *a.sel = (uint32_t)(executed & 1);
 }
@@ -674,6 +754,7 @@ static std::mutex g_grid_mu;
 static bool g_smem_attr[64] = {};
 static int g_coop_grid[64] = {};  // SMs of the device if it can launch cooperative sorts, else 0
 static int g_coop_two[64] = {};   // two 512-thread blocks of the cooperative sort fit an SM
+static int g_coop_1k[64] = {};    // one 1024-thread block of the cooperative sort fits an SM
 
 static void init_grids() {
   std::lock_guard<std::mutex> lock(g_grid_mu);
@@ -686,19 +767,20 @@ static void init_grids() {
   if (dev >= 0 && dev < 64 && !g_smem_attr[dev]) {
     cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(DownSmem));
-    cudaFuncSetAttribute(k_sort_coop<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(DownSmemT<1024>));
     cudaFuncSetAttribute(k_sort_coop<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(DownSmemT<512>));
-    int coop = 0, pc = 0, pc2 = 0, nsm = 0;
+    cudaFuncSetAttribute(k_sort_coop<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmemT<1024>));
+    int coop = 0, pc = 0, pc1k = 0, nsm = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_sort_coop<1024>, 1024,
-                                                  sizeof(DownSmemT<1024>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc2, k_sort_coop<512>, 512,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_sort_coop<512>, 512,
                                                   sizeof(DownSmemT<512>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc1k, k_sort_coop<1024>, 1024,
+                                                  sizeof(DownSmemT<1024>));
     g_coop_grid[dev] = (coop && pc > 0 && nsm > 0) ? nsm : 0;
-    g_coop_two[dev] = pc2 >= 2 ? 1 : 0;
+    g_coop_two[dev] = pc >= 2 ? 1 : 0;
+    g_coop_1k[dev] = pc1k >= 1 ? 1 : 0;
     cudaGetLastError();
     g_smem_attr[dev] = true;
   }
@@ -728,19 +810,27 @@ static cudaError_t run_sort(const SortArgs &a0, cudaStream_t s, bool hist_done =
   return cudaGetLastError();
 }
 
-// Blocks of the cooperative sort on the current device (0: the multi-kernel
-// sort is used): one 1024-thread block per SM, or two 512-thread blocks.
-static int coop_grid(bool two = false) {
+// Shapes of the cooperative sort: one 512-thread block per SM (beside
+// another kernel), two (the sort alone), or one 1024-thread block.
+enum CoopShape { kCoop512x1 = 0, kCoop512x2 = 1, kCoop1024x1 = 2 };
+
+// Blocks of the cooperative sort of that shape on the current device (0:
+// the multi-kernel sort is used).
+static int coop_grid(int shape = kCoop512x1) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  return two && g_coop_two[dev] ? 2 * g_coop_grid[dev] : g_coop_grid[dev];
+  if (shape == kCoop512x2) return g_coop_two[dev] ? 2 * g_coop_grid[dev] : g_coop_grid[dev];
+  if (shape == kCoop1024x1 && !g_coop_1k[dev]) return 0;
+  return g_coop_grid[dev];
 }
 
 // The whole sort in one cooperative launch of G blocks of NT threads; the
 // digit tables (2 x G x 256) live in a.bsum.
 template <int NT>
-static cudaError_t run_sort_coop(const SortArgs &a, CoopBar *bar, int G, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(CoopBar), s);
+static cudaError_t run_sort_coop(const SortArgs &a, int G, cudaStream_t s) {
+  // the barrier word and parity 0 of the sums start at zero
+  cudaError_t e = cudaMemsetAsync(a.bsum + (size_t)2 * G * 256, 0,
+                                  (size_t)(64 + kCoopSumRows * 256) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
@@ -752,19 +842,24 @@ static cudaError_t run_sort_coop(const SortArgs &a, CoopBar *bar, int G, cudaStr
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_sort_coop<NT>, a, bar);
+  return cudaLaunchKernelEx(&cfg, k_sort_coop<NT>, a);
 }
 
 // One sort: cooperative when the device allows it and the table fits
 // (table_rows rows of 256 counts available in a.bsum), else multi-kernel
 // (hist_done: the global histograms are already in a.hist).  `two`: two
 // blocks per SM (nothing runs beside the sort).
-static cudaError_t sort_any(const SortArgs &a, CoopBar *bar, long long table_rows, cudaStream_t s,
-                            bool hist_done = false, bool two = false) {
-  const int G = coop_grid(two);
-  if (G > 0 && 2LL * G <= table_rows) {
-    if (G > coop_grid(false)) return run_sort_coop<512>(a, bar, G, s);
-    return run_sort_coop<1024>(a, bar, G, s);
+static bool coop_sort_ok(int shape, long long table_rows) {
+  const int G = coop_grid(shape);
+  return G > 0 && G <= kCoopGroup * kCoopMaxGroups && coop_table_rows(G) <= table_rows;
+}
+
+static cudaError_t sort_any(const SortArgs &a, long long table_rows, cudaStream_t s,
+                            bool hist_done = false, int shape = kCoop512x1) {
+  if (shape == kCoop1024x1 && !coop_sort_ok(shape, table_rows)) shape = kCoop512x1;
+  if (coop_sort_ok(shape, table_rows)) {
+    if (shape == kCoop1024x1) return run_sort_coop<1024>(a, coop_grid(shape), s);
+    return run_sort_coop<512>(a, coop_grid(shape), s);
   }
   return run_sort(a, s, hist_done);
 }
@@ -777,6 +872,8 @@ struct ScanArgs {
   const uint32_t *count;            // rec_count (by item)
   uint32_t *sorted_count[2];        // the counts in depth order: the depth sort's free key
                                     //   buffer (written by the upsweep, read by the rest)
+  const uint4 *erec;                // emit records of the pair count (2 per item slot)
+  uint4 *srec;                      // out: the same records in depth order
   const unsigned long long *n_items;
   long long capacity;
   uint32_t *offsets;
@@ -790,8 +887,15 @@ __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
   return (uint32_t)((long long)nn > a.capacity ? a.capacity : (long long)nn);
 }
 
-__global__ void __launch_bounds__(256) k_offsets_up(ScanArgs a) {
-  __shared__ unsigned long long s_w[8];
+// Per-block pair sums in depth order.  Each visible item's 32-byte emit
+// record (one sector, holding its count) is gathered once, by slot, and
+// written out in depth order with the count beside it, so the offset
+// downsweep and the emit read sequentially.  1024 threads per block: the
+// gathers are random once the records leave L2, so many must be in flight.
+constexpr int kOffUpThreads = 1024, kOffUpUnroll = 4;
+
+__global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
+  __shared__ unsigned long long s_w[kOffUpThreads / 32];
   const uint32_t n = scan_n(a);
   const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
   uint32_t *scount = *a.sel ? a.sorted_count[0] : a.sorted_count[1];
@@ -800,18 +904,32 @@ __global__ void __launch_bounds__(256) k_offsets_up(ScanArgs a) {
   const long long k0 = p0 * kSortPart;
   const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
   unsigned long long sum = 0;
-  for (long long base = k0; base < k1; base += 256 * 16) {
-    uint32_t c[16];
+  for (long long base = k0; base < k1; base += kOffUpThreads * kOffUpUnroll) {
+    uint32_t it[kOffUpUnroll];
+    uint4 e0[kOffUpUnroll], e1[kOffUpUnroll];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const long long idx = base + u * 256 + threadIdx.x;
-      c[u] = idx < k1 ? a.count[items[idx]] : 0u;
+    for (int u = 0; u < kOffUpUnroll; ++u) {
+      const long long idx = base + u * kOffUpThreads + threadIdx.x;
+      it[u] = idx < k1 ? items[idx] : 0xffffffffu;
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const long long idx = base + u * 256 + threadIdx.x;
-      if (idx < k1) scount[idx] = c[u];
-      sum += c[u];
+    for (int u = 0; u < kOffUpUnroll; ++u) {
+      e0[u] = make_uint4(0u, 0u, 0u, 0u);
+      e1[u] = e0[u];
+      if (it[u] != 0xffffffffu) {
+        e0[u] = a.erec[2 * (size_t)it[u]];
+        e1[u] = a.erec[2 * (size_t)it[u] + 1];   // (same sector; only read where written)
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kOffUpUnroll; ++u) {
+      const long long idx = base + u * kOffUpThreads + threadIdx.x;
+      if (idx < k1) {
+        scount[idx] = e0[u].w;
+        a.srec[2 * idx] = e0[u];
+        a.srec[2 * idx + 1] = e1[u];
+      }
+      sum += e0[u].w;
     }
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -819,7 +937,7 @@ __global__ void __launch_bounds__(256) k_offsets_up(ScanArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int w = 0; w < 8; ++w) t += s_w[w];
+    for (int w = 0; w < kOffUpThreads / 32; ++w) t += s_w[w];
     a.bsum[blockIdx.x] = t;
   }
 }
@@ -921,7 +1039,7 @@ struct EmitArgs {
   uint32_t *hist;                    // pair sort histograms [passes][256]
   const float4 *supp;                // tight support records, or null (whole rectangle)
   const float2 *supp2;
-  const uint4 *table;                // row intervals of small rectangles (tight or foveated)
+  const uint4 *srec;                 // emit records in depth order (k_offsets_up)
   const uint32_t *level_rows;        // columns kept by the foveation filter, per row and level
   int tile;
   int passes, digit_bits;
@@ -958,6 +1076,9 @@ __device__ __forceinline__ void hist_add_warp(uint32_t (*sh)[256], bool on, uint
 // g0 + l, g0 + l + 32, ... of the group, finds the owning item by binary
 // search over the group's offsets (warp shuffles) and maps its rank to a
 // tile.  Writes are coalesced; no lane loops over another lane's item.
+// Everything an item needs besides its slot and offset is its 32-byte emit
+// record, which k_offsets_up laid out in depth order: all reads are
+// sequential.
 // Items queued for k_emit_big (many tiles, or no row table) are skipped.
 template <bool TABLE>
 __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
@@ -974,43 +1095,36 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
     set_status(a.status, GS_ERR_CAPACITY);
   const long long warps = (long long)gridDim.x * (blockDim.x / 32);
   const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + wl;
-  const uint32_t *scount = *a.sel ? a.sorted_count[0] : a.sorted_count[1];
   // software pipeline over the warp's groups of 32 items: the next group's
-  // item, offset and count loads, and its rectangle and row-table gathers,
-  // are in flight while this group's pairs are written
-  auto load_item = [&](long long k, uint32_t &j, uint32_t &off, uint32_t &cnt) {
-    j = 0; off = 0xffffffffu; cnt = 0;
+  // slot, offset and record loads are in flight while this group's pairs
+  // are written
+  auto load_item = [&](long long k, uint32_t &j, uint32_t &off, uint4 &e, uint4 &t) {
+    j = 0; off = 0xffffffffu;
+    e = make_uint4(0u, 0u, 0u, 0u);
+    t = e;
     if (k < n) {
       j = items[k];
       off = a.offsets[k];
-      cnt = scount[k];
+      e = a.srec[2 * k];
+      if (TABLE) t = a.srec[2 * k + 1];
     }
   };
-  auto load_rec = [&](long long k, uint32_t j, uint32_t cnt, uint2 &r, uint4 &t) {
-    r = make_uint2(0u, 0u);
-    t = make_uint4(0u, 0u, 0u, 0u);
-    if (k < n && cnt > 0) {
-      r = a.rect[j];
-      if (TABLE && cnt <= kBigItem) t = a.table[j];
-    }
-  };
-  uint32_t nj, noff, ncnt;
-  uint2 nr;
-  uint4 nt;
-  load_item(wid * 32 + lane, nj, noff, ncnt);
-  load_rec(wid * 32 + lane, nj, ncnt, nr, nt);
+  uint32_t nj, noff;
+  uint4 ne, nt;
+  load_item(wid * 32 + lane, nj, noff, ne, nt);
   for (long long base = wid * 32; base < n; base += warps * 32) {
     const long long k = base + lane;
     const bool valid = k < n;
-    const uint32_t j = nj, off = noff, cnt = ncnt;
-    const uint2 r = nr;
+    const uint32_t j = nj, off = noff;
+    const uint4 e = ne;
     const uint4 tload = nt;
-    load_item(base + warps * 32 + lane, nj, noff, ncnt);
-    load_rec(base + warps * 32 + lane, nj, ncnt, nr, nt);
-    const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-    // slots with no pairs (invisible ones hold stale rectangles) are never
-    // queued for the large-item emit
-    const bool huge = valid && cnt > 0 && (cnt > kBigItem || (TABLE && !has_table(x0, x1, y0, y1)));
+    const uint32_t cnt = e.w;
+    load_item(base + warps * 32 + lane, nj, noff, ne, nt);
+    const uint32_t width = e.y & 0xffffu, rows = e.y >> 16;
+    // slots with no pairs (invisible ones) are never queued for the
+    // large-item emit; the table exists iff the rectangle is small
+    const bool small = rows <= (uint32_t)kTableRows && width <= (uint32_t)kTableCols;
+    const bool huge = valid && cnt > 0 && (cnt > kBigItem || (TABLE && !small));
     const uint32_t hb = __ballot_sync(0xffffffffu, huge);
     if (hb) {
       uint32_t qb = 0;
@@ -1044,20 +1158,24 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
       const uint32_t lstart = __shfl_sync(0xffffffffu, lexcl, L);
       const uint32_t ioff = __shfl_sync(0xffffffffu, off, L);
       const uint32_t ij = __shfl_sync(0xffffffffu, j, L);
-      const uint32_t rx = __shfl_sync(0xffffffffu, r.x, L);
-      const uint32_t ry = __shfl_sync(0xffffffffu, r.y, L);
-      uint4 it;
-      it.x = __shfl_sync(0xffffffffu, tbl.x, L);
-      it.y = __shfl_sync(0xffffffffu, tbl.y, L);
-      it.z = __shfl_sync(0xffffffffu, tbl.z, L);
-      it.w = __shfl_sync(0xffffffffu, tbl.w, L);
+      const uint32_t corner = __shfl_sync(0xffffffffu, e.x, L);
+      const uint32_t tx = __shfl_sync(0xffffffffu, e.z, L);
+      uint4 it = make_uint4(0u, 0u, 0u, 0u);
+      uint32_t iw = 1;
+      if (TABLE) {
+        it.x = __shfl_sync(0xffffffffu, tbl.x, L);
+        it.y = __shfl_sync(0xffffffffu, tbl.y, L);
+        it.z = __shfl_sync(0xffffffffu, tbl.z, L);
+        it.w = __shfl_sync(0xffffffffu, tbl.w, L);
+      } else {
+        iw = __shfl_sync(0xffffffffu, width, L);
+      }
       const uint32_t rank = lp - lstart;
       const uint32_t pos = ioff + rank;
       bool wr = lp < total && (long long)pos < a.pair_capacity;
       uint32_t t = 0;
       if (wr) {
-        const int ix0 = rx & 0xffff, ix1 = rx >> 16, iy0 = ry & 0xffff;
-        int row = 0, col = 0;
+        uint32_t row = 0, col = 0;
         if (TABLE) {
           // walk the row table
           uint32_t rem = rank;
@@ -1068,21 +1186,18 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
             table_row(it, q, first, lastc);
             const uint32_t len = lastc >= first ? (uint32_t)(lastc - first + 1) : 0u;
             if (!found && rem < len) {
-              row = q;
-              col = first + (int)rem;
+              row = (uint32_t)q;
+              col = (uint32_t)first + rem;
               found = true;
             }
             if (!found) rem -= len;
           }
           wr = found;
         } else {
-          const uint32_t w = (uint32_t)(ix1 - ix0 + 1);
-          row = (int)(rank / w);
-          col = (int)(rank - (uint32_t)row * w);
+          row = rank / iw;
+          col = rank - row * iw;
         }
-        const uint32_t view = a.view[ij];
-        const ViewDev &vd = a.views[view];
-        t = (uint32_t)(vd.tile_base + (long long)(iy0 + row) * vd.tx + (ix0 + col));
+        t = corner + row * tx + col;
         if (wr) {
           a.pkey[pos] = t;
           a.pval[pos] = ij;
@@ -1226,6 +1341,13 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *key_a, const uin
 // the pair offsets, the sort's by nothing the count does).  Fork and join
 // are events enqueued under one lock, so concurrent callers cannot
 // interleave them; both are capturable into a CUDA graph.
+// Item slots up to which the pair count runs beside the depth sort (one
+// 512-thread sort block per SM leaves room for it, and the count fills the
+// sort's barrier waits); above, the count runs first and the sort takes
+// 1024-thread blocks (both kernels are throughput bound there, and a count
+// that starts first would hold the SMs the sort's grid needs).
+constexpr long long kDepthOverlapMaxSlots = 1LL << 23;
+
 struct SideStream {
   cudaStream_t st = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -1274,6 +1396,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   d.vals[1] = region<uint32_t>(p, ws, R_DVAL_B);
   d.count = &hdr->n_items;          // every slot; invisible ones sort last
   d.capacity = p->max_visible;
+  d.drop_max = 1;                   // (cooperative sort: invisible slots are dropped by its
+                                    //  first pass; the others sort the same either way)
   d.sel = &hdr->sel_depth;
   d.hist = &hdr->hist[0][0][0];
   d.skip = &hdr->skip[0];
@@ -1302,10 +1426,12 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.offsets = region<uint32_t>(p, ws, R_OFFSETS);
   sa.sorted_count[0] = d.keys[0];    // the one of the two the depth sort did not end in
   sa.sorted_count[1] = d.keys[1];
+  sa.erec = region<uint4>(p, ws, R_REC_EMIT);
+  sa.srec = region<uint4>(p, ws, R_SORTED_EMIT);
   sa.bsum = reinterpret_cast<unsigned long long *>(bsum + (size_t)p->sort_blocks * kSortSub * 256);
   sa.blocks = G;
   sa.n_pairs = &hdr->n_pairs;
-  k_offsets_up<<<G, 256, 0, s>>>(sa);
+  k_offsets_up<<<G, kOffUpThreads, 0, s>>>(sa);
   k_offsets_scan<<<1, 1024, 0, s>>>(sa);
   k_offsets_down<<<G, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
@@ -1333,7 +1459,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
   ea.supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
   ea.supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
-  ea.table = (tight || p->has_fov) ? region<uint4>(p, ws, R_REC_TABLE) : nullptr;
+  ea.srec = sa.srec;
   ea.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
   ea.tile = p->tile;
   ea.n_pairs = &hdr->n_pairs;
@@ -1343,7 +1469,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.hist = &hdr->hist[1][0][0];
   // the cooperative pair sort counts its own digits: the emit's histograms
   // are only needed by the multi-kernel sort
-  const bool coop = coop_grid(true) > 0 && 2LL * coop_grid(true) <= (long long)p->sort_blocks * kSortSub;
+  const bool coop = coop_sort_ok(kCoop512x2, (long long)p->sort_blocks * kSortSub);
   ea.passes = coop ? 0 : pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
@@ -1383,8 +1509,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.passes = pair_passes;
   t.digit_bits = pair_bits;
   t.status = &hdr->status;
-  e = sort_any(t, reinterpret_cast<CoopBar *>(hdr->coop_bar), (long long)p->sort_blocks * kSortSub,
-               s, /*hist_done=*/!coop, /*two=*/true);
+  e = sort_any(t, (long long)p->sort_blocks * kSortSub,
+               s, /*hist_done=*/!coop, kCoop512x2);
   if (e != cudaSuccess) return e;
   // 5. ranges (the pointer pair lives in the header's spare words)
   uint2 *ranges = region<uint2>(p, ws, R_RANGES);
@@ -1397,6 +1523,13 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
 
 static cudaError_t depth_sort_and_count(const gs_plan *p, void *ws, const SortArgs &d,
                                         cudaStream_t s) {
+  const long long table_rows = (long long)p->sort_blocks * kSortSub;
+  if (p->n * p->V > kDepthOverlapMaxSlots) {
+    // large: the pair count, then the sort on the whole GPU
+    cudaError_t e = launch_count_pairs(p, ws, s);
+    if (e != cudaSuccess) return e;
+    return sort_any(d, table_rows, s, false, kCoop1024x1);
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -1407,10 +1540,7 @@ static cudaError_t depth_sort_and_count(const gs_plan *p, void *ws, const SortAr
   if ((e = cudaStreamWaitEvent(ss->st, ss->fork, 0)) != cudaSuccess) return e;
   if ((e = launch_count_pairs(p, ws, ss->st)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(ss->join, ss->st)) != cudaSuccess) return e;
-  Hdr *hdr = region<Hdr>(p, ws, R_HDR);
-  if ((e = sort_any(d, reinterpret_cast<CoopBar *>(hdr->coop_bar),
-                    (long long)p->sort_blocks * kSortSub, s)) != cudaSuccess)
-    return e;
+  if ((e = sort_any(d, table_rows, s, false, kCoop512x1)) != cudaSuccess) return e;
   return cudaStreamWaitEvent(s, ss->join, 0);
 }
 
@@ -1442,8 +1572,8 @@ cudaError_t launch_sort_indices(const gs_plan *p, void *ws, const uint32_t *keys
   d.digit_bits = 8;
   d.no_skip = 1;                          // four passes: the result ends in buffer 0
   d.status = &hdr->status;
-  return sort_any(d, reinterpret_cast<CoopBar *>(hdr->coop_bar), (long long)p->sort_blocks * kSortSub,
-                  s, false, /*two=*/true);
+  return sort_any(d, (long long)p->sort_blocks * kSortSub,
+                  s, false, kCoop512x2);
 }
 
 // --------------------------------------------------------------------------
@@ -1469,7 +1599,6 @@ struct StaticHdr {
   uint32_t skip[4];
   uint32_t sel;
   uint32_t status;
-  uint32_t coop_bar[2];
 };
 
 constexpr size_t kStaticHdrBytes = (sizeof(StaticHdr) + 255) & ~size_t(255);
@@ -1555,8 +1684,8 @@ extern "C" gs_status gs_sort_pairs_static(const uint32_t *keys_in, const uint32_
   a.blocks = g_sort_blocks < kStaticBlocks ? g_sort_blocks : kStaticBlocks;
   a.no_skip = 1;
   a.status = &h->status;
-  return sort_any(a, reinterpret_cast<CoopBar *>(h->coop_bar), (long long)kStaticBlocks * kSortSub,
-                  stream, false, /*two=*/true) == cudaSuccess
+  return sort_any(a, (long long)kStaticBlocks * kSortSub,
+                  stream, false, kCoop512x2) == cudaSuccess
              ? GS_OK
              : GS_ERR_CUDA;
 }
