@@ -480,6 +480,227 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd_plain(BwdArgs a) {
   }
 }
 
+// One blend of the back-to-front replay of accumulator S (alpha al, 1 / (1 -
+// al) = rom, colour c): adds dL/dc to v[6..8], updates S and returns dL/dalpha.
+__device__ __forceinline__ float bwd_blend(BAcc &S, float al, float rom, float4 c, float (&v)[9]) {
+  const float Tb = S.T * rom;
+  const float w = al * Tb;
+  v[6] += w * S.gr;
+  v[7] += w * S.gg;
+  v[8] += w * S.gb;
+  const float dal = S.gr * (Tb * c.x - S.Sr * rom) + S.gg * (Tb * c.y - S.Sg * rom) +
+                    S.gb * (Tb * c.z - S.Sb * rom);
+  S.Sr = fmaf(w, c.x, S.Sr);
+  S.Sg = fmaf(w, c.y, S.Sg);
+  S.Sb = fmaf(w, c.z, S.Sb);
+  S.T = Tb;
+  return dal;
+}
+
+// Foveated views without per-level parameters, in the plain kernel's layout
+// (two pixels per thread, per-warp ordered lists): each pixel replays its own
+// level's accumulator and, inside a blend band, the level below's (both in
+// registers).  A point enters a warp's list only if it can reach the warp's
+// pixels, lies at or before the last position they blended, and takes part
+// in a level one of them composites.
+template <int B>
+__global__ void __launch_bounds__(B * B / 2) k_render_bwd_fov(BwdArgs a) {
+  using Sm = BwdSmem<B>;
+  using G = WarpGeom<B, 2>;
+  constexpr int NT = Sm::NT, NB = Sm::NB, SPT = Sm::SPT, NWS = Sm::NWS, NW = Sm::NW;
+  __shared__ Sm sm;
+  __shared__ uint32_t s_wlv[NW];   // levels the warp's pixels composite (bit l)
+  __shared__ uint8_t s_m[NB];
+  const long long t = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t ltmask = (1u << lane) - 1u;
+  const ViewDev vd = a.views[find_view(a.views, a.V, t)];
+  const int local = (int)(t - vd.tile_base);
+  const int tx0 = (local % vd.tx) * B, ty0 = (local / vd.tx) * B;
+  const int lx = (warp % G::kWx) * 8 + (lane & 7);
+  const int ly0 = (warp / G::kWx) * G::kRows + (lane >> 3);
+  const float px = (float)lx + 0.5f;
+  const bool mmfr = a.mmfr != 0;
+  float py[2];
+  int lvl[2];
+  bool band[2];
+  BAcc A[2], Bq[2];
+  int mylast = -1;
+  uint32_t mylv = 0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int x = tx0 + lx, y = ty0 + ly0 + 4 * k;
+    py[k] = (float)(ly0 + 4 * k) + 0.5f;
+    A[k] = BAcc{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1};
+    Bq[k] = A[k];
+    lvl[k] = 1;
+    band[k] = false;
+    if (x < vd.W && y < vd.H) {
+      float wband = 1.0f;
+      pixel_level(vd, a.L, a.band, x, y, lvl[k], band[k], wband);
+      const long long pix = vd.pix_base + (long long)y * vd.W + x;
+      const float g0 = a.dL[3 * pix], g1 = a.dL[3 * pix + 1], g2 = a.dL[3 * pix + 2];
+      const float wa = band[k] ? wband : 1.0f;
+      A[k].T = a.T[2 * pix];
+      A[k].last = a.last[2 * pix];
+      A[k].gr = wa * g0; A[k].gg = wa * g1; A[k].gb = wa * g2;
+      A[k].Sr = A[k].T * a.bg0; A[k].Sg = A[k].T * a.bg1; A[k].Sb = A[k].T * a.bg2;
+      mylast = max(mylast, A[k].last);
+      mylv |= 1u << lvl[k];
+      if (band[k]) {
+        const float wb = 1.0f - wband;
+        Bq[k].T = a.T[2 * pix + 1];
+        Bq[k].last = a.last[2 * pix + 1];
+        Bq[k].gr = wb * g0; Bq[k].gg = wb * g1; Bq[k].gb = wb * g2;
+        Bq[k].Sr = Bq[k].T * a.bg0; Bq[k].Sg = Bq[k].T * a.bg1; Bq[k].Sb = Bq[k].T * a.bg2;
+        mylast = max(mylast, Bq[k].last);
+        mylv |= 1u << (lvl[k] - 1);
+      }
+    }
+  }
+  int wl = mylast;
+  uint32_t wlv = mylv;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+    wlv |= __shfl_xor_sync(0xffffffffu, wlv, o);
+  }
+  if (tid == 0) sm.maxlast = -1;
+  for (int k = tid; k < NB * 9; k += NT) (&sm.g[0][0])[k] = 0.0f;
+  __syncthreads();
+  if (lane == 0) {
+    sm.wlast[warp] = wl;
+    s_wlv[warp] = wlv;
+    atomicMax(&sm.maxlast, wl);
+  }
+  __syncthreads();
+  const int maxlast = sm.maxlast;
+  if (maxlast < 0) return;
+  const uint2 rg = a.ranges[t];
+  const uint32_t *vals = *a.sel ? a.pval_b : a.pval_a;
+  const uint32_t end = rg.x + (uint32_t)maxlast + 1;
+  const float inv = 1.0f / (kWhiten * kWhiten);
+
+  for (uint32_t hi = end; hi > rg.x;) {
+    const uint32_t lo = hi - rg.x > (uint32_t)NB ? hi - NB : rg.x;
+    const uint32_t cnt = hi - lo;
+    const int base = (int)(lo - rg.x);
+    uint32_t wm[SPT];
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int q = tid + u * NT;
+      wm[u] = 0u;
+      if ((uint32_t)q < cnt) {
+        const uint32_t j = vals[lo + q];
+        const float4 mean = a.rec_mean[j];
+        const float mx = (mean.x - (float)tx0) + mean.z, my = (mean.y - (float)ty0) + mean.w;
+        const float4 shp = a.rec_shape[j];
+        const float4 col = a.rec_color[j];
+        const int m = a.rec_m[j];
+        sm.mean[q] = make_float2(mx, my);
+        sm.shape[q] = shp;
+        sm.col[q] = col;
+        sm.j[q] = j;
+        s_m[q] = (uint8_t)m;
+        sm.op[q] = 1.0f / a.opac[a.rec_gid[j]];   // reciprocal opacity
+        // levels the point takes part in (bit l)
+        const uint32_t pm = mmfr ? (1u << m) : ((2u << m) - 2u);
+        uint32_t msk = warp_mask_exact<B, 2>(mx, my, shp, col.w);
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+          if (base + q > sm.wlast[w] || !(pm & s_wlv[w])) msk &= ~(1u << w);
+        float4 ea, eb;
+        make_eval(mx, my, shp, col.w, msk, ea, eb);
+        sm.ea[q] = ea;
+        sm.eb[q] = eb;
+        wm[u] = msk;
+      }
+    }
+    uint32_t pfx[SPT][NW];
+#pragma unroll
+    for (int u = 0; u < SPT; ++u)
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (wm[u] >> w) & 1u);
+        pfx[u][w] = __popc(bal & ltmask);
+        if (lane == 0) sm.wcnt[w][u * NWS + warp] = (uint16_t)__popc(bal);
+      }
+    __syncthreads();
+    if (tid < NW) {
+      uint32_t run = 0;
+      for (int e = 0; e < SPT * NWS; ++e) {
+        sm.woff[tid][e] = (uint16_t)run;
+        run += sm.wcnt[tid][e];
+      }
+      sm.woff[tid][SPT * NWS] = (uint16_t)run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SPT; ++u)
+#pragma unroll
+      for (int w = 0; w < NW; ++w)
+        if ((wm[u] >> w) & 1u)
+          sm.list[w][sm.woff[w][u * NWS + warp] + pfx[u][w]] = (uint16_t)(tid + u * NT);
+    __syncthreads();
+    const int nlist = sm.woff[warp][SPT * NWS];
+    for (int li = nlist - 1; li >= 0; --li) {
+      const int q = sm.list[warp][li];
+      const int pos = base + q;
+      const float4 ea = sm.ea[q], eb = sm.eb[q], c = sm.col[q], shp = sm.shape[q];
+      const float2 mu = sm.mean[q];
+      const float io = sm.op[q];
+      const int m = s_m[q];
+      float v[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[k] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const bool useA = pos <= A[k].last && takes_part(m, lvl[k], mmfr);
+        const bool useB = band[k] && pos <= Bq[k].last && takes_part(m, lvl[k] - 1, mmfr);
+        if (!useA && !useB) continue;
+        float t1, t2;
+        const float sq = eval_s(px, py[k], ea, eb, t1, t2);
+        if (!(sq <= eb.z)) continue;
+        const float al = alpha_of(__fsub_rn(c.w, sq));
+        const float rom = 1.0f / (1.0f - al);
+        float dal = 0.0f;
+        if (useA) dal += bwd_blend(A[k], al, rom, c, v);
+        if (useB) dal += bwd_blend(Bq[k], al, rom, c, v);
+        if (al < kAlphaMax) {
+          const float dpow = dal * al;
+          const float dx = px - mu.x, dy = py[k] - mu.y;
+          v[5] += dpow * io;
+          v[0] += dpow * (shp.x * t1 + shp.z * t2) * inv;
+          v[1] += dpow * (shp.y * t1 + shp.w * t2) * inv;
+          v[2] += -0.5f * dpow * dx * dx;
+          v[3] += -dpow * dx * dy;
+          v[4] += -0.5f * dpow * dy * dy;
+        }
+      }
+      bool nz = false;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) nz = nz || v[k] != 0.0f;
+      if (__any_sync(0xffffffffu, nz)) {
+        const float tot = warp_reduce_scatter9(v, lane);
+        const int idx = lane >> 1;
+        if ((lane & 1) == 0 && idx < 9 && tot != 0.0f) atomicAdd(&sm.g[q][idx], tot);
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < (int)cnt; q += NT) {
+      float *g = a.grad_item + (long long)sm.j[q] * kGradItem;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float v = sm.g[q][k];
+        if (v != 0.f) atomicAdd(&g[k], v);
+        sm.g[q][k] = 0.f;
+      }
+    }
+    __syncthreads();
+    hi = lo;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // pass 2: chain to 3D parameters
 // ---------------------------------------------------------------------------
@@ -757,7 +978,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(PBwdArgs a) {
 template <int B>
 static void launch_rb(const BwdArgs &a, bool fov, bool mv, long long tiles, cudaStream_t s) {
   if (!fov) k_render_bwd_plain<B><<<(unsigned)tiles, B * B / 2, 0, s>>>(a);
-  else if (!mv) k_render_bwd<B, true, false><<<(unsigned)tiles, B * B, 0, s>>>(a);
+  else if (!mv) k_render_bwd_fov<B><<<(unsigned)tiles, B * B / 2, 0, s>>>(a);
   else k_render_bwd<B, true, true><<<(unsigned)tiles, B * B, 0, s>>>(a);
 }
 
