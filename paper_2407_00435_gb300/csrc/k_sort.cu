@@ -51,6 +51,8 @@ struct SortArgs {
   int no_skip;                       // run every pass (fixed buffer parity)
   int drop_max;                      // cooperative sort: the first pass drops keys equal
                                      //   to 0xffffffff (the result holds the others only)
+  uint2 *ranges;                     // cooperative sort: [start, end) of each key value in
+  long long n_ranges;                //   the result (keys < n_ranges; zeroed by the caller)
   uint32_t *status;
   int sub;                           // upsweep sub-ranges per block, 1..kSortSub (0: kSortSub)
 };
@@ -746,6 +748,26 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
     if (!grid_barrier(bar, epoch, a.status, &s_ok)) return;
   }
   if (b == 0 && tid == 0) *a.sel = (uint32_t)(executed & 1);
+  if (a.ranges) {
+    // per key value (tile) its range in the sorted keys: block b marks the
+    // starts and ends that fall in its own partitions
+    const uint32_t *key = (executed & 1) ? a.keys[1] : a.keys[0];
+    long long p0, p1;
+    block_parts(n, G, b, p0, p1);
+    const long long k0 = p0 * kSortPart;
+    const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
+    for (long long q = k0 + tid; q < k1; q += kCoopThreads) {
+      const uint32_t k = __ldcg(&key[q]);
+      const uint32_t kp = q > 0 ? __ldcg(&key[q - 1]) : ~0u;
+      const uint32_t kn = q + 1 < (long long)n ? __ldcg(&key[q + 1]) : ~0u;
+      if ((long long)k >= a.n_ranges) {   // never written by a consistent emit
+        set_status(a.status, GS_ERR_CUDA);
+        continue;
+      }
+      if (q == 0 || kp != k) a.ranges[k].x = (uint32_t)q;
+      if (q == (long long)n - 1 || kn != k) a.ranges[k].y = (uint32_t)(q + 1);
+    }
+  }
 }
 
 static int g_sort_blocks = 0;
@@ -1509,15 +1531,21 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.passes = pair_passes;
   t.digit_bits = pair_bits;
   t.status = &hdr->status;
-  e = sort_any(t, (long long)p->sort_blocks * kSortSub,
-               s, /*hist_done=*/!coop, kCoop512x2);
-  if (e != cudaSuccess) return e;
-  // 5. ranges (the pointer pair lives in the header's spare words)
+  // 5. per-tile ranges: by the cooperative sort after its last pass, else
+  // by a kernel of their own
   uint2 *ranges = region<uint2>(p, ws, R_RANGES);
   e = cudaMemsetAsync(ranges, 0, p->bytes[R_RANGES], s);
   if (e != cudaSuccess) return e;
-  k_ranges<<<g_stream_blocks, 256, 0, s>>>(t.keys[0], t.keys[1], &hdr->sel_pair, &hdr->n_pairs,
-                                         p->max_pairs, p->tiles_total, ranges, &hdr->status);
+  if (coop) {
+    t.ranges = ranges;
+    t.n_ranges = p->tiles_total;
+  }
+  e = sort_any(t, (long long)p->sort_blocks * kSortSub,
+               s, /*hist_done=*/!coop, kCoop512x2);
+  if (e != cudaSuccess) return e;
+  if (!coop)
+    k_ranges<<<g_stream_blocks, 256, 0, s>>>(t.keys[0], t.keys[1], &hdr->sel_pair, &hdr->n_pairs,
+                                           p->max_pairs, p->tiles_total, ranges, &hdr->status);
   return cudaGetLastError();
 }
 
