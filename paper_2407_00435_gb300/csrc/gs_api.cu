@@ -110,7 +110,6 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   b[R_REC_EMIT] = 32 * (size_t)M;
   b[R_DKEY_A] = b[R_DKEY_B] = b[R_DVAL_A] = b[R_DVAL_B] = 4 * (size_t)M;
   b[R_OFFSETS] = 4 * (size_t)M;
-  b[R_SORTED_EMIT] = 32 * (size_t)M;
   b[R_PKEY_A] = b[R_PKEY_B] = b[R_PVAL_A] = b[R_PVAL_B] = 4 * (size_t)K;
   b[R_BIGQ] = 4 * (size_t)M;
   b[R_RANGES] = 8 * (size_t)T;

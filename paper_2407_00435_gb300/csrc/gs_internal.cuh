@@ -52,7 +52,6 @@ enum Region : int {
                  //   tiles per row, count), row intervals of rectangles of <= 8 rows
   R_DKEY_A, R_DKEY_B, R_DVAL_A, R_DVAL_B,   // depth sort ping-pong (M)
   R_OFFSETS,     // u32 exclusive pair offsets in depth order (M)
-  R_SORTED_EMIT, // 2 x uint4 the visible items' emit records in depth order (M)
   R_PKEY_A, R_PKEY_B, R_PVAL_A, R_PVAL_B,   // pair sort ping-pong (K)
   R_BIGQ,        // u32 items with many tiles, expanded by a separate kernel (M)
   R_RANGES,      // uint2 per tile

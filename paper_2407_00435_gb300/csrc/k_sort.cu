@@ -895,7 +895,6 @@ struct ScanArgs {
   uint32_t *sorted_count[2];        // the counts in depth order: the depth sort's free key
                                     //   buffer (written by the upsweep, read by the rest)
   const uint4 *erec;                // emit records of the pair count (2 per item slot)
-  uint4 *srec;                      // out: the same records in depth order
   const unsigned long long *n_items;
   long long capacity;
   uint32_t *offsets;
@@ -909,12 +908,14 @@ __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
   return (uint32_t)((long long)nn > a.capacity ? a.capacity : (long long)nn);
 }
 
-// Per-block pair sums in depth order.  Each visible item's 32-byte emit
-// record (one sector, holding its count) is gathered once, by slot, and
-// written out in depth order with the count beside it, so the offset
-// downsweep and the emit read sequentially.  1024 threads per block: the
-// gathers are random once the records leave L2, so many must be in flight.
-constexpr int kOffUpThreads = 1024, kOffUpUnroll = 4;
+// Per-block pair sums in depth order.  Each visible item's count is gathered
+// once, by slot, and written out in depth order, so the offset downsweep and
+// the emit read counts sequentially.  1024 threads per block: the gathers
+// are random once the counts leave L2, so many must be in flight.  (Laying
+// out the 32-byte emit records in depth order here as well, so that the
+// emit would read nothing by slot, was measured slower: 10 us more at
+// 1080p, the same on a 64-view batch.)
+constexpr int kOffUpThreads = 1024, kOffUpUnroll = 8;
 
 __global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
   __shared__ unsigned long long s_w[kOffUpThreads / 32];
@@ -927,31 +928,19 @@ __global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
   const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
   unsigned long long sum = 0;
   for (long long base = k0; base < k1; base += kOffUpThreads * kOffUpUnroll) {
-    uint32_t it[kOffUpUnroll];
-    uint4 e0[kOffUpUnroll], e1[kOffUpUnroll];
+    uint32_t it[kOffUpUnroll], c[kOffUpUnroll];
 #pragma unroll
     for (int u = 0; u < kOffUpUnroll; ++u) {
       const long long idx = base + u * kOffUpThreads + threadIdx.x;
       it[u] = idx < k1 ? items[idx] : 0xffffffffu;
     }
 #pragma unroll
-    for (int u = 0; u < kOffUpUnroll; ++u) {
-      e0[u] = make_uint4(0u, 0u, 0u, 0u);
-      e1[u] = e0[u];
-      if (it[u] != 0xffffffffu) {
-        e0[u] = a.erec[2 * (size_t)it[u]];
-        e1[u] = a.erec[2 * (size_t)it[u] + 1];   // (same sector; only read where written)
-      }
-    }
+    for (int u = 0; u < kOffUpUnroll; ++u) c[u] = it[u] != 0xffffffffu ? a.count[it[u]] : 0u;
 #pragma unroll
     for (int u = 0; u < kOffUpUnroll; ++u) {
       const long long idx = base + u * kOffUpThreads + threadIdx.x;
-      if (idx < k1) {
-        scount[idx] = e0[u].w;
-        a.srec[2 * idx] = e0[u];
-        a.srec[2 * idx + 1] = e1[u];
-      }
-      sum += e0[u].w;
+      if (idx < k1) scount[idx] = c[u];
+      sum += c[u];
     }
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -1061,7 +1050,7 @@ struct EmitArgs {
   uint32_t *hist;                    // pair sort histograms [passes][256]
   const float4 *supp;                // tight support records, or null (whole rectangle)
   const float2 *supp2;
-  const uint4 *srec;                 // emit records in depth order (k_offsets_up)
+  const uint4 *erec;                 // emit records of the pair count, 2 per item slot
   const uint32_t *level_rows;        // columns kept by the foveation filter, per row and level
   int tile;
   int passes, digit_bits;
@@ -1098,9 +1087,8 @@ __device__ __forceinline__ void hist_add_warp(uint32_t (*sh)[256], bool on, uint
 // g0 + l, g0 + l + 32, ... of the group, finds the owning item by binary
 // search over the group's offsets (warp shuffles) and maps its rank to a
 // tile.  Writes are coalesced; no lane loops over another lane's item.
-// Everything an item needs besides its slot and offset is its 32-byte emit
-// record, which k_offsets_up laid out in depth order: all reads are
-// sequential.
+// Everything an item needs besides its slot, offset and count (read in depth
+// order) is its 32-byte emit record: one sector gathered per item.
 // Items queued for k_emit_big (many tiles, or no row table) are skipped.
 template <bool TABLE>
 __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
@@ -1118,8 +1106,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
   const long long warps = (long long)gridDim.x * (blockDim.x / 32);
   const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + wl;
   // software pipeline over the warp's groups of 32 items: the next group's
-  // slot, offset and record loads are in flight while this group's pairs
-  // are written
+  // slot, offset and count loads and its record gather are in flight while
+  // this group's pairs are written
+  const uint32_t *scount = *a.sel ? a.sorted_count[0] : a.sorted_count[1];
   auto load_item = [&](long long k, uint32_t &j, uint32_t &off, uint4 &e, uint4 &t) {
     j = 0; off = 0xffffffffu;
     e = make_uint4(0u, 0u, 0u, 0u);
@@ -1127,8 +1116,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
     if (k < n) {
       j = items[k];
       off = a.offsets[k];
-      e = a.srec[2 * k];
-      if (TABLE) t = a.srec[2 * k + 1];
+      if (scount[k] > 0) {
+        e = a.erec[2 * (size_t)j];
+        if (TABLE) t = a.erec[2 * (size_t)j + 1];   // (same sector)
+      }
     }
   };
   uint32_t nj, noff;
@@ -1449,7 +1440,6 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.sorted_count[0] = d.keys[0];    // the one of the two the depth sort did not end in
   sa.sorted_count[1] = d.keys[1];
   sa.erec = region<uint4>(p, ws, R_REC_EMIT);
-  sa.srec = region<uint4>(p, ws, R_SORTED_EMIT);
   sa.bsum = reinterpret_cast<unsigned long long *>(bsum + (size_t)p->sort_blocks * kSortSub * 256);
   sa.blocks = G;
   sa.n_pairs = &hdr->n_pairs;
@@ -1481,7 +1471,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
   ea.supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
   ea.supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
-  ea.srec = sa.srec;
+  ea.erec = sa.erec;
   ea.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
   ea.tile = p->tile;
   ea.n_pairs = &hdr->n_pairs;
