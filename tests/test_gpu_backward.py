@@ -81,6 +81,22 @@ def test_backward_foveated_matches_oracle(gs, orc, mv):
         _compare("dc_lv", g["dc_lv"], ref.dc_lv, ref.mag["dc_lv"])
 
 
+def test_backward_foveated_mixed_views_matches_oracle(gs, orc):
+    # one foveated and one plain view in the same foveated call: the plain
+    # view's pixels all composite level 1 with no band
+    rng = np.random.default_rng(4005)
+    sc = synth.blob_scene(rng, 3000, n_blobs=6, degree=1, log_scale=(-3.0, 0.5))
+    cams = synth.orbit_cameras(rng, 2, 3.0, [(80, 96), (96, 72)])
+    m = synth.nested_levels(rng, sc.n, 4)
+    f = synth.Foveation(4, m, synth.ring_tangents([5, 10, 16]), 6.0, synth.random_gaze(rng, cams),
+                        np.array([1, 0], np.uint8))
+    wl = synth.Workload("bwd_fov_mixed", sc, cams, 16, f)
+    g, ref = _run(gs, orc, wl, fov=f)
+    for k, rk in (("means", ref.means), ("scales", ref.scales), ("quats", ref.quats),
+                  ("opac", ref.opac), ("sh", ref.sh)):
+        _compare(k, g[k], rk, ref.mag[k])
+
+
 def test_autograd_l1_loss(gs, orc):
     import torch
     from paper_2407_00435_gb300 import autograd as ga
