@@ -72,6 +72,7 @@ struct Hdr {
   uint32_t status;
   uint32_t pad0;
   unsigned long long n_visible;   // M: visible (view, point) items
+  uint32_t depth_max, depth_nmin;  // largest visible depth key, complement of the smallest
   unsigned long long n_items;     // item slots N * V (visible or not)
   unsigned long long n_pairs;     // K (raw)
   unsigned long long n_nonfinite;

@@ -762,10 +762,12 @@ __device__ __forceinline__ void write_rec(const ProjArgs &a, unsigned long long 
 template <int S>
 __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
   __shared__ ProjSmem<S> sm;
-  __shared__ uint32_t s_vis, s_nonfinite;
+  __shared__ uint32_t s_vis, s_nonfinite, s_dmax, s_dnmin;
   const int tid = threadIdx.x;
   if (tid == 0) {
     s_vis = 0;
+    s_dmax = 0;
+    s_dnmin = 0;
     s_nonfinite = 0;
   }
   __shared__ __align__(8) uint64_t s_bar;
@@ -853,7 +855,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
   __syncthreads();
   // items (point, view) of the block, consecutive threads on consecutive
   // slots j = i V + v (coalesced record writes; one view: one point each)
-  uint32_t nvis = 0;
+  uint32_t nvis = 0, dmax = 0, dnmin = 0;   // visible items; largest depth key and complement
   const int items = cnt_rows * a.V;
   for (int k = tid; k < items; k += kProjThreads) {
     const int pl = a.V == 1 ? k : k / a.V;
@@ -880,16 +882,26 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
         project_value<S>(a, sm, pl, i, mu, cam, vd, kk, r);
         write_rec(a, (unsigned long long)j, r, (uint32_t)i, (uint32_t)v);
         ++nvis;
+        dmax = max(dmax, r.depth);
+        dnmin = max(dnmin, ~r.depth);
       } else {
         a.rec_depth[j] = 0xffffffffu;
         a.rec_count[j] = 0u;
       }
     }
   }
-  if (nvis) atomicAdd(&s_vis, nvis);
+  if (nvis) {
+    atomicAdd(&s_vis, nvis);
+    atomicMax(&s_dmax, dmax);
+    atomicMax(&s_dnmin, dnmin);
+  }
   __syncthreads();
   if (tid == 0) {
-    if (s_vis) atomicAdd(&a.hdr->n_visible, (unsigned long long)s_vis);
+    if (s_vis) {
+      atomicAdd(&a.hdr->n_visible, (unsigned long long)s_vis);
+      atomicMax(&a.hdr->depth_max, s_dmax);
+      atomicMax(&a.hdr->depth_nmin, s_dnmin);
+    }
     if (s_nonfinite) atomicAdd(&a.hdr->n_nonfinite, (unsigned long long)s_nonfinite);
   }
 }

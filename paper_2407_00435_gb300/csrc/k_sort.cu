@@ -49,6 +49,8 @@ struct SortArgs {
   int passes;
   int digit_bits;                    // bits per pass (<= 8)
   int no_skip;                       // run every pass (fixed buffer parity)
+  const uint32_t *key_range;         // cooperative sort: (largest kept key, complement of the
+                                     //   smallest), or null (see k_sort_coop)
   int drop_max;                      // cooperative sort: the first pass drops keys equal
                                      //   to 0xffffffff (the result holds the others only)
   uint2 *ranges;                     // cooperative sort: [start, end) of each key value in
@@ -309,15 +311,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pa
 // issues them; an mbarrier per half counts the bytes in).  Partitions that
 // are not full, or inputs that are not 16-byte aligned, are read with plain
 // loads instead.
-template <int NT>
+template <int NT, int NBK = 256>     // NBK digit values: digits of up to log2(NBK) bits
 struct DownSmemT {
+  static_assert(NT >= NBK, "one thread per digit value");
   uint32_t in_k[2][kSortPart];
   uint32_t in_v[2][kSortPart];
   uint32_t key[kSortPart];            // staging in digit order
   uint32_t val[kSortPart];
-  uint16_t wh[NT / 32][256];          // per-warp digit counts, then offsets
-  uint32_t base[256], carry[256], dstart[256];
-  uint32_t wsum[8];                   // the 256 digit threads' warp sums
+  uint16_t wh[NT / 32][NBK];          // per-warp digit counts, then offsets
+  uint32_t base[NBK], carry[NBK], dstart[NBK];
+  uint32_t wsum[NBK / 32];            // the digit threads' warp sums
   uint64_t bar[2];
 };
 using DownSmem = DownSmemT<kDownThreads>;
@@ -332,22 +335,26 @@ struct DownBufs {
 // the output position of the next key of digit d.  `before` = executed
 // passes before this one (selects the buffers).  `drop`: keys equal to
 // 0xffffffff are left out (not ranked, staged or written; the bases count
-// only the others).  Returns false if a bounded wait gave up (status set,
-// copies in flight drained).
-template <int NT>
+// only the others).  `dbits`: digit width of the pass; `kmin`: subtracted
+// from every kept key as it is read (0: keys as they are).  Returns false if
+// a bounded wait gave up (status set, copies in flight drained).
+template <int NT, int NBK = 256>
 __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int before,
-                                                DownSmemT<NT> &sm, DownBufs &db, long long p0,
-                                                long long p1, uint32_t n, bool drop = false) {
+                                                DownSmemT<NT, NBK> &sm, DownBufs &db,
+                                                long long p0, long long p1, uint32_t n,
+                                                bool drop, int dbits, uint32_t kmin) {
   constexpr int NW = NT / 32;
   constexpr int ITEMS = kSortPart / NT;
+  constexpr int NBITS = NBK == 512 ? 9 : 8;
+  constexpr int NDW = NBK / 32;   // warps of the digit threads
   const bool odd = (before & 1) != 0;   // (no dynamic indexing of the parameter arrays)
   const uint32_t *kin = before == 0 ? a.first_keys : (odd ? a.keys[1] : a.keys[0]);
   const uint32_t *vin = before == 0 ? a.first_vals : (odd ? a.vals[1] : a.vals[0]);
   uint32_t *kout = odd ? a.keys[0] : a.keys[1];
   uint32_t *vout = odd ? a.vals[0] : a.vals[1];
   const bool iota = vin == nullptr;
-  const int shift = a.digit_bits * pass;
-  const uint32_t dmask = (1u << a.digit_bits) - 1u;
+  const int shift = dbits * pass;
+  const uint32_t dmask = (1u << dbits) - 1u;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ltmask = lanemask_lt();
   const bool aligned = ((uintptr_t)kin & 15u) == 0 && (iota || ((uintptr_t)vin & 15u) == 0);
@@ -371,7 +378,7 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
     // the other half was last read before the barrier ending the previous
     // partition: refill it with the next partition
     if (part + 1 < p1 && aligned && part + 1 < full) issue(part + 1, h ^ 1);
-    for (int q = tid; q < NW * 256 / 2; q += NT)
+    for (int q = tid; q < NW * NBK / 2; q += NT)
       reinterpret_cast<uint32_t *>(&sm.wh[0][0])[q] = 0u;
     const long long pbase = part * kSortPart;
     // keys of this partition: local indices [0, rem)
@@ -398,6 +405,10 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
         key[k] = li < rem ? __ldcg(&kin[pbase + li]) : 0u;
       }
     }
+    if (kmin) {
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) key[k] = key[k] == 0xffffffffu ? key[k] : key[k] - kmin;
+    }
     __syncthreads();
     // warp-level stable ranking (original order = (k, lane)); the lanes
     // holding the same digit are found with one ballot per digit bit (bits
@@ -409,7 +420,7 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
       const uint32_t d = (key[k] >> shift) & dmask;
       uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-      for (int bit = 0; bit < 8; ++bit) {
+      for (int bit = 0; bit < NBITS; ++bit) {
         const bool set = ((d >> bit) & 1u) != 0u;
         const uint32_t bb = __ballot_sync(0xffffffffu, set);
         peers &= set ? bb : ~bb;
@@ -424,7 +435,7 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
     // per digit (threads 0..255): warp offsets inside the partition, the
     // running base, and the digit's start inside the partition
     uint32_t tot = 0, incl = 0;
-    if (tid < 256) {
+    if (tid < NBK) {
       const int d = tid;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
@@ -443,10 +454,10 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
       if (lane == 31) sm.wsum[warp] = incl;
     }
     __syncthreads();
-    if (tid < 256) {
+    if (tid < NBK) {
       uint32_t wofs = 0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) wofs += w < warp ? sm.wsum[w] : 0u;
+      for (int w = 0; w < NDW; ++w) wofs += w < warp ? sm.wsum[w] : 0u;
       sm.dstart[tid] = wofs + incl - tot;
     }
     // keys staged: every key of the partition, or the kept ones
@@ -454,7 +465,7 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
     if (drop) {
       pcount = 0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) pcount += sm.wsum[w];
+      for (int w = 0; w < NDW; ++w) pcount += sm.wsum[w];
     }
     __syncthreads();
     // stage the partition in digit order, then write runs of equal digits
@@ -505,7 +516,8 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
   }
   __syncthreads();
   DownBufs db = {0u, 0u, 0u, 0u};
-  downsweep_range<kDownThreads>(a, pass, passes_before(a, pass), sm, db, p0, p1, n);
+  downsweep_range<kDownThreads>(a, pass, passes_before(a, pass), sm, db, p0, p1, n, false,
+                                a.digit_bits, 0u);
 }
 
 // ---- the whole sort in one cooperative launch -------------------------------
@@ -545,10 +557,10 @@ struct CoopBar {
 constexpr int kCoopGroup = 16;                      // blocks per group of the bases
 constexpr int kCoopMaxGroups = 64;                  // grids of up to 1024 blocks
 constexpr int kCoopSumRows = 1 + kCoopMaxGroups;    // totals + group sums, per parity
-constexpr int kCoopExtraWords = 64 + 2 * kCoopSumRows * 256;
-// rows of 256 words a cooperative sort of G blocks needs in a.bsum
-__host__ __device__ constexpr long long coop_table_rows(int G) {
-  return 2LL * G + (kCoopExtraWords + 255) / 256;
+// rows of 256 words a cooperative sort of G blocks and NBK digit values needs
+// in a.bsum: two G x NBK tables, the barrier word, two parities of sums
+__host__ __device__ constexpr long long coop_table_rows(int G, int NBK = 256) {
+  return (2LL * G * NBK + 64 + 2LL * kCoopSumRows * NBK + 255) / 256;
 }
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
@@ -598,21 +610,39 @@ constexpr int kCountUnroll = 8;
 // half of each SM stays free for the pair count, which runs beside it and
 // fills the sort's barrier waits) or two (the pair sort: a block's
 // partitions overlap the other block's).
-template <int NT>
+//
+// With a.key_range (NBK = 512), the keys are the visible depth keys: the
+// first pass subtracts the smallest kept key from every kept key, and the
+// digit width and pass count follow from the span of the kept keys (9-bit
+// digits: a span of 2^27 sorts in 3 passes instead of 4), the same in every
+// block.
+template <int NT, int NBK>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  DownSmemT<NT> &sm = *reinterpret_cast<DownSmemT<NT> *>(dyn_smem);
+  DownSmemT<NT, NBK> &sm = *reinterpret_cast<DownSmemT<NT, NBK> *>(dyn_smem);
   constexpr int kCoopThreads = NT;
-  __shared__ uint32_t s_cnt[256];
-  __shared__ uint32_t s_wsum[8];
+  constexpr int NDW = NBK / 32;   // warps of the digit threads
+  __shared__ uint32_t s_cnt[NBK];
+  __shared__ uint32_t s_wsum[NDW];
   __shared__ int s_ok, s_skip;
   // keys of the current pass (after a dropping first pass: the kept ones)
   uint32_t n = sort_n(a);
   const int G = gridDim.x, b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t dmask = (1u << a.digit_bits) - 1u;
+  int dbits = a.digit_bits, npasses = a.passes;
+  uint32_t kmin = 0;
+  if (NBK == 512 && a.key_range) {
+    // key_range = (largest kept key, complement of the smallest)
+    const uint32_t kmax = a.key_range[0], lo = ~a.key_range[1];
+    const uint32_t span = kmax >= lo ? kmax - lo : 0u;
+    const int bits = span ? 32 - __clz(span) : 1;
+    dbits = 9;
+    npasses = (bits + 8) / 9;
+    kmin = lo;
+  }
+  const uint32_t dmask = (1u << dbits) - 1u;
   const bool force_first = a.first_vals == nullptr;
-  uint32_t *extra = a.bsum + (size_t)2 * G * 256;
+  uint32_t *extra = a.bsum + (size_t)2 * G * NBK;
   CoopBar *bar = reinterpret_cast<CoopBar *>(extra);
   uint32_t *sums_base = extra + 64;
   const int grp = b / kCoopGroup;
@@ -624,19 +654,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
   DownBufs db = {0u, 0u, 0u, 0u};
   int executed = 0;
   unsigned int epoch = 0;
-  for (int pass = 0; pass < a.passes; ++pass) {
+  for (int pass = 0; pass < npasses; ++pass) {
     const bool odd = (executed & 1) != 0;
     const uint32_t *kin = executed == 0 ? a.first_keys : (odd ? a.keys[1] : a.keys[0]);
-    const int shift = a.digit_bits * pass;
+    const int shift = dbits * pass;
     const bool drop = a.drop_max != 0 && pass == 0;
+    const uint32_t ksub = pass == 0 ? kmin : 0u;   // keys are relative once written
     long long p0, p1;
     block_parts(n, G, b, p0, p1);
     const long long k0 = p0 * kSortPart;
     const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
-    uint32_t *table = a.bsum + (size_t)(pass & 1) * (size_t)G * 256;
-    uint32_t *sums = sums_base + (size_t)(pass & 1) * kCoopSumRows * 256;
+    uint32_t *table = a.bsum + (size_t)(pass & 1) * (size_t)G * NBK;
+    uint32_t *sums = sums_base + (size_t)(pass & 1) * kCoopSumRows * NBK;
     // count
-    if (tid < 256) s_cnt[tid] = 0u;
+    if (tid < NBK) s_cnt[tid] = 0u;
     __syncthreads();
     const int warp = tid >> 5;
     for (long long base = k0 + (long long)warp * 32 * kCountUnroll; base < k1;
@@ -650,34 +681,35 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
 #pragma unroll
       for (int u = 0; u < kCountUnroll; ++u)
         warp_count(s_cnt, base + u * 32 + lane < k1 && !(drop && key[u] == 0xffffffffu),
-                   (key[u] >> shift) & dmask, lane);
+                   ((key[u] - ksub) >> shift) & dmask, lane);
     }
     __syncthreads();
-    if (tid < 256) {
+    if (tid < NBK) {
       const uint32_t c = s_cnt[tid];
-      table[(size_t)b * 256 + tid] = c;
+      table[(size_t)b * NBK + tid] = c;
       if (c) {
         atomicAdd(&sums[tid], c);
-        atomicAdd(&sums[(size_t)(1 + grp) * 256 + tid], c);
+        atomicAdd(&sums[(size_t)(1 + grp) * NBK + tid], c);
       }
     }
     if (!grid_barrier(bar, epoch, a.status, &s_ok)) return;
     if (b == 0) {
       // the other parity's sums, for the next pass
-      uint32_t *nxt = sums_base + (size_t)((pass + 1) & 1) * kCoopSumRows * 256;
-      for (int q = tid; q < kCoopSumRows * 256 / 4; q += kCoopThreads)
+      uint32_t *nxt = sums_base + (size_t)((pass + 1) & 1) * kCoopSumRows * NBK;
+      for (int q = tid; q < kCoopSumRows * NBK / 4; q += kCoopThreads)
         reinterpret_cast<uint4 *>(nxt)[q] = make_uint4(0u, 0u, 0u, 0u);
     }
     // bases: digit d's total over all blocks (row 0 of the sums) and its
     // count in blocks < b: the sums of groups < grp and the table rows of
     // blocks grp * kCoopGroup .. b - 1.  Thread t adds 4 digits (16-byte
-    // loads) of rows t / 64, + NG, ... of that list; the NG row groups'
-    // partial sums meet in the staging buffers (free between the passes'
-    // scatters)
+    // loads) of rows t / (NBK / 4), + NG, ... of that list; the NG row
+    // groups' partial sums meet in the staging buffers (free between the
+    // passes' scatters)
     {
-      constexpr int NG = kCoopThreads / 64;
-      static_assert(NG * 256 <= kSortPart, "partials fit the staging buffer");
-      const int dg = tid & 63, rg = tid >> 6;
+      constexpr int NQ = NBK / 4;   // 16-byte words per row
+      constexpr int NG = kCoopThreads / NQ;
+      static_assert(NG * NBK <= kSortPart, "partials fit the staging buffer");
+      const int dg = tid & (NQ - 1), rg = tid / NQ;
       const uint4 *tab4 = reinterpret_cast<const uint4 *>(table);
       const uint4 *sum4 = reinterpret_cast<const uint4 *>(sums);
       const int b0 = grp * kCoopGroup;
@@ -689,24 +721,24 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
         for (int u = 0; u < 4; ++u) {
           const int r = r0 + u * NG;
           v[u] = r >= nrows ? make_uint4(0u, 0u, 0u, 0u)
-                            : (r < grp ? __ldcg(&sum4[(size_t)(1 + r) * 64 + dg])
-                                       : __ldcg(&tab4[(size_t)(b0 + r - grp) * 64 + dg]));
+                            : (r < grp ? __ldcg(&sum4[(size_t)(1 + r) * NQ + dg])
+                                       : __ldcg(&tab4[(size_t)(b0 + r - grp) * NQ + dg]));
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           p4.x += v[u].x; p4.y += v[u].y; p4.z += v[u].z; p4.w += v[u].w;
         }
       }
-      reinterpret_cast<uint4 *>(sm.val)[rg * 64 + dg] = p4;
+      reinterpret_cast<uint4 *>(sm.val)[rg * NQ + dg] = p4;
       if (rg == 0) reinterpret_cast<uint4 *>(sm.key)[dg] = __ldcg(&sum4[dg]);
     }
     if (tid == 0) s_skip = 0;
     __syncthreads();
     uint32_t tot = 0, incl = 0, pre = 0;
-    if (tid < 256) {
+    if (tid < NBK) {
       tot = sm.key[tid];
 #pragma unroll
-      for (int q = 0; q < kCoopThreads / 64; ++q) pre += sm.val[q * 256 + tid];
+      for (int q = 0; q < kCoopThreads / (NBK / 4); ++q) pre += sm.val[q * NBK + tid];
       if (tot == n) s_skip = 1;   // one digit holds every key
       incl = tot;
 #pragma unroll
@@ -723,23 +755,24 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
     if (drop) {
       n_out = 0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) n_out += s_wsum[w];
+      for (int w = 0; w < NDW; ++w) n_out += s_wsum[w];
     }
     const bool skip = (s_skip || n == 0) && !drop &&
-                      !(force_first && executed == 0 && pass == a.passes - 1) && !a.no_skip;
+                      !(force_first && executed == 0 && pass == npasses - 1) && !a.no_skip;
     if (skip) {
       // nothing written; the barrier keeps the sums' zeroing ordered
       if (!grid_barrier(bar, epoch, a.status, &s_ok)) return;
       continue;
     }
-    if (tid < 256) {
+    if (tid < NBK) {
       uint32_t wofs = 0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) wofs += w < (tid >> 5) ? s_wsum[w] : 0u;
+      for (int w = 0; w < NDW; ++w) wofs += w < (tid >> 5) ? s_wsum[w] : 0u;
       sm.carry[tid] = wofs + incl - tot + pre;
     }
     __syncthreads();
-    if (p0 < p1 && !downsweep_range<NT>(a, pass, executed, sm, db, p0, p1, n, drop)) {
+    if (p0 < p1 &&
+        !downsweep_range<NT, NBK>(a, pass, executed, sm, db, p0, p1, n, drop, dbits, ksub)) {
       // leave the grid barrier to time out in the other blocks
       return;
     }
@@ -789,18 +822,22 @@ static void init_grids() {
   if (dev >= 0 && dev < 64 && !g_smem_attr[dev]) {
     cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(DownSmem));
-    cudaFuncSetAttribute(k_sort_coop<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(DownSmemT<512>));
-    cudaFuncSetAttribute(k_sort_coop<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(DownSmemT<1024>));
-    int coop = 0, pc = 0, pc1k = 0, nsm = 0;
+    cudaFuncSetAttribute(k_sort_coop<512, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmemT<512, 256>));
+    cudaFuncSetAttribute(k_sort_coop<512, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmemT<512, 512>));
+    cudaFuncSetAttribute(k_sort_coop<1024, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmemT<1024, 512>));
+    int coop = 0, pc = 0, pc9 = 0, pc1k = 0, nsm = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_sort_coop<512>, 512,
-                                                  sizeof(DownSmemT<512>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc1k, k_sort_coop<1024>, 1024,
-                                                  sizeof(DownSmemT<1024>));
-    g_coop_grid[dev] = (coop && pc > 0 && nsm > 0) ? nsm : 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_sort_coop<512, 256>, 512,
+                                                  sizeof(DownSmemT<512, 256>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc9, k_sort_coop<512, 512>, 512,
+                                                  sizeof(DownSmemT<512, 512>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc1k, k_sort_coop<1024, 512>, 1024,
+                                                  sizeof(DownSmemT<1024, 512>));
+    g_coop_grid[dev] = (coop && pc > 0 && pc9 > 0 && nsm > 0) ? nsm : 0;
     g_coop_two[dev] = pc >= 2 ? 1 : 0;
     g_coop_1k[dev] = pc1k >= 1 ? 1 : 0;
     cudaGetLastError();
@@ -847,41 +884,47 @@ static int coop_grid(int shape = kCoop512x1) {
 }
 
 // The whole sort in one cooperative launch of G blocks of NT threads; the
-// digit tables (2 x G x 256) live in a.bsum.
-template <int NT>
+// digit tables (2 x G x NBK) live in a.bsum.
+template <int NT, int NBK>
 static cudaError_t run_sort_coop(const SortArgs &a, int G, cudaStream_t s) {
   // the barrier word and parity 0 of the sums start at zero
-  cudaError_t e = cudaMemsetAsync(a.bsum + (size_t)2 * G * 256, 0,
-                                  (size_t)(64 + kCoopSumRows * 256) * sizeof(uint32_t), s);
+  cudaError_t e = cudaMemsetAsync(a.bsum + (size_t)2 * G * NBK, 0,
+                                  (size_t)(64 + kCoopSumRows * NBK) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = sizeof(DownSmemT<NT>);
+  cfg.dynamicSmemBytes = sizeof(DownSmemT<NT, NBK>);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_sort_coop<NT>, a);
+  return cudaLaunchKernelEx(&cfg, k_sort_coop<NT, NBK>, a);
 }
 
 // One sort: cooperative when the device allows it and the table fits
 // (table_rows rows of 256 counts available in a.bsum), else multi-kernel
-// (hist_done: the global histograms are already in a.hist).  `two`: two
-// blocks per SM (nothing runs beside the sort).
-static bool coop_sort_ok(int shape, long long table_rows) {
+// (hist_done: the global histograms are already in a.hist).  `shape`: the
+// blocks per SM and their size; a sort with a.key_range (512 digit values)
+// runs one block per SM.
+static bool coop_sort_ok(int shape, long long table_rows, int nbk = 256) {
   const int G = coop_grid(shape);
-  return G > 0 && G <= kCoopGroup * kCoopMaxGroups && coop_table_rows(G) <= table_rows;
+  return G > 0 && G <= kCoopGroup * kCoopMaxGroups && coop_table_rows(G, nbk) <= table_rows;
 }
 
 static cudaError_t sort_any(const SortArgs &a, long long table_rows, cudaStream_t s,
                             bool hist_done = false, int shape = kCoop512x1) {
-  if (shape == kCoop1024x1 && !coop_sort_ok(shape, table_rows)) shape = kCoop512x1;
-  if (coop_sort_ok(shape, table_rows)) {
-    if (shape == kCoop1024x1) return run_sort_coop<1024>(a, coop_grid(shape), s);
-    return run_sort_coop<512>(a, coop_grid(shape), s);
+  const int nbk = a.key_range ? 512 : 256;
+  if (nbk == 512 && shape == kCoop512x2) shape = kCoop512x1;
+  if (shape == kCoop1024x1 && (nbk != 512 || !coop_sort_ok(shape, table_rows, nbk)))
+    shape = kCoop512x1;
+  if (coop_sort_ok(shape, table_rows, nbk)) {
+    const int G = coop_grid(shape);
+    if (shape == kCoop1024x1) return run_sort_coop<1024, 512>(a, G, s);
+    if (nbk == 512) return run_sort_coop<512, 512>(a, G, s);
+    return run_sort_coop<512, 256>(a, G, s);
   }
   return run_sort(a, s, hist_done);
 }
@@ -1411,6 +1454,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   d.capacity = p->max_visible;
   d.drop_max = 1;                   // (cooperative sort: invisible slots are dropped by its
                                     //  first pass; the others sort the same either way)
+  d.key_range = &hdr->depth_max;    // (cooperative sort: keys relative to the visible range)
   d.sel = &hdr->sel_depth;
   d.hist = &hdr->hist[0][0][0];
   d.skip = &hdr->skip[0];
