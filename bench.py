@@ -143,7 +143,22 @@ RENDER_SOURCES = ("paper_2407_00435_gb300/csrc/k_render.cu", "paper_2407_00435_g
 RENDER_TRAFFIC = "profiles/render_plain_1080p_n1M.json"
 
 
-def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov):
+def depth_passes(r, gs):
+    """Depth-sort passes of the plan's last frame: with the cooperative sort,
+    9-bit digits over the span of the visible depth keys; else four."""
+    if not gs._lib.gs_sort_is_cooperative():
+        return 4
+    import torch
+    d = r.region(gs.GS_REGION_ITEM_DEPTH, torch.int32, r.n * r.V)
+    d = d.to(torch.int64) & 0xffffffff
+    vis = d[d != 0xffffffff]
+    if vis.numel() == 0:
+        return 1
+    span = int(vis.max() - vis.min())
+    return max(1, (max(span, 1).bit_length() + 8) // 9)
+
+
+def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov, depth_passes=4):
     """Algorithmic DRAM bytes of one gs_bin_sort (the kernels' own minimal
     reads and writes, no cache effects):
       pair count   per item slot: depth key 4 read; per visible item:
@@ -151,8 +166,8 @@ def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov):
                    record 16 (+ row table 16 with a filter) written
       depth sort   pass 0 over every slot: count read 4 + key read 4, the
                    visible items' key and value written 8 (invisible slots
-                   are dropped); passes 1-3 per visible item: count read 4,
-                   key + value read 8 and written 8
+                   are dropped); each later pass per visible item: count
+                   read 4, key + value read 8 and written 8
       offsets      per visible item: item 4 read, count 4 gathered, count 4
                    written in depth order; count 4 read, offset 4 written
       emit         per visible item: item 4 + offset 4 + count 4 read, emit
@@ -162,7 +177,7 @@ def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov):
       ranges       per pair 4 read; per tile 8 written (+ 8 cleared)"""
     table = 16 if (tight or fov) else 0
     count = n_slots * 4 + m_visible * (8 + (24 if tight else 0) + 4 + 16 + table)
-    depth = n_slots * 8 + m_visible * 8 + 3 * m_visible * 20
+    depth = n_slots * 8 + m_visible * 8 + (depth_passes - 1) * m_visible * 20
     offsets = m_visible * (4 + 4 + 4 + 4 + 4)
     emit = m_visible * (4 + 4 + 4 + 16 + table) + 8 * k_pairs
     pair = pair_passes * 20 * k_pairs
@@ -378,7 +393,7 @@ def gpu_arm(args):
     # the binning and sorting stage (pair count, depth sort, offsets, emit,
     # pair sort, ranges): HBM bound by design, algorithmic bytes / stage time
     bs_bytes = bin_sort_bytes(r.n * r.V, int(c["n_visible"]), int(c["n_pairs"]), r.T_tiles,
-                              pair_passes(r.T_tiles), True, False)
+                              pair_passes(r.T_tiles), True, False, depth_passes(r, gs))
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bs_gbs = bs_bytes / (stages["bin_sort"] * 1e-3) / 1e9
     roofline_bin_sort = {"bound": "hbm", "stage": "gs_bin_sort", "achieved": round(bs_gbs, 1),
@@ -903,7 +918,8 @@ def extra_batched(torch, gs, synth, flush, steps, views=None, points=None, separ
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bs_bytes = bin_sort_bytes(r.n * r.V, int(c["n_visible"]), int(c["n_pairs"]), r.T_tiles,
-                              pair_passes(r.T_tiles, opt["radix_bits"]), True, True)
+                              pair_passes(r.T_tiles, opt["radix_bits"]), True, True,
+                              depth_passes(r, gs))
     bs_gbs = bs_bytes / (stages["bin_sort"] * 1e-3) / 1e9
     res = {"workload": wl.name, "views": len(wl.cams), "pixels": r.P,
            "ms_per_batch": round(ms, 3), "views_per_s": round(len(wl.cams) * 1000 / ms, 2),
