@@ -118,7 +118,8 @@ typedef struct gs_config {
                             tiles (default).  See gs_render. */
   int32_t flags;         /* GS_FLAG_* */
   int32_t max_levels;    /* largest foveation L the plan must hold; 0 = 4 */
-  int32_t radix_bits;    /* digit width of the pair sort's passes, 4..8; 0 = balanced <= 8 */
+  int32_t radix_bits;    /* digit width of the pair sort's passes, 4..10 (9 and 10 need the
+                            cooperative sort, else 8 is used); 0 = balanced <= 8 */
   int32_t chunk_slots;   /* chunk slots the workspace holds for the chunked render;
                             0 = enough for any split (capped at max(tiles + 64, 65536)).
                             Tiles that do not fit are rendered whole. */

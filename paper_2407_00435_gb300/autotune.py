@@ -60,7 +60,7 @@ def _time_frames(r: Renderer, sc, fov, frames, warmup):
 
 # The search space of the coordinate search: each option's values, the
 # first one the starting point.
-SEARCH_SPACE = {"tile": [16, 8], "radix_bits": [0, 5, 6, 7, 8], "chunk": [0, 512, 1024, 2048, 4096]}
+SEARCH_SPACE = {"tile": [16, 8], "radix_bits": [0, 5, 6, 7, 8, 9, 10], "chunk": [0, 512, 1024, 2048, 4096]}
 
 
 def autotune(sc: dict, n: int, sh_degree: int, cams, fov: dict | None = None,

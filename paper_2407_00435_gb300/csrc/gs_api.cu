@@ -49,7 +49,7 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   p->tile = c.tile;
   if (c.chunk > 0 && (c.chunk < 64 || c.chunk > (1 << 24))) return GS_ERR_INVALID_ARG;
   p->chunk = c.chunk > 0 ? c.chunk : 0;
-  if (c.radix_bits != 0 && (c.radix_bits < 4 || c.radix_bits > 8)) return GS_ERR_INVALID_ARG;
+  if (c.radix_bits != 0 && (c.radix_bits < 4 || c.radix_bits > 10)) return GS_ERR_INVALID_ARG;
   p->radix_bits = c.radix_bits;
   if (((uint32_t)c.flags & GS_FLAG_MULTI_MODEL) && !((uint32_t)c.flags & GS_FLAG_FOVEATED))
     return GS_ERR_INVALID_ARG;

@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a, int pa
 // issues them; an mbarrier per half counts the bytes in).  Partitions that
 // are not full, or inputs that are not 16-byte aligned, are read with plain
 // loads instead.
-template <int NT, int NBK = 256>     // NBK digit values: digits of up to log2(NBK) bits
+template <int NT, int NBK = 256>     // NBK digit values (256, 512 or 1024): digits of up to
+                                     //   log2(NBK) bits
 struct DownSmemT {
   static_assert(NT >= NBK, "one thread per digit value");
   uint32_t in_k[2][kSortPart];
@@ -345,7 +346,7 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
                                                 bool drop, int dbits, uint32_t kmin) {
   constexpr int NW = NT / 32;
   constexpr int ITEMS = kSortPart / NT;
-  constexpr int NBITS = NBK == 512 ? 9 : 8;
+  constexpr int NBITS = NBK == 1024 ? 10 : (NBK == 512 ? 9 : 8);
   constexpr int NDW = NBK / 32;   // warps of the digit threads
   const bool odd = (before & 1) != 0;   // (no dynamic indexing of the parameter arrays)
   const uint32_t *kin = before == 0 ? a.first_keys : (odd ? a.keys[1] : a.keys[0]);
@@ -810,6 +811,7 @@ static bool g_smem_attr[64] = {};
 static int g_coop_grid[64] = {};  // SMs of the device if it can launch cooperative sorts, else 0
 static int g_coop_two[64] = {};   // two 512-thread blocks of the cooperative sort fit an SM
 static int g_coop_1k[64] = {};    // one 1024-thread block of the cooperative sort fits an SM
+static int g_coop_1k10[64] = {};  // ... with 1024 digit values
 
 static void init_grids() {
   std::lock_guard<std::mutex> lock(g_grid_mu);
@@ -828,6 +830,8 @@ static void init_grids() {
                          (int)sizeof(DownSmemT<512, 512>));
     cudaFuncSetAttribute(k_sort_coop<1024, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(DownSmemT<1024, 512>));
+    cudaFuncSetAttribute(k_sort_coop<1024, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmemT<1024, 1024>));
     int coop = 0, pc = 0, pc9 = 0, pc1k = 0, nsm = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -837,6 +841,10 @@ static void init_grids() {
                                                   sizeof(DownSmemT<512, 512>));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc1k, k_sort_coop<1024, 512>, 1024,
                                                   sizeof(DownSmemT<1024, 512>));
+    int pc1k10 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc1k10, k_sort_coop<1024, 1024>, 1024,
+                                                  sizeof(DownSmemT<1024, 1024>));
+    g_coop_1k10[dev] = pc1k10 >= 1 ? 1 : 0;
     g_coop_grid[dev] = (coop && pc > 0 && pc9 > 0 && nsm > 0) ? nsm : 0;
     g_coop_two[dev] = pc >= 2 ? 1 : 0;
     g_coop_1k[dev] = pc1k >= 1 ? 1 : 0;
@@ -870,8 +878,9 @@ static cudaError_t run_sort(const SortArgs &a0, cudaStream_t s, bool hist_done =
 }
 
 // Shapes of the cooperative sort: one 512-thread block per SM (beside
-// another kernel), two (the sort alone), or one 1024-thread block.
-enum CoopShape { kCoop512x1 = 0, kCoop512x2 = 1, kCoop1024x1 = 2 };
+// another kernel), two (the sort alone), one 1024-thread block, or one with
+// 1024 digit values.
+enum CoopShape { kCoop512x1 = 0, kCoop512x2 = 1, kCoop1024x1 = 2, kCoop1024x1d10 = 3 };
 
 // Blocks of the cooperative sort of that shape on the current device (0:
 // the multi-kernel sort is used).
@@ -880,6 +889,7 @@ static int coop_grid(int shape = kCoop512x1) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (shape == kCoop512x2) return g_coop_two[dev] ? 2 * g_coop_grid[dev] : g_coop_grid[dev];
   if (shape == kCoop1024x1 && !g_coop_1k[dev]) return 0;
+  if (shape == kCoop1024x1d10 && !g_coop_1k10[dev]) return 0;
   return g_coop_grid[dev];
 }
 
@@ -907,25 +917,40 @@ static cudaError_t run_sort_coop(const SortArgs &a, int G, cudaStream_t s) {
 // One sort: cooperative when the device allows it and the table fits
 // (table_rows rows of 256 counts available in a.bsum), else multi-kernel
 // (hist_done: the global histograms are already in a.hist).  `shape`: the
-// blocks per SM and their size; a sort with a.key_range (512 digit values)
-// runs one block per SM.
+// blocks per SM and their size.  Digit values: 512 with a.key_range, else
+// 2^digit_bits rounded up to 256, 512 or 1024; 512 values run one 512- or
+// 1024-thread block per SM, 1024 values one 1024-thread block, and digits of
+// more than 8 bits need the cooperative sort (the multi-kernel sort's
+// histograms hold 256 values).
+static int sort_nbk(const SortArgs &a) {
+  return a.key_range ? 512 : (a.digit_bits <= 8 ? 256 : (a.digit_bits == 9 ? 512 : 1024));
+}
+
+static int coop_shape_for(int nbk, int shape) {
+  if (nbk == 1024) return kCoop1024x1d10;
+  if (nbk == 512) return shape == kCoop1024x1 ? kCoop1024x1 : kCoop512x1;
+  return shape == kCoop1024x1 ? kCoop512x1 : shape;
+}
+
 static bool coop_sort_ok(int shape, long long table_rows, int nbk = 256) {
+  shape = coop_shape_for(nbk, shape);
   const int G = coop_grid(shape);
   return G > 0 && G <= kCoopGroup * kCoopMaxGroups && coop_table_rows(G, nbk) <= table_rows;
 }
 
 static cudaError_t sort_any(const SortArgs &a, long long table_rows, cudaStream_t s,
                             bool hist_done = false, int shape = kCoop512x1) {
-  const int nbk = a.key_range ? 512 : 256;
-  if (nbk == 512 && shape == kCoop512x2) shape = kCoop512x1;
-  if (shape == kCoop1024x1 && (nbk != 512 || !coop_sort_ok(shape, table_rows, nbk)))
-    shape = kCoop512x1;
+  const int nbk = sort_nbk(a);
+  if (shape == kCoop1024x1 && !coop_sort_ok(shape, table_rows, nbk)) shape = kCoop512x1;
+  shape = coop_shape_for(nbk, shape);
   if (coop_sort_ok(shape, table_rows, nbk)) {
     const int G = coop_grid(shape);
+    if (nbk == 1024) return run_sort_coop<1024, 1024>(a, G, s);
     if (shape == kCoop1024x1) return run_sort_coop<1024, 512>(a, G, s);
     if (nbk == 512) return run_sort_coop<512, 512>(a, G, s);
     return run_sort_coop<512, 256>(a, G, s);
   }
+  if (a.digit_bits > 8) return cudaErrorInvalidValue;   // (callers fall back to 8-bit digits)
   return run_sort(a, s, hist_done);
 }
 
@@ -1492,8 +1517,11 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   k_offsets_down<<<G, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
   // digit width: the requested one, else the balanced width of the fewest
-  // passes of at most 8 bits
-  const int want = p->radix_bits > 0 ? p->radix_bits : 8;
+  // passes of at most 8 bits; widths of 9 or 10 bits only with the
+  // cooperative sort (else 8)
+  const long long table_rows = (long long)p->sort_blocks * kSortSub;
+  int want = p->radix_bits > 0 ? p->radix_bits : 8;
+  if (want > 8 && !coop_sort_ok(kCoop512x2, table_rows, want == 9 ? 512 : 1024)) want = 8;
   int pair_passes = (p->tile_bits + want - 1) / want;
   if (pair_passes > 4) pair_passes = 4;   // histogram storage holds four passes
   const int pair_bits = (p->tile_bits + pair_passes - 1) / pair_passes;
@@ -1525,7 +1553,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.hist = &hdr->hist[1][0][0];
   // the cooperative pair sort counts its own digits: the emit's histograms
   // are only needed by the multi-kernel sort
-  const bool coop = coop_sort_ok(kCoop512x2, (long long)p->sort_blocks * kSortSub);
+  const bool coop = coop_sort_ok(kCoop512x2, table_rows, pair_bits <= 8 ? 256 : (pair_bits == 9 ? 512 : 1024));
   ea.passes = coop ? 0 : pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;

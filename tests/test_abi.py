@@ -38,7 +38,7 @@ def test_plan_init_validates_on_host(lib):
     bad = gs.gs_config(12, 0, 0, 0, 0, 0)
     assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(bad)) == gs.GS_ERR_INVALID_ARG
     for cfg in (gs.gs_config(16, 0, 0, 0, 3, 0, 0),      # digit width below 4
-                gs.gs_config(16, 0, 0, 0, 9, 0, 0),      # digit width above 8
+                gs.gs_config(16, 0, 0, 0, 11, 0, 0),     # digit width above 10
                 gs.gs_config(16, 32, 0, 0, 0, 0, 0),     # chunk below 64 points
                 gs.gs_config(16, 256, 0, 0, 0, -1, 0)):  # negative chunk slots
         assert lib.gs_plan_init(plan, 100, 0, cams, 1, C.byref(cfg)) == gs.GS_ERR_INVALID_ARG
