@@ -332,6 +332,34 @@ struct DownBufs {
   uint32_t issued0, issued1, used0, used1;
 };
 
+// Ranks the ITEMS keys of each lane of the warp (item k of lane l is key
+// k * 32 + l of the warp's slice): rank[k] = the key's position among the
+// warp's keys of the same digit so far; sm.wh[warp][d] counts them.  RB
+// ballots (the digit width rounded up); ALLV: every key is kept.
+template <int RB, bool ALLV, int NT, int NBK, int ITEMS>
+__device__ __forceinline__ void rank_items(const uint32_t (&key)[ITEMS], uint32_t (&rank)[ITEMS],
+                                           DownSmemT<NT, NBK> &sm, int warp, int lane,
+                                           uint32_t ltmask, int shift, uint32_t dmask, int lbase,
+                                           int rem, bool drop) {
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const bool valid = ALLV || ((lbase + k * 32 + lane < rem) && !(drop && key[k] == 0xffffffffu));
+    const uint32_t d = (key[k] >> shift) & dmask;
+    uint32_t peers = ALLV ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int bit = 0; bit < RB; ++bit) {
+      const bool set = ((d >> bit) & 1u) != 0u;
+      const uint32_t bb = __ballot_sync(0xffffffffu, set);
+      peers &= set ? bb : ~bb;
+    }
+    const uint32_t before_w = valid ? (uint32_t)sm.wh[warp][d] : 0u;
+    rank[k] = before_w + __popc(peers & ltmask);
+    __syncwarp();
+    if (valid && (__ffs(peers) - 1) == lane) sm.wh[warp][d] = (uint16_t)(before_w + __popc(peers));
+    __syncwarp();
+  }
+}
+
 // Walks partitions [p0, p1) of pass `pass` in order, sm.carry[d] holding
 // the output position of the next key of digit d.  `before` = executed
 // passes before this one (selects the buffers).  `drop`: keys equal to
@@ -414,23 +442,15 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
     // warp-level stable ranking (original order = (k, lane)); the lanes
     // holding the same digit are found with one ballot per digit bit (bits
     // above the digit width are zero in every lane: their ballots are 0 and
-    // leave the mask as it is)
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const bool valid = (lbase + k * 32 + lane < rem) && !(drop && key[k] == 0xffffffffu);
-      const uint32_t d = (key[k] >> shift) & dmask;
-      uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-      for (int bit = 0; bit < NBITS; ++bit) {
-        const bool set = ((d >> bit) & 1u) != 0u;
-        const uint32_t bb = __ballot_sync(0xffffffffu, set);
-        peers &= set ? bb : ~bb;
-      }
-      const uint32_t before_w = valid ? (uint32_t)sm.wh[warp][d] : 0u;
-      rank[k] = before_w + __popc(peers & ltmask);
-      __syncwarp();
-      if (valid && (__ffs(peers) - 1) == lane) sm.wh[warp][d] = (uint16_t)(before_w + __popc(peers));
-      __syncwarp();
+    // leave the mask as it is).  Specialised for digits of at most 7 bits
+    // (one ballot less) and for partitions whose keys are all kept.
+    const bool all_valid = rem == kSortPart && !drop;
+    if (NBK == 256 && dbits <= 7) {
+      if (all_valid) rank_items<7, true, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
+      else rank_items<7, false, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
+    } else {
+      if (all_valid) rank_items<NBITS, true, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
+      else rank_items<NBITS, false, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
     }
     __syncthreads();
     // per digit (threads 0..255): warp offsets inside the partition, the
