@@ -48,6 +48,8 @@ struct SortArgs {
   int blocks;                        // G, the grid of upsweep and downsweep
   int passes;
   int digit_bits;                    // bits per pass (<= 8)
+  int key_bits;                      // significant bits of the keys (0: passes x digit_bits);
+                                     //   the last pass ranks only the bits left
   int no_skip;                       // run every pass (fixed buffer parity)
   const uint32_t *key_range;         // cooperative sort: (largest kept key, complement of the
                                      //   smallest), or null (see k_sort_coop)
@@ -365,13 +367,15 @@ __device__ __forceinline__ void rank_items(const uint32_t (&key)[ITEMS], uint32_
 // passes before this one (selects the buffers).  `drop`: keys equal to
 // 0xffffffff are left out (not ranked, staged or written; the bases count
 // only the others).  `dbits`: digit width of the pass; `kmin`: subtracted
-// from every kept key as it is read (0: keys as they are).  Returns false if
+// from every kept key as it is read (0: keys as they are); `rbits`: the
+// digit's significant bits in this pass (fewer in a last pass), the ballots
+// the ranking takes.  Returns false if
 // a bounded wait gave up (status set, copies in flight drained).
 template <int NT, int NBK = 256>
 __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int before,
                                                 DownSmemT<NT, NBK> &sm, DownBufs &db,
                                                 long long p0, long long p1, uint32_t n,
-                                                bool drop, int dbits, uint32_t kmin) {
+                                                bool drop, int dbits, uint32_t kmin, int rbits) {
   constexpr int NW = NT / 32;
   constexpr int ITEMS = kSortPart / NT;
   constexpr int NBITS = NBK == 1024 ? 10 : (NBK == 512 ? 9 : 8);
@@ -383,7 +387,7 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
   uint32_t *vout = odd ? a.vals[0] : a.vals[1];
   const bool iota = vin == nullptr;
   const int shift = dbits * pass;
-  const uint32_t dmask = (1u << dbits) - 1u;
+  const uint32_t dmask = (1u << rbits) - 1u;   // (keys have no bits above: nothing is lost)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ltmask = lanemask_lt();
   const bool aligned = ((uintptr_t)kin & 15u) == 0 && (iota || ((uintptr_t)vin & 15u) == 0);
@@ -444,14 +448,26 @@ __device__ __forceinline__ bool downsweep_range(const SortArgs &a, int pass, int
     // above the digit width are zero in every lane: their ballots are 0 and
     // leave the mask as it is).  Specialised for digits of at most 7 bits
     // (one ballot less) and for partitions whose keys are all kept.
-    const bool all_valid = rem == kSortPart && !drop;
-    if (NBK == 256 && dbits <= 7) {
-      if (all_valid) rank_items<7, true, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
-      else rank_items<7, false, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
+    const bool allv = rem == kSortPart && !drop;
+#define GS_RANK(R)                                                                              \
+  do {                                                                                          \
+    if (allv) rank_items<R, true, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask,     \
+                                           lbase, rem, drop);                                   \
+    else rank_items<R, false, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase,  \
+                                       rem, drop);                                              \
+  } while (0)
+    if (NBK == 256) {
+      if (rbits <= 6) GS_RANK(6);
+      else if (rbits == 7) GS_RANK(7);
+      else GS_RANK(8);
+    } else if (NBK == 512) {
+      if (rbits <= 8) GS_RANK(8);
+      else GS_RANK(9);
     } else {
-      if (all_valid) rank_items<NBITS, true, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
-      else rank_items<NBITS, false, NT, NBK>(key, rank, sm, warp, lane, ltmask, shift, dmask, lbase, rem, drop);
+      if (rbits <= 9) GS_RANK(9);
+      else GS_RANK(10);
     }
+#undef GS_RANK
     __syncthreads();
     // per digit (threads 0..255): warp offsets inside the partition, the
     // running base, and the digit's start inside the partition
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(kDownThreads, 2) k_downsweep(SortArgs a, int p
   __syncthreads();
   DownBufs db = {0u, 0u, 0u, 0u};
   downsweep_range<kDownThreads>(a, pass, passes_before(a, pass), sm, db, p0, p1, n, false,
-                                a.digit_bits, 0u);
+                                a.digit_bits, 0u, a.digit_bits);
 }
 
 // ---- the whole sort in one cooperative launch -------------------------------
@@ -651,6 +667,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
   const int G = gridDim.x, b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
   int dbits = a.digit_bits, npasses = a.passes;
+  int kbits = a.key_bits > 0 ? a.key_bits : a.digit_bits * a.passes;
   uint32_t kmin = 0;
   if (NBK == 512 && a.key_range) {
     // key_range = (largest kept key, complement of the smallest)
@@ -660,8 +677,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
     dbits = 9;
     npasses = (bits + 8) / 9;
     kmin = lo;
+    kbits = bits;
   }
-  const uint32_t dmask = (1u << dbits) - 1u;
   const bool force_first = a.first_vals == nullptr;
   uint32_t *extra = a.bsum + (size_t)2 * G * NBK;
   CoopBar *bar = reinterpret_cast<CoopBar *>(extra);
@@ -681,6 +698,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
     const int shift = dbits * pass;
     const bool drop = a.drop_max != 0 && pass == 0;
     const uint32_t ksub = pass == 0 ? kmin : 0u;   // keys are relative once written
+    // this pass's significant digit bits (the last pass may have fewer)
+    const int rbits = min(dbits, max(1, kbits - shift));
+    const uint32_t pmask = (1u << rbits) - 1u;
     long long p0, p1;
     block_parts(n, G, b, p0, p1);
     const long long k0 = p0 * kSortPart;
@@ -702,7 +722,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
 #pragma unroll
       for (int u = 0; u < kCountUnroll; ++u)
         warp_count(s_cnt, base + u * 32 + lane < k1 && !(drop && key[u] == 0xffffffffu),
-                   ((key[u] - ksub) >> shift) & dmask, lane);
+                   ((key[u] - ksub) >> shift) & pmask, lane);
     }
     __syncthreads();
     if (tid < NBK) {
@@ -792,8 +812,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sort_coop(SortArgs a) {
       sm.carry[tid] = wofs + incl - tot + pre;
     }
     __syncthreads();
-    if (p0 < p1 &&
-        !downsweep_range<NT, NBK>(a, pass, executed, sm, db, p0, p1, n, drop, dbits, ksub)) {
+    if (p0 < p1 && !downsweep_range<NT, NBK>(a, pass, executed, sm, db, p0, p1, n, drop, dbits,
+                                             ksub, rbits)) {
       // leave the grid barrier to time out in the other blocks
       return;
     }
@@ -1612,6 +1632,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.blocks = G;
   t.passes = pair_passes;
   t.digit_bits = pair_bits;
+  t.key_bits = p->tile_bits;
   t.status = &hdr->status;
   // 5. per-tile ranges: by the cooperative sort after its last pass, else
   // by a kernel of their own
