@@ -535,9 +535,38 @@ def extra_foveated(torch, gs, synth, flush, steps, points=None):
     ms_f = _ms(torch, fov_step, steps, 2, flush)
     ms_p = _ms(torch, plain_step, steps, 2, flush)
     px = rf.P
+    # the foveated frame's stages, timed apart, and the foveated render's
+    # roofline (the plain render's op count per walked position and blend)
+    st = {"project": [], "bin_sort": [], "render": []}
+    for _ in range(max(3, steps // 2)):
+        flush()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        rf.project(sc, f)
+        ev[1].record()
+        rf.bin_sort()
+        ev[2].record()
+        rf.render(of, fov=True)
+        ev[3].record()
+        torch.cuda.synchronize()
+        for q, nm in enumerate(("project", "bin_sort", "render")):
+            st[nm].append(ev[q].elapsed_time(ev[q + 1]))
+    stages = {k: round(sorted(v)[len(v) // 2], 4) for k, v in st.items()}
+    peaks, _ = _peaks()
+    n_sm = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    peak_tops = n_sm * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ach = (OPS_PER_EVAL * int(cntf["n_evals"]) + OPS_PER_BLEND * int(cntf["n_blends"])) / \
+        (stages["render"] * 1e-3) / 1e12
     del rf, rp, sc
     torch.cuda.empty_cache()
     return {"workload": wl.name, "fps_foveated": round(1000 / ms_f, 2),
+            "stages_ms_foveated": stages,
+            "roofline_render_foveated": {"bound": "alu", "achieved": round(ach, 3),
+                                         "peak": round(peak_tops, 3),
+                                         "unit": "TFLOP/s (FP32 lane-ops)",
+                                         "frac": round(ach / peak_tops, 4),
+                                         "note": "both eyes' render, ops as the plain render's "
+                                                 "roofline; of measured"},
             "fps_plain": round(1000 / ms_p, 2), "speedup": round(ms_p / ms_f, 3),
             "gpix_per_s_foveated": round(px / ms_f / 1e6, 3),
             "pairs_foveated": int(cf["n_pairs"]), "pairs_plain": int(cp["n_pairs"]),
