@@ -161,7 +161,6 @@ __device__ __forceinline__ void composite_plain(const uint16_t *list, int nlist,
     const int q = list[li];
     const float4 sa = ra[q], sb = rb[q], c = rc[q];
     const int pos = base + q;
-    bool live = false;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
       float t1, t2;
@@ -181,9 +180,14 @@ __device__ __forceinline__ void composite_plain(const uint16_t *list, int nlist,
         A[k].done = true;
         walk_end[k] = pos + 1;
       }
-      live = live || !A[k].done;
     }
-    if ((li & 3) == 3 && !__any_sync(0xffffffffu, live)) break;
+    if ((li & 3) == 3) {
+      // leave once no pixel of the warp is still compositing
+      bool live = false;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) live = live || !A[k].done;
+      if (!__any_sync(0xffffffffu, live)) break;
+    }
   }
 }
 
@@ -210,7 +214,6 @@ __device__ __forceinline__ void composite_fov_a(const uint16_t *list, int nlist,
     const float4 sa = ra[q], sb = rb[q], c = rc[q];
     const uint32_t pm = (uint32_t)rm[q];
     const int pos = base + q;
-    bool live = false;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
       float t1, t2;
@@ -230,9 +233,14 @@ __device__ __forceinline__ void composite_fov_a(const uint16_t *list, int nlist,
         A[k].done = true;
         walk_end[k] = pos + 1;
       }
-      live = live || !A[k].done;
     }
-    if ((li & 3) == 3 && !__any_sync(0xffffffffu, live)) break;
+    if ((li & 3) == 3) {
+      // leave once no pixel of the warp is still compositing
+      bool live = false;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) live = live || !A[k].done;
+      if (!__any_sync(0xffffffffu, live)) break;
+    }
   }
 }
 
@@ -262,7 +270,6 @@ __device__ __forceinline__ void composite_fov_ab(const uint16_t *list, int nlist
     const float4 sa = ra[q], sb = rb[q], c = rc[q];
     const uint32_t pm = (uint32_t)rm[q];
     const int pos = base + q;
-    bool live = false;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
       float t1, t2;
@@ -298,9 +305,13 @@ __device__ __forceinline__ void composite_fov_ab(const uint16_t *list, int nlist
         }
         if (hit && Tn < kTMin) Bq[k].done = true;
       }
-      live = live || !A[k].done || !Bq[k].done;
     }
-    if ((li & 3) == 3 && !__any_sync(0xffffffffu, live)) break;
+    if ((li & 3) == 3) {
+      bool live = false;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) live = live || !A[k].done || !Bq[k].done;
+      if (!__any_sync(0xffffffffu, live)) break;
+    }
   }
 }
 
@@ -820,8 +831,11 @@ __device__ __forceinline__ void render_item(const RenderArgs &a,
 // Whole tiles (CHUNK = false): one block per tile.  Chunked (CHUNK = true):
 // persistent blocks take work items from a queue -- first the chunks of the
 // heavy tiles, then the remaining tiles in order.
+// Blocks per SM: foveated two-pixel blocks get 6 (room for both
+// accumulators' registers without spills), the others fill 1024 threads.
 template <int B, bool FOV, bool MV, bool STATS, int PX, bool CHUNK>
-__global__ void __launch_bounds__(B * B / PX, (CHUNK ? 768 : 1024) / (B * B / PX))
+__global__ void __launch_bounds__(B * B / PX, (FOV && PX == 2 && !CHUNK) ? 6
+                                                  : (CHUNK ? 768 : 1024) / (B * B / PX))
     k_render(RenderArgs a) {
   __shared__ RSmem<B, FOV, MV, STATS, PX> sm;
   const uint32_t *vals = *a.sel ? a.pval_b : a.pval_a;
