@@ -831,11 +831,12 @@ __device__ __forceinline__ void render_item(const RenderArgs &a,
 // Whole tiles (CHUNK = false): one block per tile.  Chunked (CHUNK = true):
 // persistent blocks take work items from a queue -- first the chunks of the
 // heavy tiles, then the remaining tiles in order.
-// Blocks per SM: foveated two-pixel blocks get 6 (room for both
-// accumulators' registers without spills), the others fill 1024 threads.
+// Blocks per SM: foveated two-pixel blocks fill 768 threads (room for both
+// accumulators' registers: no spills with 16 x 16 tiles, fewer with 8 x 8),
+// the others 1024 (768 chunked).
 template <int B, bool FOV, bool MV, bool STATS, int PX, bool CHUNK>
-__global__ void __launch_bounds__(B * B / PX, (FOV && PX == 2 && !CHUNK) ? 6
-                                                  : (CHUNK ? 768 : 1024) / (B * B / PX))
+__global__ void __launch_bounds__(B * B / PX, ((FOV && PX == 2) || CHUNK ? 768 : 1024) /
+                                                  (B * B / PX))
     k_render(RenderArgs a) {
   __shared__ RSmem<B, FOV, MV, STATS, PX> sm;
   const uint32_t *vals = *a.sel ? a.pval_b : a.pval_a;
