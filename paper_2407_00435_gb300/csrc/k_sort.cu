@@ -1166,6 +1166,7 @@ struct EmitArgs {
 };
 
 constexpr uint32_t kBigItem = 64;   // items with more pairs go to k_emit_big
+static_assert(kBigItem < 128, "the emit's byte-packed row prefixes");
 constexpr int kEmitThreads = 128;
 
 // Adds the pair sort's digits of tile id t (lanes with `on`) to the block's
@@ -1253,8 +1254,26 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
       qb = __shfl_sync(0xffffffffu, qb, __ffs(hb) - 1);
       if (huge) a.bigq[qb + __popc(hb & ltmask)] = (uint32_t)k;
     }
-    uint4 tbl = make_uint4(0u, 0u, 0u, 0u);
-    if (TABLE && valid && !huge && cnt > 0) tbl = tload;
+    // the row table as byte-packed inclusive prefixes of the row lengths
+    // (at most kBigItem <= 127 pairs) and first columns: a pair's row is the
+    // number of prefixes <= its rank
+    uint32_t cumA = 0, cumB = 0, fstA = 0, fstB = 0;
+    if (TABLE && valid && !huge && cnt > 0) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int q = 0; q < kTableRows; ++q) {
+        int first, lastc;
+        table_row(tload, q, first, lastc);
+        run += lastc >= first ? (uint32_t)(lastc - first + 1) : 0u;
+        if (q < 4) {
+          cumA |= run << (8 * q);
+          fstA |= (uint32_t)first << (8 * q);
+        } else {
+          cumB |= run << (8 * (q - 4));
+          fstB |= (uint32_t)first << (8 * (q - 4));
+        }
+      }
+    }
     // the pairs this kernel writes: the warp's items without the queued ones,
     // numbered by a warp scan (queued items take no iterations here)
     const uint32_t ce = (valid && !huge) ? cnt : 0u;
@@ -1281,13 +1300,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
       const uint32_t ij = __shfl_sync(0xffffffffu, j, L);
       const uint32_t corner = __shfl_sync(0xffffffffu, e.x, L);
       const uint32_t tx = __shfl_sync(0xffffffffu, e.z, L);
-      uint4 it = make_uint4(0u, 0u, 0u, 0u);
-      uint32_t iw = 1;
+      uint32_t icA = 0, icB = 0, ifA = 0, ifB = 0, iw = 1;
       if (TABLE) {
-        it.x = __shfl_sync(0xffffffffu, tbl.x, L);
-        it.y = __shfl_sync(0xffffffffu, tbl.y, L);
-        it.z = __shfl_sync(0xffffffffu, tbl.z, L);
-        it.w = __shfl_sync(0xffffffffu, tbl.w, L);
+        icA = __shfl_sync(0xffffffffu, cumA, L);
+        icB = __shfl_sync(0xffffffffu, cumB, L);
+        ifA = __shfl_sync(0xffffffffu, fstA, L);
+        ifB = __shfl_sync(0xffffffffu, fstB, L);
       } else {
         iw = __shfl_sync(0xffffffffu, width, L);
       }
@@ -1298,22 +1316,16 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
       if (wr) {
         uint32_t row = 0, col = 0;
         if (TABLE) {
-          // walk the row table
-          uint32_t rem = rank;
-          bool found = false;
-#pragma unroll
-          for (int q = 0; q < kTableRows; ++q) {
-            int first, lastc;
-            table_row(it, q, first, lastc);
-            const uint32_t len = lastc >= first ? (uint32_t)(lastc - first + 1) : 0u;
-            if (!found && rem < len) {
-              row = (uint32_t)q;
-              col = (uint32_t)first + rem;
-              found = true;
-            }
-            if (!found) rem -= len;
-          }
-          wr = found;
+          // row = #{q : prefix_q <= rank}, byte by byte: (128 + rank) -
+          // prefix keeps its top bit iff prefix <= rank (both below 128: no
+          // borrow between bytes)
+          const uint32_t rb = (rank * 0x01010101u) | 0x80808080u;
+          row = (uint32_t)(__popc((rb - icA) & 0x80808080u) + __popc((rb - icB) & 0x80808080u));
+          const unsigned long long cum = (unsigned long long)icA | ((unsigned long long)icB << 32);
+          const unsigned long long fst = (unsigned long long)ifA | ((unsigned long long)ifB << 32);
+          const uint32_t prev = row ? (uint32_t)(cum >> (8 * (row - 1))) & 0xffu : 0u;
+          col = ((uint32_t)(fst >> (8 * row)) & 0xffu) + (rank - prev);
+          wr = row < (uint32_t)kTableRows;   // (always: rank < the item's count)
         } else {
           row = rank / iw;
           col = rank - row * iw;
