@@ -79,27 +79,45 @@ __device__ __forceinline__ int count_reached(float d2, float focal, const float 
 // count is taken by the channel-0 warps.
 constexpr int kRowRun = 8;
 
-__global__ void k_hvsq_rows(HvsqArgs a) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= 3LL * a.H) return;
-  const int y = (int)(warp / 3), c = (int)(warp % 3);
+// One block of three warps per image row (warp c: channel c).  Each chunk
+// of 256 pixels of both images is first staged in shared memory with
+// coalesced loads (channel-planar, 9 floats per 8 pixels so that the lanes'
+// runs fall in different banks); then lane l sums pixels 8l .. 8l + 7 in
+// order and a warp scan of the lane totals gives the prefixes.
+constexpr int kRowChunk = 32 * kRowRun;              // pixels per chunk
+constexpr int kRowPad = kRowChunk / 8 * 9;           // padded floats per channel
+
+__global__ void __launch_bounds__(96) k_hvsq_rows(HvsqArgs a) {
+  __shared__ float s_a[3][kRowPad], s_r[3][kRowPad];
+  __shared__ double s_out[3][kRowPad];   // one quantity's prefixes of the chunk, per warp
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const int y = blockIdx.x;
   const int W1 = a.W + 1;
   double *P0 = a.S + (4 * c) * a.plane + (long long)(y + 1) * W1 + 1;
   double carry[4] = {0.0, 0.0, 0.0, 0.0};
-  uint32_t cnt[kMaxRings + 1] = {};   // this lane's pixels per region (channel-0 warps)
-  for (int x0 = 0; x0 < a.W; x0 += 32 * kRowRun) {
+  uint32_t cnt[kMaxRings + 1] = {};   // this lane's pixels per region (channel-0 warp)
+  const float *arow = a.alt + 3LL * y * a.W, *rrow = a.ref + 3LL * y * a.W;
+  for (int x0 = 0; x0 < a.W; x0 += kRowChunk) {
+    const int n3 = 3 * min(kRowChunk, a.W - x0);
+    __syncthreads();   // the previous chunk is read
+    for (int q = threadIdx.x; q < 3 * kRowChunk; q += 96) {
+      const int px = q / 3, ch = q - 3 * px;
+      const int sidx = px + (px >> 3);
+      s_a[ch][sidx] = q < n3 ? arow[3LL * x0 + q] : 0.5f;
+      s_r[ch][sidx] = q < n3 ? rrow[3LL * x0 + q] : 0.5f;
+    }
+    __syncthreads();
     const int xs = x0 + lane * kRowRun;
     double run[4][kRowRun];
     double tot[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int u = 0; u < kRowRun; ++u) {
       const int x = xs + u;
+      const int sidx = lane * 9 + u;   // (8 lane + u) + (8 lane + u) / 8
       double v0 = 0.0, v2 = 0.0;
       if (x < a.W) {
-        const long long i = (long long)y * a.W + x;
-        v0 = (double)a.alt[3 * i + c] - 0.5;
-        v2 = (double)a.ref[3 * i + c] - 0.5;
+        v0 = (double)s_a[c][sidx] - 0.5;
+        v2 = (double)s_r[c][sidx] - 0.5;
         if (c == 0) {
           const int g = count_reached(dist2(a, x, y), a.focal, a.ring_tan, a.n_rings);
 #pragma unroll
@@ -122,9 +140,16 @@ __global__ void k_hvsq_rows(HvsqArgs a) {
         if (lane >= o) incl += t;
       }
       const double off = carry[q] + (incl - tot[q]);
+      // through shared memory, so that the global writes are coalesced
 #pragma unroll
-      for (int u = 0; u < kRowRun; ++u)
-        if (xs + u < a.W) P0[q * a.plane + xs + u] = run[q][u] + off;
+      for (int u = 0; u < kRowRun; ++u) s_out[c][lane * 9 + u] = run[q][u] + off;
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kRowRun; ++u) {
+        const int px = u * 32 + lane;
+        if (x0 + px < a.W) P0[q * a.plane + x0 + px] = s_out[c][px + (px >> 3)];
+      }
+      __syncwarp();
       carry[q] += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
@@ -381,7 +406,7 @@ extern "C" gs_status gs_hvsq(const float *alt, const float *ref, int32_t width, 
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const int W1 = width + 1, H1 = height + 1;
   const int strips = (W1 + 31) / 32;
-  k_hvsq_rows<<<(int)((3LL * height * 32 + 255) / 256), 256, 0, stream>>>(a);
+  k_hvsq_rows<<<height, 96, 0, stream>>>(a);
   k_scan_cols<<<kValPlanes * strips, 32 * kColSegs, 0, stream>>>(a.S, kValPlanes, W1, H1, a.plane);
   if (d_alt) {
     k_hvsq_stats<true><<<grid, kStatThreads, 0, stream>>>(a);
