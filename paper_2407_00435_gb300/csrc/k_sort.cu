@@ -995,7 +995,21 @@ static cudaError_t sort_any(const SortArgs &a, long long table_rows, cudaStream_
 }
 
 // ---- exclusive scan of pair counts in depth order -> emit offsets --------
-// Reduce-then-scan over the same fixed block ranges as the sort passes.
+// Reduce-then-scan over the same fixed block ranges as the sort passes: the
+// upsweep sums each block's counts, the downsweep adds up the sums of the
+// blocks before its own and scans its range.
+
+constexpr uint32_t kBigItem = 64;   // items with more pairs go to k_emit_big
+static_assert(kBigItem < 128, "the emit's byte-packed row prefixes");
+
+// An item the emit leaves to k_emit_big: more than kBigItem pairs, or (with a
+// row table: tight support or foveation) a rectangle too large for the table.
+__device__ __forceinline__ bool big_item(uint32_t cnt, uint32_t width_rows, bool table) {
+  const uint32_t width = width_rows & 0xffffu, rows = width_rows >> 16;
+  const bool small = rows <= (uint32_t)kTableRows && width <= (uint32_t)kTableCols;
+  return cnt > 0 && (cnt > kBigItem || (table && !small));
+}
+
 struct ScanArgs {
   const uint32_t *sorted_items[2];
   const uint32_t *sel;
@@ -1006,9 +1020,12 @@ struct ScanArgs {
   const unsigned long long *n_items;
   long long capacity;
   uint32_t *offsets;
-  unsigned long long *bsum;         // [G] block sums -> block bases
+  unsigned long long *bsum;         // [G] block sums
   int blocks;
   unsigned long long *n_pairs;
+  uint32_t *bigq;                   // depth positions of the items for k_emit_big
+  uint32_t *big_count;
+  int table;                        // the emit uses row tables (tight support or foveation)
 };
 
 __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
@@ -1016,13 +1033,15 @@ __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
   return (uint32_t)((long long)nn > a.capacity ? a.capacity : (long long)nn);
 }
 
-// Per-block pair sums in depth order.  Each visible item's count is gathered
-// once, by slot, and written out in depth order, so the offset downsweep and
-// the emit read counts sequentially.  1024 threads per block: the gathers
-// are random once the counts leave L2, so many must be in flight.  (Laying
-// out the 32-byte emit records in depth order here as well, so that the
-// emit would read nothing by slot, was measured slower: 10 us more at
-// 1080p, the same on a 64-view batch.)
+// Per-block pair sums in depth order.  Each visible item's emit record is
+// gathered once, by slot: its count is written out in depth order, so the
+// offset downsweep and the emit read counts sequentially, and its size
+// decides whether the item goes to the queue of k_emit_big (which can then
+// run beside the emit).  1024 threads per block: the gathers are random once
+// the records leave L2, so many must be in flight.  (Laying out the whole
+// 32-byte emit records in depth order here, so that the emit would read
+// nothing by slot, was measured slower: 10 us more at 1080p, the same on a
+// 64-view batch.)
 constexpr int kOffUpThreads = 1024, kOffUpUnroll = 8;
 
 __global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
@@ -1034,21 +1053,37 @@ __global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
   block_parts(n, a.blocks, blockIdx.x, p0, p1);
   const long long k0 = p0 * kSortPart;
   const long long k1 = p1 * kSortPart < (long long)n ? p1 * kSortPart : (long long)n;
+  const uint32_t ltmask = (1u << (threadIdx.x & 31)) - 1u;
   unsigned long long sum = 0;
   for (long long base = k0; base < k1; base += kOffUpThreads * kOffUpUnroll) {
-    uint32_t it[kOffUpUnroll], c[kOffUpUnroll];
+    uint32_t it[kOffUpUnroll], c[kOffUpUnroll], wr[kOffUpUnroll];
 #pragma unroll
     for (int u = 0; u < kOffUpUnroll; ++u) {
       const long long idx = base + u * kOffUpThreads + threadIdx.x;
       it[u] = idx < k1 ? items[idx] : 0xffffffffu;
     }
 #pragma unroll
-    for (int u = 0; u < kOffUpUnroll; ++u) c[u] = it[u] != 0xffffffffu ? a.count[it[u]] : 0u;
+    for (int u = 0; u < kOffUpUnroll; ++u) {
+      // (every item of the visible range has its record: the pair count
+      // writes one for each visible slot)
+      const uint4 e = it[u] != 0xffffffffu ? a.erec[2 * (size_t)it[u]] : make_uint4(0u, 0u, 0u, 0u);
+      c[u] = e.w;
+      wr[u] = e.y;
+    }
 #pragma unroll
     for (int u = 0; u < kOffUpUnroll; ++u) {
       const long long idx = base + u * kOffUpThreads + threadIdx.x;
       if (idx < k1) scount[idx] = c[u];
       sum += c[u];
+      const bool big = idx < k1 && big_item(c[u], wr[u], a.table != 0);
+      const uint32_t bb = __ballot_sync(0xffffffffu, big);
+      if (bb) {
+        const int leader = __ffs(bb) - 1;
+        uint32_t q0 = 0;
+        if ((int)(threadIdx.x & 31) == leader) q0 = atomicAdd(a.big_count, (uint32_t)__popc(bb));
+        q0 = __shfl_sync(0xffffffffu, q0, leader);
+        if (big) a.bigq[q0 + __popc(bb & ltmask)] = (uint32_t)idx;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -1061,36 +1096,6 @@ __global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_offsets_scan(ScanArgs a) {
-  __shared__ unsigned long long s_w[32];
-  const int G = a.blocks;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int per = (G + 1023) / 1024;
-  const int r0 = threadIdx.x * per < G ? threadIdx.x * per : G;
-  const int r1 = r0 + per < G ? r0 + per : G;
-  unsigned long long local = 0;
-  for (int r = r0; r < r1; ++r) local += a.bsum[r];
-  unsigned long long incl = local;
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  if (lane == 31) s_w[warp] = incl;
-  __syncthreads();
-  unsigned long long woff = 0, total = 0;
-  for (int w = 0; w < 32; ++w) {
-    if (w < warp) woff += s_w[w];
-    total += s_w[w];
-  }
-  unsigned long long run = woff + incl - local;
-  for (int r = r0; r < r1; ++r) {
-    const unsigned long long c = a.bsum[r];
-    a.bsum[r] = run;
-    run += c;
-  }
-  if (threadIdx.x == 0) *a.n_pairs = total;
-}
-
 __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
   __shared__ unsigned long long s_w[8];
   __shared__ unsigned long long s_carry;
@@ -1099,7 +1104,21 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   long long p0, p1;
   block_parts(n, a.blocks, blockIdx.x, p0, p1);
-  if (tid == 0) s_carry = a.bsum[blockIdx.x];
+  {
+    // this block's base: the sums of the blocks before it (a few hundred
+    // values, read from L2 by every block instead of a scan launch)
+    unsigned long long before = 0;
+    for (int r = tid; r < (int)blockIdx.x; r += 256) before += a.bsum[r];
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+    if (lane == 0) s_w[warp] = before;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < 8; ++w) t += s_w[w];
+      s_carry = t;
+    }
+    __syncthreads();
+  }
   for (long long part = p0; part < p1; ++part) {
     const long long base = part * kSortPart + (long long)tid * 16;
     uint32_t c[16];
@@ -1134,6 +1153,8 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
     __syncthreads();
     if (tid == 0) s_carry += total;
   }
+  // the last block's carry ends as the sum over all blocks
+  if (tid == 0 && (int)blockIdx.x == a.blocks - 1) *a.n_pairs = s_carry;
 }
 
 // ---- emit (tile, item) pairs in depth order ------------------------------
@@ -1165,8 +1186,6 @@ struct EmitArgs {
   uint32_t *status;
 };
 
-constexpr uint32_t kBigItem = 64;   // items with more pairs go to k_emit_big
-static_assert(kBigItem < 128, "the emit's byte-packed row prefixes");
 constexpr int kEmitThreads = 128;
 
 // Adds the pair sort's digits of tile id t (lanes with `on`) to the block's
@@ -1208,7 +1227,6 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
   const long long n = (long long)nn > a.item_capacity ? a.item_capacity : (long long)nn;
   const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const uint32_t ltmask = (1u << lane) - 1u;
   const uint32_t dmask = (1u << a.digit_bits) - 1u;
   if (blockIdx.x == 0 && threadIdx.x == 0 && (long long)*a.n_pairs > a.pair_capacity)
     set_status(a.status, GS_ERR_CAPACITY);
@@ -1242,18 +1260,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
     const uint4 tload = nt;
     const uint32_t cnt = e.w;
     load_item(base + warps * 32 + lane, nj, noff, ne, nt);
-    const uint32_t width = e.y & 0xffffu, rows = e.y >> 16;
-    // slots with no pairs (invisible ones) are never queued for the
-    // large-item emit; the table exists iff the rectangle is small
-    const bool small = rows <= (uint32_t)kTableRows && width <= (uint32_t)kTableCols;
-    const bool huge = valid && cnt > 0 && (cnt > kBigItem || (TABLE && !small));
-    const uint32_t hb = __ballot_sync(0xffffffffu, huge);
-    if (hb) {
-      uint32_t qb = 0;
-      if (lane == __ffs(hb) - 1) qb = atomicAdd(a.big_count, (uint32_t)__popc(hb));
-      qb = __shfl_sync(0xffffffffu, qb, __ffs(hb) - 1);
-      if (huge) a.bigq[qb + __popc(hb & ltmask)] = (uint32_t)k;
-    }
+    const uint32_t width = e.y & 0xffffu;
+    // items the offset upsweep queued for k_emit_big (the same test on the
+    // same record); the table exists iff the rectangle is small
+    const bool huge = valid && big_item(cnt, e.y, TABLE);
     // the row table as byte-packed inclusive prefixes of the row lengths
     // (at most kBigItem <= 127 pairs) and first columns: a pair's row is the
     // number of prefixes <= its rank
@@ -1564,8 +1574,13 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.bsum = reinterpret_cast<unsigned long long *>(bsum + (size_t)p->sort_blocks * kSortSub * 256);
   sa.blocks = G;
   sa.n_pairs = &hdr->n_pairs;
+  const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
+  sa.table = (p->has_fov || tight) ? 1 : 0;
+  sa.bigq = region<uint32_t>(p, ws, R_BIGQ);
+  sa.big_count = &hdr->big_count;
+  e = cudaMemsetAsync(&hdr->big_count, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
   k_offsets_up<<<G, kOffUpThreads, 0, s>>>(sa);
-  k_offsets_scan<<<1, 1024, 0, s>>>(sa);
   k_offsets_down<<<G, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
   // digit width: the requested one, else the balanced width of the fewest
@@ -1592,7 +1607,6 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.views = region<ViewDev>(p, ws, R_VIEWS);
   ea.tile_level = p->has_fov ? region<uint8_t>(p, ws, R_TILE_LEVEL) : nullptr;
   ea.rec_m = p->has_fov ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
-  const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
   ea.supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
   ea.supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
   ea.erec = sa.erec;
@@ -1609,23 +1623,28 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.passes = coop ? 0 : pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
-  ea.bigq = region<uint32_t>(p, ws, R_BIGQ);
-  ea.big_count = &hdr->big_count;
-  e = cudaMemsetAsync(&hdr->big_count, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  const bool fov = ea.tile_level != nullptr;
-  if (fov && tight) {
-    k_emit_expand<true><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
-    k_emit_big<true, true><<<g_stream_blocks, 256, 0, s>>>(ea);
-  } else if (fov) {
-    k_emit_expand<true><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
-    k_emit_big<true, false><<<g_stream_blocks, 256, 0, s>>>(ea);
-  } else if (tight) {
-    k_emit_expand<true><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
-    k_emit_big<false, true><<<g_stream_blocks, 256, 0, s>>>(ea);
-  } else {
-    k_emit_expand<false><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
-    k_emit_big<false, false><<<g_stream_blocks, 256, 0, s>>>(ea);
+  ea.bigq = sa.bigq;
+  ea.big_count = sa.big_count;
+  // the large items (queued by the offset upsweep) on the side stream, beside
+  // the emit of the others
+  {
+    const bool fov = ea.tile_level != nullptr;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    SideStream *ss = nullptr;
+    if ((e = side_stream(dev, ss)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ss->fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ss->st, ss->fork, 0)) != cudaSuccess) return e;
+    if (fov && tight) k_emit_big<true, true><<<g_stream_blocks, 256, 0, ss->st>>>(ea);
+    else if (fov) k_emit_big<true, false><<<g_stream_blocks, 256, 0, ss->st>>>(ea);
+    else if (tight) k_emit_big<false, true><<<g_stream_blocks, 256, 0, ss->st>>>(ea);
+    else k_emit_big<false, false><<<g_stream_blocks, 256, 0, ss->st>>>(ea);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ss->join, ss->st)) != cudaSuccess) return e;
+    if (fov || tight) k_emit_expand<true><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
+    else k_emit_expand<false><<<2 * g_stream_blocks, kEmitThreads, 0, s>>>(ea);
+    if ((e = cudaStreamWaitEvent(s, ss->join, 0)) != cudaSuccess) return e;
   }
   // 4. stable sort of the pairs by tile
   SortArgs t = {};

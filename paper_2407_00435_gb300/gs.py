@@ -426,14 +426,13 @@ class Renderer:
         # views, levels (+ level rows), project, pair count
         project = 1 + (2 if fov else 0) + (2 if self.n > 0 else 0)
         # depth sort (one cooperative launch, or hist, scan and 4 passes of
-        # upsweep + scan + downsweep), offsets (upsweep, scan, downsweep),
-        # emit + large-item emit, pair sort (one cooperative launch that also
-        # marks the tile ranges, or scan + 3 kernels per pass and a ranges
-        # kernel)
+        # upsweep + scan + downsweep), offsets (upsweep, downsweep), emit +
+        # large-item emit, pair sort (one cooperative launch that also marks
+        # the tile ranges, or scan + 3 kernels per pass and a ranges kernel)
         if _lib.gs_sort_is_cooperative():
-            sort = 0 if self.n == 0 else 1 + 3 + 2 + 1
+            sort = 0 if self.n == 0 else 1 + 2 + 2 + 1
         else:
-            sort = 0 if self.n == 0 else (2 + 4 * 3) + 3 + 2 + (1 + 3 * passes) + 1
+            sort = 0 if self.n == 0 else (2 + 4 * 3) + 2 + 2 + (1 + 3 * passes) + 1
         render = 1 + (1 if stats and self.n > 0 else 0)
         if self.cfg.chunk > 0 and not stats and self.T_tiles > 0:
             render += 1     # work list of the chunked render
