@@ -168,8 +168,9 @@ def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov, 
                    visible items' key and value written 8 (invisible slots
                    are dropped); each later pass per visible item: count
                    read 4, key + value read 8 and written 8
-      offsets      per visible item: item 4 read, count 4 gathered, count 4
-                   written in depth order; count 4 read, offset 4 written
+      offsets      per visible item: item 4 read, count and size 8 gathered
+                   (from the emit record), count 4 written in depth order;
+                   count 4 read, offset 4 written
       emit         per visible item: item 4 + offset 4 + count 4 read, emit
                    record 16 (+ 16 row table) gathered; per pair 8 written
       pair sort    per pair and pass: count read 4, key + value read 8 and
@@ -178,7 +179,7 @@ def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov, 
     table = 16 if (tight or fov) else 0
     count = n_slots * 4 + m_visible * (8 + (24 if tight else 0) + 4 + 16 + table)
     depth = n_slots * 8 + m_visible * 8 + (depth_passes - 1) * m_visible * 20
-    offsets = m_visible * (4 + 4 + 4 + 4 + 4)
+    offsets = m_visible * (4 + 8 + 4 + 4 + 4)
     emit = m_visible * (4 + 4 + 4 + 16 + table) + 8 * k_pairs
     pair = pair_passes * 20 * k_pairs
     ranges = 4 * k_pairs + 16 * tiles
