@@ -1026,6 +1026,8 @@ struct ScanArgs {
   uint32_t *bigq;                   // depth positions of the items for k_emit_big
   uint32_t *big_count;
   int table;                        // the emit uses row tables (tight support or foveation)
+  uint2 *ranges;                    // the per-tile ranges, zeroed here for the pair sort
+  long long n_ranges;
 };
 
 __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
@@ -1037,14 +1039,14 @@ __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
 // gathered once, by slot: its count is written out in depth order, so the
 // offset downsweep and the emit read counts sequentially, and its size
 // decides whether the item goes to the queue of k_emit_big (which can then
-// run beside the emit).  1024 threads per block: the gathers are random once
-// the records leave L2, so many must be in flight.  (Laying out the whole
-// 32-byte emit records in depth order here, so that the emit would read
-// nothing by slot, was measured slower: 10 us more at 1080p, the same on a
-// 64-view batch.)
-constexpr int kOffUpThreads = 1024, kOffUpUnroll = 8;
+// run beside the emit).  1024 threads per block, two blocks per SM: the
+// gathers are random once the records leave L2, so many must be in flight.
+// (Laying out the whole 32-byte emit records in depth order here, so that
+// the emit would read nothing by slot, was measured slower: 10 us more at
+// 1080p, the same on a 64-view batch.)
+constexpr int kOffUpThreads = 1024, kOffUpUnroll = 4;
 
-__global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
+__global__ void __launch_bounds__(kOffUpThreads, 2) k_offsets_up(ScanArgs a) {
   __shared__ unsigned long long s_w[kOffUpThreads / 32];
   const uint32_t n = scan_n(a);
   const uint32_t *items = *a.sel ? a.sorted_items[1] : a.sorted_items[0];
@@ -1066,9 +1068,11 @@ __global__ void __launch_bounds__(kOffUpThreads) k_offsets_up(ScanArgs a) {
     for (int u = 0; u < kOffUpUnroll; ++u) {
       // (every item of the visible range has its record: the pair count
       // writes one for each visible slot)
-      const uint4 e = it[u] != 0xffffffffu ? a.erec[2 * (size_t)it[u]] : make_uint4(0u, 0u, 0u, 0u);
-      c[u] = e.w;
-      wr[u] = e.y;
+      // the record's size and count words (one sector; two loads keep the
+      // registers at two blocks per SM)
+      const uint32_t *er = reinterpret_cast<const uint32_t *>(a.erec + 2 * (size_t)it[u]);
+      c[u] = it[u] != 0xffffffffu ? er[3] : 0u;
+      wr[u] = it[u] != 0xffffffffu ? er[1] : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kOffUpUnroll; ++u) {
@@ -1155,6 +1159,9 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
   }
   // the last block's carry ends as the sum over all blocks
   if (tid == 0 && (int)blockIdx.x == a.blocks - 1) *a.n_pairs = s_carry;
+  // empty ranges for the tiles the pair sort will not mark
+  for (long long q = (long long)blockIdx.x * 256 + tid; q < a.n_ranges; q += (long long)gridDim.x * 256)
+    a.ranges[q] = make_uint2(0u, 0u);
 }
 
 // ---- emit (tile, item) pairs in depth order ------------------------------
@@ -1518,8 +1525,11 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   Hdr *hdr = region<Hdr>(p, ws, R_HDR);
   cudaError_t e;
   init_grids();
-  // histograms of this stage start from zero
-  e = cudaMemsetAsync(&hdr->hist[0][0][0], 0, sizeof(hdr->hist), s);
+  // histograms of this stage and the large-item queue start from zero
+  // (adjacent header fields: one memset)
+  static_assert(offsetof(Hdr, hist) - offsetof(Hdr, big_count) == 2 * sizeof(uint32_t),
+                "big_count, pad2 and hist are adjacent");
+  e = cudaMemsetAsync(&hdr->big_count, 0, 2 * sizeof(uint32_t) + sizeof(hdr->hist), s);
   if (e != cudaSuccess) return e;
   if (p->n == 0) {
     // nothing visible: empty ranges
@@ -1578,8 +1588,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.table = (p->has_fov || tight) ? 1 : 0;
   sa.bigq = region<uint32_t>(p, ws, R_BIGQ);
   sa.big_count = &hdr->big_count;
-  e = cudaMemsetAsync(&hdr->big_count, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
+  sa.ranges = region<uint2>(p, ws, R_RANGES);
+  sa.n_ranges = p->tiles_total;
   k_offsets_up<<<G, kOffUpThreads, 0, s>>>(sa);
   k_offsets_down<<<G, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
@@ -1667,9 +1677,8 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   t.status = &hdr->status;
   // 5. per-tile ranges: by the cooperative sort after its last pass, else
   // by a kernel of their own
-  uint2 *ranges = region<uint2>(p, ws, R_RANGES);
-  e = cudaMemsetAsync(ranges, 0, p->bytes[R_RANGES], s);
-  if (e != cudaSuccess) return e;
+  // (the ranges were zeroed by the offset downsweep)
+  uint2 *ranges = sa.ranges;
   if (coop) {
     t.ranges = ranges;
     t.n_ranges = p->tiles_total;
