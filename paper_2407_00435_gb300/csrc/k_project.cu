@@ -559,6 +559,8 @@ __device__ __forceinline__ void project_value(const ProjArgs &a, const ProjSmem<
 //   [0] = (global tile id of the rectangle's corner, width | rows << 16,
 //          tiles per row of the item's view, count)
 //   [1] = the row table (only written, and only read, for items that have one)
+// It also clears the counter of the large-item queue that the offset
+// upsweep, which runs after it, fills.
 constexpr int kCountThreads = 256;
 
 __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
@@ -568,6 +570,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
   const long long warps = (long long)gridDim.x * (kCountThreads / 32);
   const long long wid = (long long)blockIdx.x * (kCountThreads / 32) + wl;
   const bool tight = a.rec_supp != nullptr, fov = a.tile_level != nullptr;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->big_count = 0u;
   for (long long base = wid * 32; base < slots; base += warps * 32) {
     const long long j = base + lane;
     // every record the item may need, loaded at once (invisible slots hold

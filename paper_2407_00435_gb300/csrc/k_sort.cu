@@ -57,6 +57,8 @@ struct SortArgs {
                                      //   to 0xffffffff (the result holds the others only)
   uint2 *ranges;                     // cooperative sort: [start, end) of each key value in
   long long n_ranges;                //   the result (keys < n_ranges; zeroed by the caller)
+  int extra_zeroed;                  // cooperative sort: the caller cleared the barrier word
+                                     //   and the first parity of sums (coop_extra)
   uint32_t *status;
   int sub;                           // upsweep sub-ranges per block, 1..kSortSub (0: kSortSub)
 };
@@ -938,9 +940,12 @@ static int coop_grid(int shape = kCoop512x1) {
 template <int NT, int NBK>
 static cudaError_t run_sort_coop(const SortArgs &a, int G, cudaStream_t s) {
   // the barrier word and parity 0 of the sums start at zero
-  cudaError_t e = cudaMemsetAsync(a.bsum + (size_t)2 * G * NBK, 0,
-                                  (size_t)(64 + kCoopSumRows * NBK) * sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (!a.extra_zeroed) {
+    e = cudaMemsetAsync(a.bsum + (size_t)2 * G * NBK, 0,
+                        (size_t)(64 + kCoopSumRows * NBK) * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(NT);
@@ -978,12 +983,26 @@ static bool coop_sort_ok(int shape, long long table_rows, int nbk = 256) {
   return G > 0 && G <= kCoopGroup * kCoopMaxGroups && coop_table_rows(G, nbk) <= table_rows;
 }
 
+// The shape of the cooperative sort that sort_any runs for digits of nbk
+// values and the requested shape, or -1 (the multi-kernel sort).
+static int coop_pick(int nbk, long long table_rows, int shape) {
+  if (shape == kCoop1024x1 && !coop_sort_ok(shape, table_rows, nbk)) shape = kCoop512x1;
+  shape = coop_shape_for(nbk, shape);
+  return coop_sort_ok(shape, table_rows, nbk) ? shape : -1;
+}
+
+// The words of a.bsum that a cooperative sort of that shape needs cleared
+// before it starts (its barrier word and first parity of sums).
+static uint32_t *coop_extra(uint32_t *bsum, int shape, int nbk, long long &words) {
+  words = 64 + (long long)kCoopSumRows * nbk;
+  return bsum + (size_t)2 * coop_grid(shape) * nbk;
+}
+
 static cudaError_t sort_any(const SortArgs &a, long long table_rows, cudaStream_t s,
                             bool hist_done = false, int shape = kCoop512x1) {
   const int nbk = sort_nbk(a);
-  if (shape == kCoop1024x1 && !coop_sort_ok(shape, table_rows, nbk)) shape = kCoop512x1;
-  shape = coop_shape_for(nbk, shape);
-  if (coop_sort_ok(shape, table_rows, nbk)) {
+  shape = coop_pick(nbk, table_rows, shape);
+  if (shape >= 0) {
     const int G = coop_grid(shape);
     if (nbk == 1024) return run_sort_coop<1024, 1024>(a, G, s);
     if (shape == kCoop1024x1) return run_sort_coop<1024, 512>(a, G, s);
@@ -1028,6 +1047,8 @@ struct ScanArgs {
   int table;                        // the emit uses row tables (tight support or foveation)
   uint2 *ranges;                    // the per-tile ranges, zeroed here for the pair sort
   long long n_ranges;
+  uint32_t *clear;                  // words zeroed here for the cooperative pair sort, or null
+  long long n_clear;
 };
 
 __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
@@ -1159,9 +1180,12 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
   }
   // the last block's carry ends as the sum over all blocks
   if (tid == 0 && (int)blockIdx.x == a.blocks - 1) *a.n_pairs = s_carry;
-  // empty ranges for the tiles the pair sort will not mark
-  for (long long q = (long long)blockIdx.x * 256 + tid; q < a.n_ranges; q += (long long)gridDim.x * 256)
-    a.ranges[q] = make_uint2(0u, 0u);
+  // empty ranges for the tiles the pair sort will not mark, and the pair
+  // sort's barrier word and sums
+  const long long t0 = (long long)blockIdx.x * 256 + tid, tstride = (long long)gridDim.x * 256;
+  for (long long q = t0; q < a.n_ranges; q += tstride) a.ranges[q] = make_uint2(0u, 0u);
+  if (a.clear)
+    for (long long q = t0; q < a.n_clear; q += tstride) a.clear[q] = 0u;
 }
 
 // ---- emit (tile, item) pairs in depth order ------------------------------
@@ -1525,12 +1549,26 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   Hdr *hdr = region<Hdr>(p, ws, R_HDR);
   cudaError_t e;
   init_grids();
-  // histograms of this stage and the large-item queue start from zero
-  // (adjacent header fields: one memset)
-  static_assert(offsetof(Hdr, hist) - offsetof(Hdr, big_count) == 2 * sizeof(uint32_t),
-                "big_count, pad2 and hist are adjacent");
-  e = cudaMemsetAsync(&hdr->big_count, 0, 2 * sizeof(uint32_t) + sizeof(hdr->hist), s);
-  if (e != cudaSuccess) return e;
+  // pair sort digit width: the requested one, else the balanced width of the
+  // fewest passes of at most 8 bits; widths of 9 or 10 bits only with the
+  // cooperative sort (else 8)
+  const long long table_rows = (long long)p->sort_blocks * kSortSub;
+  int want = p->radix_bits > 0 ? p->radix_bits : 8;
+  if (want > 8 && !coop_sort_ok(kCoop512x2, table_rows, want == 9 ? 512 : 1024)) want = 8;
+  int pair_passes = (p->tile_bits + want - 1) / want;
+  if (pair_passes > 4) pair_passes = 4;   // histogram storage holds four passes
+  const int pair_bits = (p->tile_bits + pair_passes - 1) / pair_passes;
+  const int pair_nbk = pair_bits <= 8 ? 256 : (pair_bits == 9 ? 512 : 1024);
+  const int pair_shape = coop_pick(pair_nbk, table_rows, kCoop512x2);
+  const bool coop = pair_shape >= 0;
+  const bool depth_coop =
+      coop_pick(512, table_rows, p->n * p->V > kDepthOverlapMaxSlots ? kCoop1024x1 : kCoop512x1) >= 0;
+  // the multi-kernel sorts' histograms start from zero (the large-item
+  // queue counter is cleared by the pair count)
+  if (!coop || !depth_coop) {
+    e = cudaMemsetAsync(&hdr->hist[0][0][0], 0, sizeof(hdr->hist), s);
+    if (e != cudaSuccess) return e;
+  }
   if (p->n == 0) {
     // nothing visible: empty ranges
     e = cudaMemsetAsync(region<uint2>(p, ws, R_RANGES), 0, p->bytes[R_RANGES], s);
@@ -1590,18 +1628,10 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.big_count = &hdr->big_count;
   sa.ranges = region<uint2>(p, ws, R_RANGES);
   sa.n_ranges = p->tiles_total;
+  if (coop) sa.clear = coop_extra(bsum, pair_shape, pair_nbk, sa.n_clear);
   k_offsets_up<<<G, kOffUpThreads, 0, s>>>(sa);
   k_offsets_down<<<G, 256, 0, s>>>(sa);
   // 3. emit pairs (+ the pair sort's histograms)
-  // digit width: the requested one, else the balanced width of the fewest
-  // passes of at most 8 bits; widths of 9 or 10 bits only with the
-  // cooperative sort (else 8)
-  const long long table_rows = (long long)p->sort_blocks * kSortSub;
-  int want = p->radix_bits > 0 ? p->radix_bits : 8;
-  if (want > 8 && !coop_sort_ok(kCoop512x2, table_rows, want == 9 ? 512 : 1024)) want = 8;
-  int pair_passes = (p->tile_bits + want - 1) / want;
-  if (pair_passes > 4) pair_passes = 4;   // histogram storage holds four passes
-  const int pair_bits = (p->tile_bits + pair_passes - 1) / pair_passes;
   EmitArgs ea = {};
   ea.sorted_items[0] = d.vals[0];
   ea.sorted_items[1] = d.vals[1];
@@ -1629,7 +1659,6 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.hist = &hdr->hist[1][0][0];
   // the cooperative pair sort counts its own digits: the emit's histograms
   // are only needed by the multi-kernel sort
-  const bool coop = coop_sort_ok(kCoop512x2, table_rows, pair_bits <= 8 ? 256 : (pair_bits == 9 ? 512 : 1024));
   ea.passes = coop ? 0 : pair_passes;
   ea.digit_bits = pair_bits;
   ea.status = &hdr->status;
@@ -1682,6 +1711,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   if (coop) {
     t.ranges = ranges;
     t.n_ranges = p->tiles_total;
+    t.extra_zeroed = 1;   // (by the offset downsweep)
   }
   e = sort_any(t, (long long)p->sort_blocks * kSortSub,
                s, /*hist_done=*/!coop, kCoop512x2);
