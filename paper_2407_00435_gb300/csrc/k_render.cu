@@ -149,17 +149,11 @@ __device__ __forceinline__ void composite_plain(const uint16_t *list, int nlist,
                                                 const float4 *ra, const float4 *rb,
                                                 const float4 *rc, int base, const Pix<PX> &pp,
                                                 Acc (&A)[PX], uint32_t (&walk_end)[PX]) {
-  // pixel centres packed twice: the paired FMA operands of eval_s2; the
-  // later pixels of the thread lie dy rows below the one before, so their
-  // whitened offsets are the previous ones plus dy (w1y, w2y): one paired FMA
+  // pixel centres packed twice: the paired FMA operands of eval_s2
   const unsigned long long px2 = f2_pack(pp.px, pp.px);
-  const unsigned long long py2 = f2_pack(pp.py[0], pp.py[0]);
-  unsigned long long dy2[PX];
+  unsigned long long py2[PX];
 #pragma unroll
-  for (int k = 1; k < PX; ++k) {
-    const float dy = pp.py[k] - pp.py[k - 1];
-    dy2[k] = f2_pack(dy, dy);
-  }
+  for (int k = 0; k < PX; ++k) py2[k] = f2_pack(pp.py[k], pp.py[k]);
   // unrolled so that the shared-memory loads of later entries are issued
   // above the arithmetic of earlier ones (measured faster than 1, 2, 4 or 6)
 #pragma unroll 8
@@ -167,13 +161,10 @@ __device__ __forceinline__ void composite_plain(const uint16_t *list, int nlist,
     const int q = list[li];
     const float4 sa = ra[q], sb = rb[q], c = rc[q];
     const int pos = base + q;
-    unsigned long long tt = 0;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
       float t1, t2;
-      tt = k == 0 ? eval_t2(px2, py2, sa, sb) : f2_fma(f2_pack(sa.z, sa.w), dy2[k], tt);
-      f2_unpack(tt, t1, t2);
-      const float sq = __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
+      const float sq = eval_s2(px2, py2[k], sa, sb, t1, t2);
       const float al = alpha_of(__fsub_rn(c.w, sq));
       const float Tn = __fmaf_rn(-al, A[k].T, A[k].T);
       const bool hit = !A[k].done && sq <= sb.z;

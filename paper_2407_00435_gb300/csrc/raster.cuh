@@ -174,16 +174,10 @@ __device__ __forceinline__ void make_eval(float mx, float my, float4 sh, float F
 //   t1 = fma(w1x, px, fma(w1y, py, c1)),  t2 = fma(w2x, px, fma(w2y, py, c2)),
 //   s = fma(t1, t1, t2 * t2).
 // The point can blend iff s <= F - floor, and then alpha = min(0.99, 2^(F - s)).
-// eval_t2 returns (t1, t2) packed; eval_s2 unpacks them and returns s.
-__device__ __forceinline__ unsigned long long eval_t2(unsigned long long px2, unsigned long long py2,
-                                                      float4 a, float4 b) {
-  const unsigned long long in = f2_fma(f2_pack(a.z, a.w), py2, f2_pack(b.x, b.y));
-  return f2_fma(f2_pack(a.x, a.y), px2, in);
-}
-
 __device__ __forceinline__ float eval_s2(unsigned long long px2, unsigned long long py2,
                                          float4 a, float4 b, float &t1, float &t2) {
-  f2_unpack(eval_t2(px2, py2, a, b), t1, t2);
+  const unsigned long long in = f2_fma(f2_pack(a.z, a.w), py2, f2_pack(b.x, b.y));
+  f2_unpack(f2_fma(f2_pack(a.x, a.y), px2, in), t1, t2);
   return __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
 }
 
