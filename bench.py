@@ -163,23 +163,24 @@ def bin_sort_bytes(n_slots, m_visible, k_pairs, tiles, pair_passes, tight, fov, 
     reads and writes, no cache effects):
       pair count   per item slot: depth key 4 read; per visible item:
                    rectangle 8 (+ tight support 24) read, count 4 + emit
-                   record 16 (+ row table 16 with a filter) written
+                   record 16 (+ row table 16 with a filter) + count word 4
+                   written
       depth sort   pass 0 over every slot: count read 4 + key read 4, the
                    visible items' key and value written 8 (invisible slots
                    are dropped); each later pass per visible item: count
                    read 4, key + value read 8 and written 8
-      offsets      per visible item: item 4 read, count and size 8 gathered
-                   (from the emit record), count 4 written in depth order;
-                   count 4 read, offset 4 written
+      offsets      per visible item: item 4 read, count word 4 gathered,
+                   count 4 written in depth order; count 4 read, offset 4
+                   written
       emit         per visible item: item 4 + offset 4 + count 4 read, emit
                    record 16 (+ 16 row table) gathered; per pair 8 written
       pair sort    per pair and pass: count read 4, key + value read 8 and
                    written 8
       ranges       per pair 4 read; per tile 8 written (+ 8 cleared)"""
     table = 16 if (tight or fov) else 0
-    count = n_slots * 4 + m_visible * (8 + (24 if tight else 0) + 4 + 16 + table)
+    count = n_slots * 4 + m_visible * (8 + (24 if tight else 0) + 4 + 16 + table + 4)
     depth = n_slots * 8 + m_visible * 8 + (depth_passes - 1) * m_visible * 20
-    offsets = m_visible * (4 + 8 + 4 + 4 + 4)
+    offsets = m_visible * (4 + 4 + 4 + 4 + 4)
     emit = m_visible * (4 + 4 + 4 + 16 + table) + 8 * k_pairs
     pair = pair_passes * 20 * k_pairs
     ranges = 4 * k_pairs + 16 * tiles
@@ -572,6 +573,15 @@ def extra_foveated(torch, gs, synth, flush, steps, points=None):
         for q, nm in enumerate(("project", "bin_sort", "render")):
             st[nm].append(ev[q].elapsed_time(ev[q + 1]))
     stages = {k: round(sorted(v)[len(v) // 2], 4) for k, v in st.items()}
+    # one more staged frame in an NVTX range (what kernel profiles of this
+    # workload select)
+    flush()
+    torch.cuda.nvtx.range_push("foveated_frame")
+    rf.project(sc, f)
+    rf.bin_sort()
+    rf.render(of, fov=True)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
     peaks, _ = _peaks()
     n_sm = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
     peak_tops = n_sm * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12

@@ -108,6 +108,7 @@ gs_status gs_plan_init(gs_plan *p, int64_t n, int32_t sh_degree, const gs_camera
   b[R_REC_SUPP] = tight ? 16 * (size_t)M : 0;
   b[R_REC_SUPP2] = tight ? 8 * (size_t)M : 0;
   b[R_REC_EMIT] = 32 * (size_t)M;
+  b[R_REC_CBIG] = 4 * (size_t)M;
   b[R_DKEY_A] = b[R_DKEY_B] = b[R_DVAL_A] = b[R_DVAL_B] = 4 * (size_t)M;
   b[R_OFFSETS] = 4 * (size_t)M;
   b[R_PKEY_A] = b[R_PKEY_B] = b[R_PVAL_A] = b[R_PVAL_B] = 4 * (size_t)K;

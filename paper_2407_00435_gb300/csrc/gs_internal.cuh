@@ -50,6 +50,7 @@ enum Region : int {
   R_REC_SUPP2,   // float2 tight support (covariance c, tau) [tight]
   R_REC_EMIT,    // 2 x uint4 emit record per item slot: (corner tile, width | rows << 16,
                  //   tiles per row, count), row intervals of rectangles of <= 8 rows
+  R_REC_CBIG,    // u32 count | (item goes to the large-item emit) << 31, visible slots
   R_DKEY_A, R_DKEY_B, R_DVAL_A, R_DVAL_B,   // depth sort ping-pong (M)
   R_OFFSETS,     // u32 exclusive pair offsets in depth order (M)
   R_PKEY_A, R_PKEY_B, R_PVAL_A, R_PVAL_B,   // pair sort ping-pong (K)

@@ -204,6 +204,7 @@ struct ProjArgs {
   float4 *rec_supp;             // (u, v, a, b)
   float2 *rec_supp2;            // (c, tau)
   uint4 *rec_emit;               // emit records, 2 per slot (see k_count_pairs)
+  uint32_t *rec_cbig;            // count | large-item flag << 31 (see k_count_pairs)
   const uint32_t *level_rows;    // columns kept by the foveation filter, per row and level
   const float *opacity_lv;      // (L-1, N) level opacities the support must cover, or null
   int n_opacity_lv;
@@ -559,8 +560,9 @@ __device__ __forceinline__ void project_value(const ProjArgs &a, const ProjSmem<
 //   [0] = (global tile id of the rectangle's corner, width | rows << 16,
 //          tiles per row of the item's view, count)
 //   [1] = the row table (only written, and only read, for items that have one)
-// It also clears the counter of the large-item queue that the offset
-// upsweep, which runs after it, fills.
+// and, in a compact array, the count with the large-item flag in bit 31 (what
+// the offset upsweep gathers in depth order).  It also clears the counter of
+// the large-item queue that the upsweep, which runs after it, fills.
 constexpr int kCountThreads = 256;
 
 __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
@@ -737,6 +739,8 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
       a.rec_count[j] = my_count;
       a.rec_emit[2 * j] = make_uint4(corner, (uint32_t)(x1 - x0 + 1) | ((uint32_t)(y1 - y0 + 1) << 16),
                                      (uint32_t)vd.tx, my_count);
+      const bool big = big_item(my_count, tight || fov, has_table(x0, x1, y0, y1));
+      a.rec_cbig[j] = my_count | (big ? 0x80000000u : 0u);
     }
     __syncwarp();
   }
@@ -942,6 +946,7 @@ static ProjArgs make_proj_args(const gs_plan *p, void *ws) {
   a.rec_supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
   a.rec_supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
   a.rec_emit = region<uint4>(p, ws, R_REC_EMIT);
+  a.rec_cbig = region<uint32_t>(p, ws, R_REC_CBIG);
   a.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
   a.opacity_lv = p->has_fov ? p->fov.opacity_lv : nullptr;
   a.n_opacity_lv = a.opacity_lv ? p->fov.n_levels - 1 : 0;

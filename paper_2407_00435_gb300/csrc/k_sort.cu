@@ -1018,24 +1018,13 @@ static cudaError_t sort_any(const SortArgs &a, long long table_rows, cudaStream_
 // upsweep sums each block's counts, the downsweep adds up the sums of the
 // blocks before its own and scans its range.
 
-constexpr uint32_t kBigItem = 64;   // items with more pairs go to k_emit_big
-static_assert(kBigItem < 128, "the emit's byte-packed row prefixes");
-
-// An item the emit leaves to k_emit_big: more than kBigItem pairs, or (with a
-// row table: tight support or foveation) a rectangle too large for the table.
-__device__ __forceinline__ bool big_item(uint32_t cnt, uint32_t width_rows, bool table) {
-  const uint32_t width = width_rows & 0xffffu, rows = width_rows >> 16;
-  const bool small = rows <= (uint32_t)kTableRows && width <= (uint32_t)kTableCols;
-  return cnt > 0 && (cnt > kBigItem || (table && !small));
-}
-
 struct ScanArgs {
   const uint32_t *sorted_items[2];
   const uint32_t *sel;
   const uint32_t *count;            // rec_count (by item)
   uint32_t *sorted_count[2];        // the counts in depth order: the depth sort's free key
                                     //   buffer (written by the upsweep, read by the rest)
-  const uint4 *erec;                // emit records of the pair count (2 per item slot)
+  const uint32_t *cbig;             // count | large-item flag << 31, by item slot
   const unsigned long long *n_items;
   long long capacity;
   uint32_t *offsets;
@@ -1044,7 +1033,6 @@ struct ScanArgs {
   unsigned long long *n_pairs;
   uint32_t *bigq;                   // depth positions of the items for k_emit_big
   uint32_t *big_count;
-  int table;                        // the emit uses row tables (tight support or foveation)
   uint2 *ranges;                    // the per-tile ranges, zeroed here for the pair sort
   long long n_ranges;
   uint32_t *clear;                  // words zeroed here for the cooperative pair sort, or null
@@ -1056,12 +1044,14 @@ __device__ __forceinline__ uint32_t scan_n(const ScanArgs &a) {
   return (uint32_t)((long long)nn > a.capacity ? a.capacity : (long long)nn);
 }
 
-// Per-block pair sums in depth order.  Each visible item's emit record is
-// gathered once, by slot: its count is written out in depth order, so the
-// offset downsweep and the emit read counts sequentially, and its size
-// decides whether the item goes to the queue of k_emit_big (which can then
-// run beside the emit).  1024 threads per block, two blocks per SM: the
-// gathers are random once the records leave L2, so many must be in flight.
+// Per-block pair sums in depth order.  Each visible item's count word (the
+// count and the pair count's large-item flag, in a compact array that stays
+// in L2 longer than the 32-byte emit records) is gathered once, by slot: the
+// count is written out in depth order, so the offset downsweep and the emit
+// read counts sequentially, and the flag puts the item in the queue of
+// k_emit_big (which can then run beside the emit).  1024 threads per block,
+// two blocks per SM: the gathers are random once the words leave L2, so many
+// must be in flight.
 // (Laying out the whole 32-byte emit records in depth order here, so that
 // the emit would read nothing by slot, was measured slower: 10 us more at
 // 1080p, the same on a 64-view batch.)
@@ -1079,28 +1069,23 @@ __global__ void __launch_bounds__(kOffUpThreads, 2) k_offsets_up(ScanArgs a) {
   const uint32_t ltmask = (1u << (threadIdx.x & 31)) - 1u;
   unsigned long long sum = 0;
   for (long long base = k0; base < k1; base += kOffUpThreads * kOffUpUnroll) {
-    uint32_t it[kOffUpUnroll], c[kOffUpUnroll], wr[kOffUpUnroll];
+    uint32_t it[kOffUpUnroll], c[kOffUpUnroll];
 #pragma unroll
     for (int u = 0; u < kOffUpUnroll; ++u) {
       const long long idx = base + u * kOffUpThreads + threadIdx.x;
       it[u] = idx < k1 ? items[idx] : 0xffffffffu;
     }
+    // (every item of the visible range has its word: the pair count writes
+    // one for each visible slot)
 #pragma unroll
-    for (int u = 0; u < kOffUpUnroll; ++u) {
-      // (every item of the visible range has its record: the pair count
-      // writes one for each visible slot)
-      // the record's size and count words (one sector; two loads keep the
-      // registers at two blocks per SM)
-      const uint32_t *er = reinterpret_cast<const uint32_t *>(a.erec + 2 * (size_t)it[u]);
-      c[u] = it[u] != 0xffffffffu ? er[3] : 0u;
-      wr[u] = it[u] != 0xffffffffu ? er[1] : 0u;
-    }
+    for (int u = 0; u < kOffUpUnroll; ++u) c[u] = it[u] != 0xffffffffu ? a.cbig[it[u]] : 0u;
 #pragma unroll
     for (int u = 0; u < kOffUpUnroll; ++u) {
       const long long idx = base + u * kOffUpThreads + threadIdx.x;
-      if (idx < k1) scount[idx] = c[u];
-      sum += c[u];
-      const bool big = idx < k1 && big_item(c[u], wr[u], a.table != 0);
+      const uint32_t cnt = c[u] & 0x7fffffffu;
+      if (idx < k1) scount[idx] = cnt;
+      sum += cnt;
+      const bool big = idx < k1 && (c[u] >> 31) != 0u;
       const uint32_t bb = __ballot_sync(0xffffffffu, big);
       if (bb) {
         const int leader = __ffs(bb) - 1;
@@ -1291,10 +1276,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_expand(EmitArgs a) {
     const uint4 tload = nt;
     const uint32_t cnt = e.w;
     load_item(base + warps * 32 + lane, nj, noff, ne, nt);
-    const uint32_t width = e.y & 0xffffu;
-    // items the offset upsweep queued for k_emit_big (the same test on the
-    // same record); the table exists iff the rectangle is small
-    const bool huge = valid && big_item(cnt, e.y, TABLE);
+    const uint32_t width = e.y & 0xffffu, rows = e.y >> 16;
+    // items the offset upsweep queued for k_emit_big (the pair count's test,
+    // taken again on the same record); the table exists iff the rectangle
+    // is small
+    const bool small = rows <= (uint32_t)kTableRows && width <= (uint32_t)kTableCols;
+    const bool huge = valid && big_item(cnt, TABLE, small);
     // the row table as byte-packed inclusive prefixes of the row lengths
     // (at most kBigItem <= 127 pairs) and first columns: a pair's row is the
     // number of prefixes <= its rank
@@ -1618,12 +1605,11 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   sa.offsets = region<uint32_t>(p, ws, R_OFFSETS);
   sa.sorted_count[0] = d.keys[0];    // the one of the two the depth sort did not end in
   sa.sorted_count[1] = d.keys[1];
-  sa.erec = region<uint4>(p, ws, R_REC_EMIT);
+  sa.cbig = region<uint32_t>(p, ws, R_REC_CBIG);
   sa.bsum = reinterpret_cast<unsigned long long *>(bsum + (size_t)p->sort_blocks * kSortSub * 256);
   sa.blocks = G;
   sa.n_pairs = &hdr->n_pairs;
   const bool tight = (p->flags & GS_FLAG_TIGHT) != 0;
-  sa.table = (p->has_fov || tight) ? 1 : 0;
   sa.bigq = region<uint32_t>(p, ws, R_BIGQ);
   sa.big_count = &hdr->big_count;
   sa.ranges = region<uint2>(p, ws, R_RANGES);
@@ -1649,7 +1635,7 @@ cudaError_t launch_bin_sort(const gs_plan *p, void *ws, cudaStream_t s) {
   ea.rec_m = p->has_fov ? region<uint8_t>(p, ws, R_REC_M) : nullptr;
   ea.supp = tight ? region<float4>(p, ws, R_REC_SUPP) : nullptr;
   ea.supp2 = tight ? region<float2>(p, ws, R_REC_SUPP2) : nullptr;
-  ea.erec = sa.erec;
+  ea.erec = region<uint4>(p, ws, R_REC_EMIT);
   ea.level_rows = p->has_fov ? region<uint32_t>(p, ws, R_LEVEL_ROWS) : nullptr;
   ea.tile = p->tile;
   ea.n_pairs = &hdr->n_pairs;

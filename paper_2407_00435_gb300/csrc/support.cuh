@@ -120,6 +120,16 @@ __device__ __forceinline__ bool has_table(int x0, int x1, int y0, int y1) {
   return y1 - y0 < kTableRows && x1 - x0 < kTableCols;
 }
 
+// Items the emit leaves to its large-item kernel: more than kBigItem pairs,
+// or (when the emit reads row tables: tight support or foveation) a
+// rectangle without a table.
+constexpr uint32_t kBigItem = 64;
+static_assert(kBigItem < 128, "the emit's byte-packed row prefixes");
+
+__device__ __forceinline__ bool big_item(uint32_t cnt, bool table, bool small) {
+  return cnt > 0 && (cnt > kBigItem || (table && !small));
+}
+
 // Columns [la, lb] of global tile row `grow` whose tile level is <= m (the
 // foveation filter keeps a pair iff tile level <= m).  A tile's level is a
 // non-decreasing function of the smallest gaze distance of its pixels,
