@@ -99,86 +99,88 @@ __device__ __forceinline__ int pixel_need_level(const ViewDev &vd, int L, float 
   return need;
 }
 
-// One block per tile; the tile's filter level is the smallest level any of
-// its pixels needs (Sec. 4.2: a point takes part in a tile only if the
-// tile's level t <= m).
-__global__ void k_tile_levels(const ViewDev *views, int V, int tile, int L, float band,
-                              uint8_t *tile_level, long long tiles_total) {
-  long long t = blockIdx.x;
-  if (t >= tiles_total) return;
+// One warp per tile (four tiles per block); the tile's filter level is the
+// smallest level any of its pixels needs (Sec. 4.2: a point takes part in a
+// tile only if the tile's level t <= m).
+constexpr int kLevelWarps = 4;
+
+__global__ void __launch_bounds__(32 * kLevelWarps) k_tile_levels(const ViewDev *views, int V,
+                                                                  int tile, int L, float band,
+                                                                  uint8_t *tile_level,
+                                                                  long long tiles_total) {
+  const long long t = (long long)blockIdx.x * kLevelWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= tiles_total) return;   // (whole warps)
   // find the view by binary search over tile bases
   int lo = 0, hi = V - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (views[mid].tile_base <= t) lo = mid; else hi = mid - 1;
   }
-  const ViewDev vd = views[lo];
+  const ViewDev &vd = views[lo];
   int local = (int)(t - vd.tile_base);
   int bx = local % vd.tx, by = local / vd.tx;
   int need = 255;
   if (vd.fov) {
-    for (int q = threadIdx.x; q < tile * tile; q += blockDim.x) {
+    for (int q = lane; q < tile * tile; q += 32) {
       int x = bx * tile + q % tile, y = by * tile + q / tile;
       if (x < vd.W && y < vd.H) need = min(need, pixel_need_level(vd, L, band, x, y));
     }
   } else {
     need = 1;
   }
-  // block minimum
-  for (int o = 16; o > 0; o >>= 1) need = min(need, __shfl_xor_sync(0xffffffffu, need, o));
-  __shared__ int wmin[32];
-  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = need;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int m = 255;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = min(m, wmin[w]);
-    tile_level[t] = (uint8_t)m;
-  }
+  need = (int)__reduce_min_sync(0xffffffffu, (unsigned)need);
+  if (lane == 0) tile_level[t] = (uint8_t)need;
 }
 
 // Per tile row and level m, the columns whose tile level is <= m (one
-// interval, see level_row).
-__global__ void k_level_rows(const ViewDev *views, int V, const uint8_t *tile_level,
-                             long long rows_total, uint32_t *out) {
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < rows_total;
-       g += (long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = V - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (views[mid].row_base <= g) lo = mid; else hi = mid - 1;
-    }
-    const ViewDev &vd = views[lo];
-    const uint8_t *tl = tile_level + vd.tile_base + (g - vd.row_base) * vd.tx;
-    int first[GS_MAX_LEVELS], last[GS_MAX_LEVELS];
+// interval, see level_row): one warp per tile row, lanes over its columns,
+// first and last column per level by warp reductions.
+__global__ void __launch_bounds__(32 * kLevelWarps) k_level_rows(const ViewDev *views, int V,
+                                                                 const uint8_t *tile_level,
+                                                                 long long rows_total,
+                                                                 uint32_t *out) {
+  const long long g = (long long)blockIdx.x * kLevelWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= rows_total) return;   // (whole warps)
+  int lo = 0, hi = V - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (views[mid].row_base <= g) lo = mid; else hi = mid - 1;
+  }
+  const ViewDev &vd = views[lo];
+  const uint8_t *tl = tile_level + vd.tile_base + (g - vd.row_base) * vd.tx;
+  unsigned first[GS_MAX_LEVELS], last[GS_MAX_LEVELS];
 #pragma unroll
-    for (int m = 0; m < GS_MAX_LEVELS; ++m) {
-      first[m] = 0xffff;
-      last[m] = 0;
-    }
-    for (int x = 0; x < vd.tx; ++x) {
-      const int lvl = tl[x];
-#pragma unroll
-      for (int m = 0; m < GS_MAX_LEVELS; ++m)
-        if (lvl <= m + 1) {
-          first[m] = min(first[m], x);
-          last[m] = max(last[m], x);
-        }
-    }
+  for (int m = 0; m < GS_MAX_LEVELS; ++m) {
+    first[m] = 0xffffu;
+    last[m] = 0u;
+  }
+  for (int x = lane; x < vd.tx; x += 32) {
+    const int lvl = tl[x];
 #pragma unroll
     for (int m = 0; m < GS_MAX_LEVELS; ++m)
-      out[g * GS_MAX_LEVELS + m] = (uint32_t)first[m] | ((uint32_t)last[m] << 16);
+      if (lvl <= m + 1) {
+        first[m] = min(first[m], (unsigned)x);
+        last[m] = max(last[m], (unsigned)x);
+      }
+  }
+#pragma unroll
+  for (int m = 0; m < GS_MAX_LEVELS; ++m) {
+    const unsigned f = __reduce_min_sync(0xffffffffu, first[m]);
+    const unsigned l = __reduce_max_sync(0xffffffffu, last[m]);
+    if (lane == 0) out[g * GS_MAX_LEVELS + m] = f | (l << 16);
   }
 }
 
 cudaError_t launch_tile_levels(const gs_plan *p, void *ws, cudaStream_t s) {
   if (!p->has_fov || p->tiles_total == 0) return cudaSuccess;
-  k_tile_levels<<<(unsigned)p->tiles_total, 64, 0, s>>>(
-      region<ViewDev>(p, ws, R_VIEWS), p->V, p->tile, p->fov.n_levels, p->fov.band_px,
-      region<uint8_t>(p, ws, R_TILE_LEVEL), p->tiles_total);
-  const long long rb = (p->rows_total + 127) / 128;
-  k_level_rows<<<(unsigned)(rb < 4096 ? rb : 4096), 128, 0, s>>>(
-      region<ViewDev>(p, ws, R_VIEWS), p->V, region<uint8_t>(p, ws, R_TILE_LEVEL), p->rows_total,
-      region<uint32_t>(p, ws, R_LEVEL_ROWS));
+  k_tile_levels<<<(unsigned)((p->tiles_total + kLevelWarps - 1) / kLevelWarps), 32 * kLevelWarps, 0,
+                  s>>>(region<ViewDev>(p, ws, R_VIEWS), p->V, p->tile, p->fov.n_levels,
+                       p->fov.band_px, region<uint8_t>(p, ws, R_TILE_LEVEL), p->tiles_total);
+  k_level_rows<<<(unsigned)((p->rows_total + kLevelWarps - 1) / kLevelWarps), 32 * kLevelWarps, 0,
+                 s>>>(region<ViewDev>(p, ws, R_VIEWS), p->V, region<uint8_t>(p, ws, R_TILE_LEVEL),
+                      p->rows_total, region<uint32_t>(p, ws, R_LEVEL_ROWS));
   return cudaGetLastError();
 }
 
