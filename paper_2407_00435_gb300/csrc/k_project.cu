@@ -575,8 +575,16 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
   const long long wid = (long long)blockIdx.x * (kCountThreads / 32) + wl;
   const bool tight = a.rec_supp != nullptr, fov = a.tile_level != nullptr;
   if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->big_count = 0u;
+  // the view of slot j = i V + v, by 32-bit division where the slots allow
+  // (a 64-bit remainder is a long instruction sequence)
+  const bool slots32 = slots <= 0xffffffffLL;
+  auto view_of = [&](long long jj) -> int {
+    if (a.V == 1) return 0;
+    return slots32 ? (int)((uint32_t)jj % (uint32_t)a.V) : (int)(jj % a.V);
+  };
   for (long long base = wid * 32; base < slots; base += warps * 32) {
     const long long j = base + lane;
+    const int vj = view_of(j);
     // every record the item may need, loaded at once (invisible slots hold
     // stale values that are never used): one round trip instead of a chain
     const bool in = j < slots;
@@ -606,7 +614,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
           // many rows: counted by the whole warp below
         } else {
           // foveation filter only: one interval lookup per row
-          const ViewDev &vd = a.views[j % a.V];
+          const ViewDev &vd = a.views[vj];
           const int m = mrec;
           uint32_t pairs = 0;
           for (int y = y0; y <= y1; ++y) {
@@ -628,7 +636,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
       if (tight) pre = supp_prep(sp, sp2);
       if (fov) {
         m = mrec;
-        rbase = a.views[j % a.V].row_base;
+        rbase = a.views[vj].row_base;
       }
     }
     // inclusive prefix of the rows over the warp
@@ -691,7 +699,6 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
     while (pending) {
       const int src = __ffs(pending) - 1;
       pending &= pending - 1;
-      const long long jb = base + src;
       const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
       const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
       const float2 s1 = make_float2(__shfl_sync(0xffffffffu, sp2.x, src),
@@ -701,7 +708,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
           __shfl_sync(0xffffffffu, sp.z, src), __shfl_sync(0xffffffffu, sp.w, src));
       const SuppPre pb = supp_prep(bsp, s1);
       const int bm = __shfl_sync(0xffffffffu, mrec, src);
-      const int brb = fov ? a.views[jb % a.V].row_base : 0;
+      const int brb = fov ? a.views[__shfl_sync(0xffffffffu, vj, src)].row_base : 0;
       uint32_t bpairs = 0;
       for (int y = by0 + lane; y <= by1; y += 32) {
         int xa, xb;
@@ -736,7 +743,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
       a.rec_emit[2 * j + 1] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
     }
     if (vis) {
-      const ViewDev &vd = a.views[a.V == 1 ? 0 : (int)(j % a.V)];
+      const ViewDev &vd = a.views[vj];
       const uint32_t corner = (uint32_t)(vd.tile_base + (long long)y0 * vd.tx + x0);
       a.rec_count[j] = my_count;
       a.rec_emit[2 * j] = make_uint4(corner, (uint32_t)(x1 - x0 + 1) | ((uint32_t)(y1 - y0 + 1) << 16),
