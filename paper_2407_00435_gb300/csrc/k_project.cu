@@ -568,7 +568,8 @@ __device__ __forceinline__ void project_value(const ProjArgs &a, const ProjSmem<
 constexpr int kCountThreads = 256;
 
 __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
-  __shared__ uint16_t s_row[kCountThreads / 32][32][kTableRows];   // xa | xb << 8 (relative)
+  __shared__ __align__(16) uint16_t s_row[kCountThreads / 32][32][kTableRows];   // xa | xb << 8
+                                                                                 //   (relative)
   const long long slots = a.n * a.V;
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const long long warps = (long long)gridDim.x * (kCountThreads / 32);
@@ -660,17 +661,19 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
       const int oexcl = __shfl_sync(0xffffffffu, excl, L);
       const int ox0 = __shfl_sync(0xffffffffu, x0, L), ox1 = __shfl_sync(0xffffffffu, x1, L);
       const int oy0 = __shfl_sync(0xffffffffu, y0, L);
-      SuppPre p;
-      p.u = __shfl_sync(0xffffffffu, pre.u, L);
-      p.v = __shfl_sync(0xffffffffu, pre.v, L);
-      p.b = __shfl_sync(0xffffffffu, pre.b, L);
-      p.ic = __shfl_sync(0xffffffffu, pre.ic, L);
-      p.det = __shfl_sync(0xffffffffu, pre.det, L);
-      p.ct = __shfl_sync(0xffffffffu, pre.ct, L);
-      p.xe = __shfl_sync(0xffffffffu, pre.xe, L);
-      p.ye = __shfl_sync(0xffffffffu, pre.ye, L);
-      p.dys = __shfl_sync(0xffffffffu, pre.dys, L);
-      p.any = __shfl_sync(0xffffffffu, (int)pre.any, L) != 0;
+      SuppPre p = {};
+      if (tight) {
+        p.u = __shfl_sync(0xffffffffu, pre.u, L);
+        p.v = __shfl_sync(0xffffffffu, pre.v, L);
+        p.b = __shfl_sync(0xffffffffu, pre.b, L);
+        p.ic = __shfl_sync(0xffffffffu, pre.ic, L);
+        p.det = __shfl_sync(0xffffffffu, pre.det, L);
+        p.ct = __shfl_sync(0xffffffffu, pre.ct, L);
+        p.xe = __shfl_sync(0xffffffffu, pre.xe, L);
+        p.ye = __shfl_sync(0xffffffffu, pre.ye, L);
+        p.dys = __shfl_sync(0xffffffffu, pre.dys, L);
+        p.any = __shfl_sync(0xffffffffu, (int)pre.any, L) != 0;
+      }
       const int om = __shfl_sync(0xffffffffu, m, L), orb = __shfl_sync(0xffffffffu, rbase, L);
       if (q < total) {
         const int r = q - oexcl, y = oy0 + r;
@@ -727,17 +730,20 @@ __global__ void __launch_bounds__(kCountThreads) k_count_pairs(ProjArgs a) {
       if (lane == src) my_count = bpairs;
     }
     if (rows) {
-      uint32_t tb[4] = {0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu, 0x00ff00ffu};
+      // the item's 8 table entries in one load; rows past its last are empty
+      // (first 255 > last 0)
+      static_assert(kTableRows == 8, "one 16-byte load per table");
+      const uint4 raw = *reinterpret_cast<const uint4 *>(&s_row[wl][lane][0]);
+      uint32_t tb[4] = {raw.x, raw.y, raw.z, raw.w};
       uint32_t pairs = 0;
-      for (int r = 0; r < rows; ++r) {
-        const uint32_t e = s_row[wl][lane][r];
+#pragma unroll
+      for (int r = 0; r < kTableRows; ++r) {
+        const int sh = 16 * (r & 1);
+        uint32_t e = (tb[r >> 1] >> sh) & 0xffffu;
+        if (r >= rows) e = 0x00ffu;
         const int first = (int)(e & 0xffu), last = (int)(e >> 8);
         if (first <= last) pairs += (uint32_t)(last - first + 1);
-        const int sh = 16 * (r & 1);
-        if (r < 2) tb[0] = (tb[0] & ~(0xffffu << sh)) | (e << sh);
-        else if (r < 4) tb[1] = (tb[1] & ~(0xffffu << sh)) | (e << sh);
-        else if (r < 6) tb[2] = (tb[2] & ~(0xffffu << sh)) | (e << sh);
-        else tb[3] = (tb[3] & ~(0xffffu << sh)) | (e << sh);
+        tb[r >> 1] = (tb[r >> 1] & ~(0xffffu << sh)) | (e << sh);
       }
       my_count = pairs;
       a.rec_emit[2 * j + 1] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
