@@ -1021,7 +1021,7 @@ static cudaError_t sort_any(const SortArgs &a, long long table_rows, cudaStream_
 struct ScanArgs {
   const uint32_t *sorted_items[2];
   const uint32_t *sel;
-  const uint32_t *count;            // rec_count (by item)
+  const uint32_t *count;            // rec_count (by item; handed on to the emit)
   uint32_t *sorted_count[2];        // the counts in depth order: the depth sort's free key
                                     //   buffer (written by the upsweep, read by the rest)
   const uint32_t *cbig;             // count | large-item flag << 31, by item slot
