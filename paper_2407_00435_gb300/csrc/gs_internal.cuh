@@ -113,7 +113,7 @@ constexpr int kSortPart = kDownThreads * kDownItems;  // 4096 keys per partition
 constexpr int kSortBlocksPerSm = 8;   // most sort blocks resident per SM (sizes the block table)
 constexpr int kSortMaxBlocks = 1024;  // grid cap of the sort's downsweep
 constexpr int kSortSub = 4;           // upsweep sub-ranges per downsweep block
-constexpr int kProjThreads = 128;
+constexpr int kProjThreads = 64;
 
 }  // namespace gs
 

@@ -782,7 +782,7 @@ __device__ __forceinline__ void write_rec(const ProjArgs &a, unsigned long long 
 // visible item) and zero pairs; the number of visible items is counted with
 // one atomic per block.
 template <int S>
-__global__ void __launch_bounds__(kProjThreads, 5) k_project(ProjArgs a) {
+__global__ void __launch_bounds__(kProjThreads, 10) k_project(ProjArgs a) {
   __shared__ ProjSmem<S> sm;
   __shared__ uint32_t s_vis, s_nonfinite, s_dmax, s_dnmin;
   const int tid = threadIdx.x;
