@@ -195,8 +195,10 @@ gs_status gs_project(gs_plan *plan, void *ws, size_t ws_bytes,
 
 /* Sorting: emit (tile, point) pairs of the visible items in depth order,
  * stable radix sort by tile, per-tile ranges and the render work list.
- * Device-side capacity overflow sets GS_ERR_CAPACITY (pairs beyond the
- * capacity are dropped, nothing is written out of bounds). */
+ * ws: the workspace gs_project was given (256-byte aligned, else
+ * GS_ERR_INVALID_ARG).  Device-side capacity overflow sets GS_ERR_CAPACITY
+ * (pairs beyond the capacity are dropped, nothing is written out of
+ * bounds). */
 gs_status gs_bin_sort(gs_plan *plan, void *ws, cudaStream_t stream);
 
 /* Rasterization of plain views (Eq. 1a) with the readings: alpha =

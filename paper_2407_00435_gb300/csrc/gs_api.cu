@@ -216,6 +216,7 @@ gs_status gs_project(gs_plan *p, void *ws, size_t ws_bytes, const gs_scene *scen
 
 gs_status gs_bin_sort(gs_plan *p, void *ws, cudaStream_t stream) {
   if (!plan_ok(p) || !ws || !p->cams) return GS_ERR_INVALID_ARG;
+  if (((uintptr_t)ws & 255) != 0) return GS_ERR_INVALID_ARG;   // (16-byte vector and bulk accesses)
   return cuda_status(launch_bin_sort(p, ws, stream));
 }
 

@@ -1131,14 +1131,24 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
   }
   for (long long part = p0; part < p1; ++part) {
     const long long base = part * kSortPart + (long long)tid * 16;
+    // a thread's 16 consecutive counts: four 16-byte loads when all are in
+    // range (base is a multiple of 16 items, the buffers 256-byte aligned)
+    const bool whole = base + 16 <= (long long)n;
     uint32_t c[16];
+    if (whole) {
+      const uint4 *s4 = reinterpret_cast<const uint4 *>(scount + base);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 v = s4[q];
+        c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) c[k] = base + k < (long long)n ? scount[base + k] : 0u;
+    }
     unsigned long long tsum = 0;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      long long idx = base + k;
-      c[k] = idx < (long long)n ? scount[idx] : 0u;
-      tsum += c[k];
-    }
+    for (int k = 0; k < 16; ++k) tsum += c[k];
     unsigned long long incl = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1154,11 +1164,21 @@ __global__ void __launch_bounds__(256) k_offsets_down(ScanArgs a) {
       total += s_w[w];
     }
     unsigned long long run = s_carry + woff + incl - tsum;
+    uint32_t o[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      long long idx = base + k;
-      if (idx < (long long)n) a.offsets[idx] = (uint32_t)(run > 0xffffffffull ? 0xffffffffull : run);
+      o[k] = (uint32_t)(run > 0xffffffffull ? 0xffffffffull : run);
       run += c[k];
+    }
+    if (whole) {
+      uint4 *o4 = reinterpret_cast<uint4 *>(a.offsets + base);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        o4[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (base + k < (long long)n) a.offsets[base + k] = o[k];
     }
     __syncthreads();
     if (tid == 0) s_carry += total;
