@@ -101,7 +101,14 @@ __device__ __forceinline__ int pixel_need_level(const ViewDev &vd, int L, float 
 
 // One warp per tile (four tiles per block); the tile's filter level is the
 // smallest level any of its pixels needs (Sec. 4.2: a point takes part in a
-// tile only if the tile's level t <= m).
+// tile only if the tile's level t <= m).  A pixel's need is a non-decreasing
+// function of its FP32 squared gaze distance (ring counts, then the band
+// test of the inner ring), and that distance, fl(fl(dx^2) + fl(dy^2)), is
+// non-decreasing in |dx| and |dy| separately; |fl(dx)| over the tile's
+// columns is smallest at a column next to gx - 1/2 (clamped to the tile), and
+// likewise for rows.  So the minimum over the tile is the need of that one
+// pixel; the 4 x 4 pixels around it are evaluated, a margin for the rounding
+// of the candidate itself.
 constexpr int kLevelWarps = 4;
 
 __global__ void __launch_bounds__(32 * kLevelWarps) k_tile_levels(const ViewDev *views, int V,
@@ -122,9 +129,15 @@ __global__ void __launch_bounds__(32 * kLevelWarps) k_tile_levels(const ViewDev 
   int bx = local % vd.tx, by = local / vd.tx;
   int need = 255;
   if (vd.fov) {
-    for (int q = lane; q < tile * tile; q += 32) {
-      int x = bx * tile + q % tile, y = by * tile + q / tile;
-      if (x < vd.W && y < vd.H) need = min(need, pixel_need_level(vd, L, band, x, y));
+    const int xa = bx * tile, xb = min(xa + tile, vd.W) - 1;
+    const int ya = by * tile, yb = min(ya + tile, vd.H) - 1;
+    if (lane < 16 && xa <= xb && ya <= yb) {
+      // (clamped as floats first: a far gaze stays in int range)
+      const int cx = (int)floorf(fminf(fmaxf(vd.gx - 0.5f, (float)xa - 2.0f), (float)xb + 2.0f));
+      const int cy = (int)floorf(fminf(fmaxf(vd.gy - 0.5f, (float)ya - 2.0f), (float)yb + 2.0f));
+      const int x = min(max(cx - 1 + (lane & 3), xa), xb);
+      const int y = min(max(cy - 1 + (lane >> 2), ya), yb);
+      need = pixel_need_level(vd, L, band, x, y);
     }
   } else {
     need = 1;
